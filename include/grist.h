@@ -1,0 +1,256 @@
+/*
+ * grist.h - C ABI of the GB300 (sm_103a) GRIST hot-path library.
+ *
+ * The library advances the explicit horizontal operators of the GRIST
+ * dynamical core (arXiv 2404.08849) on the icosahedral Voronoi C-grid over
+ * every vertical level:
+ *   - tracer transport, Eq. 10 (third-order upwind edge flux, FCT limiter,
+ *     cell-divergence gather; Sec. 2.1),
+ *   - the hydrostatic dycore (Eqs. 3-5, 8; RK + Mesinger forward-backward,
+ *     Sec. 2.1) and the non-hydrostatic dycore (Eqs. 3-7, 9; horizontally
+ *     explicit, vertically implicit, Sec. 2.1),
+ *   - compensated global mass sums (Sec. 2.3: mass conserved to FP64
+ *     round-off),
+ * in FP64 or in the paper's mixed precision (Sec. 2.2-2.3).
+ *
+ * General conventions
+ *   - Every function returns a grist_status (0 = success, < 0 = error).
+ *     Nothing aborts, exits or throws across the ABI.
+ *   - "device" pointers are CUDA global-memory pointers on the mesh's
+ *     device, owned by the caller (e.g. PyTorch tensors), and must stay
+ *     valid until the enqueued work has finished.  "host" pointers are
+ *     ordinary CPU memory, read during the call only.
+ *   - Field layout is structure-of-arrays with the level index innermost:
+ *     a layer field is [entity][ld] (ld >= n_levels, entries k >= n_levels
+ *     are never read or written); an interface field is [cell][ld_int]
+ *     (ld_int >= n_levels + 1, interface 0 = model top).
+ *   - Fields are in the library's internal numbering (cells renumbered along
+ *     a space-filling curve, see grist_mesh_permutation).
+ *   - Step calls are asynchronous on the given CUDA stream (NULL = legacy
+ *     default stream); the return code covers argument validation and launch
+ *     errors.  Numerical faults are reported by grist_last_step_status
+ *     after the stream has been synchronised.
+ *   - Calls on one mesh handle must not overlap from several host threads.
+ */
+#ifndef GRIST_H
+#define GRIST_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GRIST_OK = 0,
+    GRIST_EINVAL = -1,       /* bad argument or inconsistent mesh tables */
+    GRIST_ECUDA = -2,        /* a CUDA runtime call failed */
+    GRIST_ENOMEM = -3,       /* device or host allocation failed */
+    GRIST_ENUMERIC = -4,     /* non-finite values produced */
+    GRIST_ETIMEOUT = -5,     /* a bounded device-side wait gave up */
+    GRIST_EUNSUPPORTED = -6  /* valid but not supported request */
+} grist_status;
+
+/* Precision policy (Sec. 2.2: the KIND parameter "ns"; Sec. 2.3: the
+ * compile switch for the mass-flux divergence).
+ *   GRIST_FP64          every array and operation in double precision.
+ *   GRIST_MIX           advective terms, winds u_n and tracers stored and
+ *                       computed in single precision; pressure gradient,
+ *                       gravity, vertical integrals, the equation of state,
+ *                       the implicit column solve, surface pressure, layer
+ *                       mass and all global sums in double (Sec. 2.3).
+ *   GRIST_MIX_DBL_MASS  as GRIST_MIX but the mass flux dpi*V and its
+ *                       divergence in double (Sec. 2.3, Sec. 4.4). */
+typedef enum { GRIST_FP64 = 0, GRIST_MIX = 1, GRIST_MIX_DBL_MASS = 2 } grist_precision;
+
+/* ---------------------------------------------------------------------- */
+/* Mesh (Sec. 2.1: hexagonal Arakawa-C grid; Table 1 grid sizes)           */
+/* ---------------------------------------------------------------------- */
+
+typedef struct grist_mesh_s *grist_mesh; /* opaque, library-owned */
+
+/* Host tables of one icosahedral Voronoi mesh, 0-based, original numbering.
+ * Orientation: cells_on_edge[e] = (c1, c2), the normal points c1 -> c2;
+ * t = k x n and vertices_on_edge[e] = (v1, v2) with v2 - v1 along t.
+ * Per-cell lists are counter-clockwise seen from outside; slot 5 of a
+ * pentagon is -1.  edge_sign_on_cell = +1 where the normal leaves the cell;
+ * edge_sign_on_vertex = +1 where the normal turns counter-clockwise about
+ * the vertex.  The TRiSK weights w(e,e') give the tangential mass flux
+ * (1/dc_e) sum_e' w(e,e') dv_e' F_e'; the deriv-two stencil gives the
+ * normal second derivative at side s of edge e as sum_j coef q(stencil_j).
+ * All arrays are copied by grist_mesh_create; the caller keeps ownership. */
+typedef struct {
+    int32_t n_cells, n_edges, n_vertices, max_edges; /* max_edges must be 6 */
+    double radius;                                    /* sphere radius [m] */
+    const double *cell_xyz;                           /* [nC][3] unit vectors */
+    const double *cell_area;                          /* [nC] m^2 */
+    const double *vertex_xyz;                         /* [nV][3] */
+    const double *vertex_area;                        /* [nV] m^2 (dual triangle) */
+    const double *edge_dc;                            /* [nE] cell-centre distance */
+    const double *edge_dv;                            /* [nE] Voronoi edge length */
+    const double *f_vertex;                           /* [nV] Coriolis parameter */
+    const int32_t *cells_on_edge;                     /* [nE][2] */
+    const int32_t *vertices_on_edge;                  /* [nE][2] */
+    const int32_t *n_edges_on_cell;                   /* [nC] 5 or 6 */
+    const int32_t *edges_on_cell;                     /* [nC][6] */
+    const int32_t *cells_on_cell;                     /* [nC][6] */
+    const int32_t *edges_on_vertex;                   /* [nV][3] */
+    const int32_t *cells_on_vertex;                   /* [nV][3] */
+    const double *edge_sign_on_cell;                  /* [nC][6] +-1, 0 padding */
+    const double *edge_sign_on_vertex;                /* [nV][3] +-1 */
+    const double *kite_area;                          /* [nV][3] aligned with cells_on_vertex */
+    const int32_t *n_edges_on_edge;                   /* [nE] <= 10 */
+    const int32_t *edges_on_edge;                     /* [nE][10] */
+    const double *trisk_weight;                       /* [nE][10] */
+    const int32_t *d2_stencil;                        /* [nE][2][7], -1 padding */
+    const double *d2_coef;                            /* [nE][2][7] */
+    int32_t sfc_reorder;                              /* 1 = renumber along a Hilbert curve */
+} grist_mesh_desc;
+
+/* Validate and copy the tables (counts, index ranges, Euler characteristic,
+ * pentagon count, area sums), renumber them (sfc_reorder), pack them
+ * structure-of-arrays and upload them to `device`.  On success *out holds a
+ * handle owning all device tables and the step scratch; GRIST_EINVAL for
+ * inconsistent tables, GRIST_ECUDA / GRIST_ENOMEM on device failures.
+ * Allocates device memory; not stream-ordered (synchronous). */
+int grist_mesh_create(const grist_mesh_desc *desc, int device, grist_mesh *out);
+
+/* Free every device and host resource of the handle (synchronises the
+ * device first).  NULL is accepted. */
+int grist_mesh_destroy(grist_mesh mesh);
+
+/* Host copies of the renumbering: new index of every original cell, edge
+ * and vertex (arrays of n_cells / n_edges / n_vertices; any may be NULL). */
+int grist_mesh_permutation(grist_mesh mesh, int32_t *cell_new_of_old, int32_t *edge_new_of_old,
+                           int32_t *vertex_new_of_old);
+
+/* Entity counts of the handle (any pointer may be NULL). */
+int grist_mesh_counts(grist_mesh mesh, int32_t *n_cells, int32_t *n_edges, int32_t *n_vertices);
+
+/* ---------------------------------------------------------------------- */
+/* Tracer transport (Eq. 10, horizontal; Sec. 2.1, Sec. 2.3)               */
+/* ---------------------------------------------------------------------- */
+
+/* One ensemble member: a set of n_tracers tracers on n_levels levels.
+ *   q          device, in/out, [n_tracers][n_cells][ld]; double for
+ *              GRIST_FP64, float for the mixed policies (Sec. 2.3: tracer
+ *              transport mostly in single precision).
+ *   dpi        device, in, [n_cells][ld] double: layer mass at t^n.
+ *   mass_flux  device, in, [n_edges][ld] double: time-mean mass flux
+ *              dpi*V_n at edges (Sec. 2.3: accumulated from the continuity
+ *              equation, used in double).
+ * The layer mass at each RK stage follows the tracer solver's continuity
+ * with the same flux, dpi^(s) = dpi - dt_s div(mass_flux). */
+typedef struct {
+    int32_t n_levels, n_tracers, ld;
+    void *q;
+    const double *dpi;
+    const double *mass_flux;
+} grist_tracer_member;
+
+/* A batch of members (uneven tracer and level counts allowed) advanced in
+ * one call.  limiter: 1 = FCT on the final RK stage, 0 = none.
+ * beta_upwind: upwind weight of the third-order flux (1 = third order,
+ * 0 = fourth-order centred).  prec: GRIST_FP64 or a mixed policy. */
+typedef struct {
+    int32_t n_members;
+    const grist_tracer_member *members; /* host array of n_members */
+    grist_precision prec;
+    int32_t limiter;
+    double beta_upwind;
+} grist_tracer_batch;
+
+/* Advance every member by dt with Wicker-Skamarock RK3 (dt/3, dt/2, dt),
+ * the third-order upwind flux each stage and, if limiter, the Zalesak FCT
+ * on the final stage.  Asynchronous on `stream`.  GRIST_EINVAL on bad
+ * sizes or NULL pointers. */
+int grist_tracer_step(grist_mesh mesh, const grist_tracer_batch *batch, double dt, void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* Dycore (Eqs. 3-9; Sec. 2.1, Sec. 2.3)                                   */
+/* ---------------------------------------------------------------------- */
+
+/* Constants and vertical grid.  Pure sigma-mass coordinate:
+ * pi_{k+1/2} = pi_top + b_interface[k] (ps - pi_top), b = 0 at the top,
+ * 1 at the surface. */
+typedef struct {
+    int32_t n_levels, ld, ld_int;  /* ld >= L, ld_int >= L + 1 */
+    double pi_top;                 /* [Pa] constant model-top pressure */
+    double p0, rd, cp, g;          /* reference pressure, gas constant, heat capacity, gravity */
+    double offcentre_beta;         /* implicit weight of the NH vertical terms (0.5..1) */
+    const double *b_interface;     /* host, [L+1] */
+    const double *phi_surface;     /* device, [nC] surface geopotential */
+} grist_dycore_params;
+
+/* Prognostic state (device, in/out, caller-owned).
+ *   u           [nE][ld] edge-normal wind: double (FP64) or float (mixed)
+ *   ps          [nC] double, dry surface pressure
+ *   dpi_theta   [nC][ld] double, mass-weighted potential temperature
+ *   w, phi      [nC][ld_int] double, NH vertical velocity and geopotential
+ *               at interfaces (ignored by the hydrostatic step)
+ *   mass_flux_accum [nE][ld] double or NULL: the final-stage mass flux of
+ *               the step is added to it (time-mean flux for the tracer,
+ *               Sec. 2.3 "accumulated and averaged")
+ *   accum_weight device double or NULL: incremented by 1 per step. */
+typedef struct {
+    void *u;
+    double *ps;
+    double *dpi_theta;
+    double *w;
+    double *phi;
+    double *mass_flux_accum;
+    double *accum_weight;
+} grist_dycore_state;
+
+/* Hydrostatic step: WS-RK3, Mesinger forward-backward inside each stage
+ * (mass and theta first, then the hydrostatic diagnostics Eq. 8 from the
+ * new mass, then momentum Eq. 5).  Asynchronous on `stream`. */
+int grist_dycore_step_hydro(grist_mesh mesh, grist_dycore_state *state, const grist_dycore_params *params,
+                            grist_precision prec, double dt, void *stream);
+
+/* Non-hydrostatic step: WS-RK3 with, per stage, mass and theta, the
+ * explicit parts of w and phi (Eqs. 6-7), one FP64 tridiagonal solve per
+ * column for the implicit part (off-centred by offcentre_beta), the
+ * equation of state Eq. 9, then momentum Eq. 5 with the new pressure and
+ * geopotential.  Asynchronous on `stream`. */
+int grist_dycore_step_nh(grist_mesh mesh, grist_dycore_state *state, const grist_dycore_params *params,
+                         grist_precision prec, double dt, void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* Global sums (Sec. 2.3: global mass conserved to round-off)              */
+/* ---------------------------------------------------------------------- */
+
+typedef enum {
+    GRIST_SUM_DRY_MASS = 0,      /* sum_i A_i (field_i - offset), field [nC] double */
+    GRIST_SUM_TRACER_MASS = 1,   /* sum_{i,k} A_i dpi_{i,k} field_{i,k}, field [nC][ld] */
+    GRIST_SUM_AREA_WEIGHTED = 2  /* sum_{i,k} A_i field_{i,k}, field [nC][ld] (n_levels >= 1) */
+} grist_sum_kind;
+
+/* Deterministic compensated (Neumaier / double-double) global sum over all
+ * cells (and levels) in a fixed order.  field: device, double (field_prec
+ * GRIST_FP64) or float (mixed); dpi: device [nC][ld] double, only for the
+ * tracer mass.  out_sum_and_err: host double[2] = {sum, compensation term}.
+ * Enqueued on `stream`, then waits for the stream (the result is on the
+ * host when the call returns). */
+int grist_global_sums(grist_mesh mesh, grist_sum_kind kind, const void *field, const double *dpi,
+                      int32_t n_levels, int32_t ld, grist_precision field_prec, double offset,
+                      double *out_sum_and_err, void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* Status                                                                  */
+/* ---------------------------------------------------------------------- */
+
+#define GRIST_FLAG_NONFINITE 0x1u  /* a step wrote NaN or Inf */
+#define GRIST_FLAG_TIMEOUT 0x2u    /* a bounded device wait gave up */
+
+/* Flags raised by the steps since the previous call (read after the stream
+ * has been synchronised; synchronises the device and clears the flags). */
+int grist_last_step_status(grist_mesh mesh, uint32_t *flags);
+
+/* Static description of a status code. */
+const char *grist_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GRIST_H */

@@ -1,0 +1,191 @@
+"""GB300 (sm_103a) GRIST hot-path library - Python binding.
+
+Thin wrapper over the C ABI of ``libgrist_gb300.so`` (``include/grist.h``):
+it marshals NumPy mesh tables and PyTorch device tensors (pointers, sizes,
+the current CUDA stream) into the C structs and raises on a non-zero status.
+All computation runs in the library's CUDA kernels; there is no CPU path.
+
+Numbering: the library renumbers cells / edges / vertices along a
+space-filling curve.  ``Mesh.to_internal`` / ``Mesh.from_internal`` permute
+host arrays between the generator's numbering and the internal one.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import (GRIST_FLAG_NONFINITE, GRIST_FLAG_TIMEOUT, GRIST_FP64, GRIST_MIX, GRIST_MIX_DBL_MASS,
+                   GRIST_SUM_AREA_WEIGHTED, GRIST_SUM_DRY_MASS, GRIST_SUM_TRACER_MASS, GristError)
+
+__all__ = ["Mesh", "DycoreParams", "GRIST_FP64", "GRIST_MIX", "GRIST_MIX_DBL_MASS", "GristError",
+           "GRIST_SUM_DRY_MASS", "GRIST_SUM_TRACER_MASS", "GRIST_SUM_AREA_WEIGHTED", "load",
+           "GRIST_FLAG_NONFINITE", "GRIST_FLAG_TIMEOUT"]
+
+PREC = {"fp64": GRIST_FP64, "mix": GRIST_MIX, "mix_dbl_mass": GRIST_MIX_DBL_MASS}
+
+
+def load():
+    return _lib.load()
+
+
+def _ptr(t):
+    return ctypes.c_void_p(int(t.data_ptr())) if t is not None else None
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(stream.cuda_stream))
+
+
+def _prec(p):
+    return PREC[p] if isinstance(p, str) else int(p)
+
+
+class Mesh:
+    """Device copy of one icosahedral Voronoi mesh (``grist_mesh_create``)."""
+
+    def __init__(self, m: dict, device: int = 0, sfc_reorder: bool = True):
+        lib = _lib.load()
+        self.m = m
+        self.nC, self.nE, self.nV = int(m["n_cells"]), int(m["n_edges"]), int(m["n_vertices"])
+        d = _lib.MeshDesc()
+        self._keep = []
+
+        def dp(a):
+            a = np.ascontiguousarray(a, dtype=np.float64)
+            self._keep.append(a)
+            return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+        def ip(a):
+            a = np.ascontiguousarray(a, dtype=np.int32)
+            self._keep.append(a)
+            return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+        d.n_cells, d.n_edges, d.n_vertices, d.max_edges = self.nC, self.nE, self.nV, int(m["max_edges"])
+        d.radius = float(m["radius"])
+        for f in ("cell_xyz", "cell_area", "vertex_xyz", "vertex_area", "edge_dc", "edge_dv", "f_vertex",
+                  "edge_sign_on_cell", "edge_sign_on_vertex", "kite_area", "trisk_weight", "d2_coef"):
+            setattr(d, f, dp(m[f]))
+        for f in ("cells_on_edge", "vertices_on_edge", "n_edges_on_cell", "edges_on_cell", "cells_on_cell",
+                  "edges_on_vertex", "cells_on_vertex", "n_edges_on_edge", "edges_on_edge", "d2_stencil"):
+            setattr(d, f, ip(m[f]))
+        d.sfc_reorder = 1 if sfc_reorder else 0
+        h = ctypes.c_void_p()
+        _lib.check("grist_mesh_create", lib.grist_mesh_create(ctypes.byref(d), int(device), ctypes.byref(h)))
+        self._keep = []
+        self.handle = h
+        self.device = device
+        self.cell_new = np.empty(self.nC, np.int32)
+        self.edge_new = np.empty(self.nE, np.int32)
+        self.vertex_new = np.empty(self.nV, np.int32)
+        P = ctypes.POINTER(ctypes.c_int32)
+        _lib.check("grist_mesh_permutation", lib.grist_mesh_permutation(
+            h, self.cell_new.ctypes.data_as(P), self.edge_new.ctypes.data_as(P), self.vertex_new.ctypes.data_as(P)))
+        self.cell_old = np.argsort(self.cell_new).astype(np.int64)
+        self.edge_old = np.argsort(self.edge_new).astype(np.int64)
+        self.vertex_old = np.argsort(self.vertex_new).astype(np.int64)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.load().grist_mesh_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- numbering ---------------------------------------------------------
+    def _old(self, kind):
+        return {"cell": self.cell_old, "edge": self.edge_old, "vertex": self.vertex_old}[kind]
+
+    def _new(self, kind):
+        return {"cell": self.cell_new, "edge": self.edge_new, "vertex": self.vertex_new}[kind]
+
+    def to_internal(self, a, kind="cell", axis=0):
+        """Array in the generator's numbering -> internal numbering."""
+        return np.ascontiguousarray(np.take(np.asarray(a), self._old(kind), axis=axis))
+
+    def from_internal(self, a, kind="cell", axis=0):
+        return np.ascontiguousarray(np.take(np.asarray(a), self._new(kind), axis=axis))
+
+    # ---- steps ---------------------------------------------------------------
+    def tracer_step(self, members, dt, prec="fp64", limiter=True, beta=1.0, stream=None):
+        """members: list of dicts with torch CUDA tensors q [T][nC][ld]
+        (float64 for fp64, float32 for the mixed policies), dpi [nC][ld]
+        and mass_flux [nE][ld] (float64), and int n_levels."""
+        lib = _lib.load()
+        arr = (_lib.TracerMember * max(1, len(members)))()
+        for i, mb in enumerate(members):
+            q = mb["q"]
+            arr[i].n_levels = int(mb["n_levels"])
+            arr[i].n_tracers = int(q.shape[0])
+            arr[i].ld = int(q.shape[2])
+            arr[i].q = _ptr(q)
+            arr[i].dpi = _ptr(mb["dpi"])
+            arr[i].mass_flux = _ptr(mb["mass_flux"])
+        b = _lib.TracerBatch()
+        b.n_members = len(members)
+        b.members = arr
+        b.prec = _prec(prec)
+        b.limiter = 1 if limiter else 0
+        b.beta_upwind = float(beta)
+        _lib.check("grist_tracer_step", lib.grist_tracer_step(self.handle, ctypes.byref(b), float(dt),
+                                                              _stream_handle(stream)))
+
+    def _dycore(self, fn, state, params, prec, dt, stream):
+        lib = _lib.load()
+        s = _lib.DycoreState()
+        s.u, s.ps, s.dpi_theta = _ptr(state["u"]), _ptr(state["ps"]), _ptr(state["dpi_theta"])
+        s.w, s.phi = _ptr(state.get("w")), _ptr(state.get("phi"))
+        s.mass_flux_accum = _ptr(state.get("mass_flux_accum"))
+        s.accum_weight = _ptr(state.get("accum_weight"))
+        _lib.check(fn, getattr(lib, fn)(self.handle, ctypes.byref(s), ctypes.byref(params.c), _prec(prec),
+                                        float(dt), _stream_handle(stream)))
+
+    def dycore_step_hydro(self, state, params, dt, prec="fp64", stream=None):
+        self._dycore("grist_dycore_step_hydro", state, params, prec, dt, stream)
+
+    def dycore_step_nh(self, state, params, dt, prec="fp64", stream=None):
+        self._dycore("grist_dycore_step_nh", state, params, prec, dt, stream)
+
+    def global_sum(self, kind, field, dpi=None, n_levels=1, offset=0.0, stream=None):
+        """Compensated deterministic sum; returns (sum, compensation)."""
+        import torch
+        lib = _lib.load()
+        out = (ctypes.c_double * 2)()
+        prec = GRIST_FP64 if field.dtype == torch.float64 else GRIST_MIX
+        ld = int(field.shape[-1]) if field.dim() > 1 else 1
+        _lib.check("grist_global_sums", lib.grist_global_sums(
+            self.handle, int(kind), _ptr(field), _ptr(dpi), int(n_levels), ld, prec, float(offset), out,
+            _stream_handle(stream)))
+        return float(out[0]), float(out[1])
+
+    def last_status(self):
+        lib = _lib.load()
+        f = ctypes.c_uint32()
+        _lib.check("grist_last_step_status", lib.grist_last_step_status(self.handle, ctypes.byref(f)))
+        return int(f.value)
+
+
+class DycoreParams:
+    """grist_dycore_params; b_interface kept on the host, phi_surface a
+    device tensor [nC] (internal numbering)."""
+
+    def __init__(self, n_levels, b_interface, pi_top, phi_surface, ld=None, ld_int=None, p0=1.0e5, rd=287.04,
+                 cp=1004.64, g=9.80616, beta=0.55):
+        self.b = np.ascontiguousarray(b_interface, dtype=np.float64)
+        self.phi_surface = phi_surface
+        c = _lib.DycoreParams()
+        c.n_levels = int(n_levels)
+        c.ld = int(ld if ld is not None else n_levels)
+        c.ld_int = int(ld_int if ld_int is not None else n_levels + 1)
+        c.pi_top, c.p0, c.rd, c.cp, c.g, c.offcentre_beta = pi_top, p0, rd, cp, g, beta
+        c.b_interface = self.b.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        c.phi_surface = _ptr(phi_surface)
+        self.c = c

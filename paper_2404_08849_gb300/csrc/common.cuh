@@ -1,0 +1,130 @@
+// common.cuh - device-side mesh view, index helpers and precision policies
+// shared by the kernels of the GRIST hot-path library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "grist.h"
+
+#define GRIST_MAXE 6
+#define GRIST_MAXEOE 10
+#define GRIST_D2P 7
+#define GRIST_MAXL 256
+
+namespace grist {
+
+// Mesh tables on the device, in the library's (space-filling-curve)
+// numbering.  Per-cell / per-edge / per-vertex lists are padded to a fixed
+// width with a valid index and a zero coefficient, so every loop runs a
+// fixed trip count without branches.  Geometric factors are folded into
+// the coefficient arrays once at mesh creation:
+//   cdiv[i][j]  = s(e,i) dv_e / A_i        (cell divergence)
+//   kec[i][j]   = dc_e dv_e / (4 A_i)      (cell kinetic energy)
+//   ccurl[v][j] = t(e,v) dc_e / A_v        (vertex circulation)
+//   ckite[v][j] = kite(i,v) / A_v          (cell -> vertex remap)
+//   wpv[e][j]   = w(e,e') dv_e' / dc_e     (TRiSK tangential flux)
+//   d2c[e][s][j]= deriv-two coefficient    (normal second derivative)
+// Single-precision copies (suffix _f) feed the FP32 advective kernels.
+struct DevMesh {
+    int nC, nE, nV;
+    // cells
+    const int32_t *eoc;   // [nC][6]  pad: eoc[i][0]
+    const int32_t *coc;   // [nC][6]  pad: i itself
+    const double *cdiv;   // [nC][6]
+    const float *cdiv_f;
+    const double *kec;    // [nC][6]
+    const double *area;   // [nC]
+    // edges
+    const int2 *coe;      // [nE] (c1, c2)
+    const int2 *voe;      // [nE] (v1, v2)
+    const double *rdc;    // [nE] 1/dc
+    const double *dc2;    // [nE] dc^2/12
+    const float *dc2_f;
+    const int32_t *d2i;   // [nE][2][7] pad: centre cell
+    const double *d2c;    // [nE][2][7]
+    const float *d2c_f;
+    const int32_t *eoe;   // [nE][10] pad: e itself
+    const double *wpv;    // [nE][10]
+    const float *wpv_f;
+    // vertices
+    const int32_t *eov;   // [nV][3]
+    const int32_t *cov;   // [nV][3]
+    const double *ccurl;  // [nV][3]
+    const float *ccurl_f;
+    const double *ckite;  // [nV][3]
+    const double *fv;     // [nV]
+};
+
+// Division of a flat (entity, level) index by the level count without a
+// hardware divide: q = umulhi(n, floor((2^32-1)/d)) is floor(n/d) or one
+// less for n < 2^31; one correction step makes it exact.
+struct LevelDiv {
+    uint32_t d, m;
+};
+inline LevelDiv make_div(uint32_t d) { return LevelDiv{d, 0xFFFFFFFFu / d}; }
+
+__device__ __forceinline__ void split_index(uint32_t n, LevelDiv D, int &ent, int &k) {
+    uint32_t q = __umulhi(n, D.m);
+    uint32_t r = n - q * D.d;
+    if (r >= D.d) { q++; r -= D.d; }
+    ent = (int)q;
+    k = (int)r;
+}
+
+template <typename T> __device__ __forceinline__ T ldg(const T *p) { return __ldg(p); }
+
+// Precision policies (Sec. 2.2 "ns" kind parameter; Sec. 2.3 mass switch).
+//   TU : storage of the edge wind u_n
+//   TA : advective compute / storage (theta flux, PV flux, tracer fluxes)
+//   TM : mass flux dpi*V and its divergence
+struct PolFP64 { using TU = double; using TA = double; using TM = double; };
+struct PolMIX { using TU = float; using TA = float; using TM = float; };
+struct PolMIXDBL { using TU = float; using TA = float; using TM = double; };
+
+template <typename T> struct Coef;
+template <> struct Coef<double> {
+    static __device__ __forceinline__ const double *cdiv(const DevMesh &m) { return m.cdiv; }
+    static __device__ __forceinline__ const double *d2c(const DevMesh &m) { return m.d2c; }
+    static __device__ __forceinline__ const double *dc2(const DevMesh &m) { return m.dc2; }
+    static __device__ __forceinline__ const double *wpv(const DevMesh &m) { return m.wpv; }
+    static __device__ __forceinline__ const double *ccurl(const DevMesh &m) { return m.ccurl; }
+    static __device__ __forceinline__ double tiny() { return 2.2250738585072014e-308; }  // DBL_MIN
+};
+template <> struct Coef<float> {
+    static __device__ __forceinline__ const float *cdiv(const DevMesh &m) { return m.cdiv_f; }
+    static __device__ __forceinline__ const float *d2c(const DevMesh &m) { return m.d2c_f; }
+    static __device__ __forceinline__ const float *dc2(const DevMesh &m) { return m.dc2_f; }
+    static __device__ __forceinline__ const float *wpv(const DevMesh &m) { return m.wpv_f; }
+    static __device__ __forceinline__ const float *ccurl(const DevMesh &m) { return m.ccurl_f; }
+    static __device__ __forceinline__ float tiny() { return 1.17549435e-38f; }  // FLT_MIN
+};
+
+__device__ __forceinline__ double fmin_(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ float fmin_(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double fmax_(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float fmax_(float a, float b) { return fmaxf(a, b); }
+
+inline unsigned grid_for(long long n, int block) {
+    long long g = (n + block - 1) / block;
+    return (unsigned)(g > 0 ? g : 1);
+}
+
+}  // namespace grist
+
+// Library handle (host side), defined in mesh.cu.
+struct grist_mesh_s;
+namespace grist {
+const DevMesh &dev_mesh(grist_mesh_s *m);
+int mesh_device(grist_mesh_s *m);
+// Device scratch owned by the handle; grows (synchronously) when a call
+// needs more than the current size.  slot separates independent users.
+void *scratch(grist_mesh_s *m, int slot, size_t bytes);
+uint32_t *status_word(grist_mesh_s *m);
+}  // namespace grist
+
+#define GRIST_CUDA_TRY(x)                                  \
+    do {                                                   \
+        cudaError_t e_ = (x);                              \
+        if (e_ != cudaSuccess) return GRIST_ECUDA;         \
+    } while (0)

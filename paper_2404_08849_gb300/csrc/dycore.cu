@@ -1,0 +1,617 @@
+// dycore.cu - GRIST dry dynamical core steps (Eqs. 3-9, Sec. 2.1):
+// hydrostatic (RK3 + Mesinger forward-backward) and non-hydrostatic
+// (horizontally explicit, vertically implicit) on the Voronoi C-grid, in
+// FP64 or the paper's mixed precision (Sec. 2.3): advective terms in the
+// policy's single-precision type, pressure gradient / gravity, vertical
+// integrals, the equation of state, the column solve, surface pressure and
+// layer mass in FP64.
+//
+// Layer fields [entity][ld], interface fields [cell][ld_int]; one thread per
+// (entity, level) for the horizontal stencils, one warp per column for the
+// vertical scans (continuity prefix, hydrostatic integral) and one thread
+// per column for the tridiagonal solve.
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+
+namespace grist {
+namespace {
+
+constexpr int kBlock = 256;
+constexpr int kMaxChunks = GRIST_MAXL / 32;
+constexpr int kNHMax = 128;  // levels supported by the column solver
+
+struct DyPar {
+    int L, ld, ldi;
+    double pi_top, p0, rd, cp, g, beta, kappa, gamma;
+    const double *B;    // [L+1] interface coordinate
+    const double *dB;   // [L]   layer thickness in B
+    const double *phis; // [nC]  surface geopotential
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// Eq. 3: mass flux at edges F = dpi_e u, dpi_e = mean of the two cells.
+// In the final stage the flux is also accumulated for the tracer solver
+// (Sec. 2.3: single computed, saved double).
+template <class P>
+__global__ void k_mass_edge(DevMesh m, DyPar d, LevelDiv Dv, const double *__restrict__ ps_s,
+                            const typename P::TU *__restrict__ u_s, typename P::TM *__restrict__ F,
+                            double *__restrict__ Facc) {
+    using TM = typename P::TM;
+    uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= (uint32_t)m.nE * (uint32_t)d.L) return;
+    int e, k;
+    split_index(n, Dv, e, k);
+    const int2 c = ldg(m.coe + e);
+    const double dpe = 0.5 * ldg(d.dB + k) * ((ldg(ps_s + c.x) - d.pi_top) + (ldg(ps_s + c.y) - d.pi_top));
+    const size_t x = (size_t)e * d.ld + k;
+    const TM f = (TM)dpe * (TM)u_s[x];
+    F[x] = f;
+    if (Facc) Facc[x] += (double)f;
+}
+
+// Eq. 3 column part, one warp per cell: layer divergence D_k, surface
+// pressure tendency from FP64 column sums of the edge fluxes (each edge's
+// column sum is formed identically by both of its cells, so the global sum
+// of the tendency cancels to round-off), vertical mass flux
+// M_{k+1/2} = -B_{k+1/2} dps/dt - sum_{l<=k} D_l by a warp scan, the stage
+// update of ps, and theta = (dpi theta)/dpi of the stage input for Eq. 4.
+template <class P>
+__global__ void k_mass_col(DevMesh m, DyPar d, const typename P::TM *__restrict__ F, const double *__restrict__ ps_s,
+                           const double *__restrict__ ps_n, double *__restrict__ ps_out,
+                           const double *__restrict__ th_s, typename P::TA *__restrict__ theta,
+                           double *__restrict__ Mv, double dts) {
+    using TM = typename P::TM;
+    using TA = typename P::TA;
+    const int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= m.nC) return;
+    int eidx[GRIST_MAXE];
+    TM cw[GRIST_MAXE];
+    double cw64[GRIST_MAXE];
+#pragma unroll
+    for (int j = 0; j < GRIST_MAXE; j++) {
+        eidx[j] = ldg(m.eoc + i * 6 + j);
+        cw64[j] = ldg(m.cdiv + i * 6 + j);
+        cw[j] = (TM)cw64[j];
+    }
+    const double dps = ldg(ps_s + i) - d.pi_top;
+    double col[GRIST_MAXE] = {0, 0, 0, 0, 0, 0};
+    double Dk[kMaxChunks];
+    const int nch = (d.L + 31) >> 5;
+#pragma unroll
+    for (int ch = 0; ch < kMaxChunks; ch++) {
+        Dk[ch] = 0.0;
+        if (ch < nch) {
+            const int k = ch * 32 + lane;
+            if (k < d.L) {
+                TM s = 0;
+#pragma unroll
+                for (int j = 0; j < GRIST_MAXE; j++) {
+                    TM f = ldg(F + (size_t)eidx[j] * d.ld + k);
+                    s += cw[j] * f;
+                    col[j] += (double)f;
+                }
+                Dk[ch] = (double)s;
+                const size_t x = (size_t)i * d.ld + k;
+                theta[x] = (TA)(th_s[x] / (ldg(d.dB + k) * dps));
+            }
+        }
+    }
+    double pst = 0.0;
+#pragma unroll
+    for (int j = 0; j < GRIST_MAXE; j++) pst -= cw64[j] * warp_sum(col[j]);
+    if (lane == 0) {
+        ps_out[i] = ps_n[i] + dts * pst;
+        Mv[(size_t)i * d.ldi] = 0.0;
+        Mv[(size_t)i * d.ldi + d.L] = 0.0;
+    }
+    double run = 0.0;
+#pragma unroll
+    for (int ch = 0; ch < kMaxChunks; ch++) {
+        if (ch < nch) {
+            double v = Dk[ch];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                double t = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += t;
+            }
+            const int k = ch * 32 + lane;
+            if (k < d.L - 1) Mv[(size_t)i * d.ldi + k + 1] = -ldg(d.B + k + 1) * pst - (run + v);
+            run += __shfl_sync(0xffffffffu, v, 31);
+        }
+    }
+}
+
+// Eq. 4 horizontal flux: third-order upwind (beta = 1) edge value of theta
+// times the mass flux.
+template <class P>
+__global__ void k_theta_flux(DevMesh m, DyPar d, LevelDiv Dv, const typename P::TM *__restrict__ F,
+                             const typename P::TA *__restrict__ th, typename P::TA *__restrict__ Fth) {
+    using TA = typename P::TA;
+    uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= (uint32_t)m.nE * (uint32_t)d.L) return;
+    int e, k;
+    split_index(n, Dv, e, k);
+    const int2 c = ldg(m.coe + e);
+    const size_t x = (size_t)e * d.ld + k;
+    const TA f = (TA)F[x];
+    const int side = f >= (TA)0 ? 0 : 1;
+    const int32_t *st = m.d2i + (size_t)e * 14 + side * GRIST_D2P;
+    const TA *cf = Coef<TA>::d2c(m) + (size_t)e * 14 + side * GRIST_D2P;
+    TA s = 0;
+#pragma unroll
+    for (int j = 0; j < GRIST_D2P; j++) s += ldg(cf + j) * ldg(th + (size_t)ldg(st + j) * d.ld + k);
+    const TA te = (TA)0.5 * (ldg(th + (size_t)c.x * d.ld + k) + ldg(th + (size_t)c.y * d.ld + k)) -
+                  (TA)2 * ldg(Coef<TA>::dc2(m) + e) * s;
+    Fth[x] = f * te;
+}
+
+// Eq. 4 update: dpi theta^(s) = dpi theta^n + dt_s (-div F_theta - delta(M theta)).
+template <class P>
+__global__ void k_theta_update(DevMesh m, DyPar d, LevelDiv Dv, const typename P::TA *__restrict__ Fth,
+                               const typename P::TA *__restrict__ th, const double *__restrict__ Mv,
+                               const double *__restrict__ th_n, double *__restrict__ th_out, double dts) {
+    using TA = typename P::TA;
+    uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= (uint32_t)m.nC * (uint32_t)d.L) return;
+    int i, k;
+    split_index(n, Dv, i, k);
+    TA div = 0;
+#pragma unroll
+    for (int j = 0; j < GRIST_MAXE; j++)
+        div += ldg(Coef<TA>::cdiv(m) + i * 6 + j) * ldg(Fth + (size_t)ldg(m.eoc + i * 6 + j) * d.ld + k);
+    const size_t x = (size_t)i * d.ld + k;
+    const TA tk = th[x];
+    TA top = 0, bot = 0;
+    if (k > 0) top = (TA)Mv[(size_t)i * d.ldi + k] * ((TA)0.5 * (th[x - 1] + tk));
+    if (k < d.L - 1) bot = (TA)Mv[(size_t)i * d.ldi + k + 1] * ((TA)0.5 * (tk + th[x + 1]));
+    const TA tend = -div - (bot - top);
+    th_out[x] = th_n[x] + dts * (double)tend;
+}
+
+// Eq. 8 (hydrostatic diagnostics), one warp per column: mid-layer pressure,
+// alpha = Rd theta (p/p0)^kappa / p, geopotential integrated upward from
+// phi_s by a suffix scan, layer geopotential = mean of its interfaces.
+__global__ void k_hydro_diag(DevMesh m, DyPar d, const double *__restrict__ ps, const double *__restrict__ th,
+                             double *__restrict__ p, double *__restrict__ al, double *__restrict__ phl) {
+    const int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= m.nC) return;
+    const double dps = ps[i] - d.pi_top;
+    const int nch = (d.L + 31) >> 5;
+    double carry = ldg(d.phis + i);
+    for (int ch = nch - 1; ch >= 0; ch--) {
+        const int k = ch * 32 + lane;
+        double contrib = 0.0, a = 0.0, pk = 0.0;
+        if (k < d.L) {
+            const double pt = d.pi_top + ldg(d.B + k) * dps, pb = d.pi_top + ldg(d.B + k + 1) * dps;
+            const double dp = pb - pt;
+            pk = 0.5 * (pt + pb);
+            a = d.rd * (th[(size_t)i * d.ld + k] / dp) * pow(pk / d.p0, d.kappa) / pk;
+            contrib = a * dp;
+        }
+        // inclusive suffix sum within the chunk
+        double v = contrib;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            double t = __shfl_down_sync(0xffffffffu, v, o);
+            if (lane + o < 32) v += t;
+        }
+        if (k < d.L) {
+            const size_t x = (size_t)i * d.ld + k;
+            p[x] = pk;
+            al[x] = a;
+            phl[x] = carry + (v - contrib) + 0.5 * contrib;
+        }
+        carry += __shfl_sync(0xffffffffu, v, 0);
+    }
+}
+
+// Vertex PV, Sec. 2.3: zeta_p = (zeta + f) / dpi_v, the relative vorticity
+// from the circulation of u (advective type), dpi_v the kite-weighted remap
+// of the FP64 layer mass (dpi must be double for zeta_p).
+template <class P>
+__global__ void k_vort(DevMesh m, DyPar d, LevelDiv Dv, const typename P::TU *__restrict__ u,
+                       const double *__restrict__ ps_s, typename P::TA *__restrict__ qv) {
+    using TA = typename P::TA;
+    uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= (uint32_t)m.nV * (uint32_t)d.L) return;
+    int v, k;
+    split_index(n, Dv, v, k);
+    TA z = 0;
+    double dpv = 0.0;
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        z += ldg(Coef<TA>::ccurl(m) + v * 3 + j) * (TA)ldg(u + (size_t)ldg(m.eov + v * 3 + j) * d.ld + k);
+        dpv += ldg(m.ckite + v * 3 + j) * (ldg(ps_s + ldg(m.cov + v * 3 + j)) - d.pi_top);
+    }
+    dpv *= ldg(d.dB + k);
+    qv[(size_t)v * d.ld + k] = (TA)(((double)z + ldg(m.fv + v)) / dpv);
+}
+
+// Cell kinetic energy K = sum (dc dv / 4A) u^2 (FP64: boxed term of Eq. 5).
+template <class P>
+__global__ void k_ke(DevMesh m, DyPar d, LevelDiv Dv, const typename P::TU *__restrict__ u, double *__restrict__ K) {
+    uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= (uint32_t)m.nC * (uint32_t)d.L) return;
+    int i, k;
+    split_index(n, Dv, i, k);
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < GRIST_MAXE; j++) {
+        double ue = (double)ldg(u + (size_t)ldg(m.eoc + i * 6 + j) * d.ld + k);
+        s += ldg(m.kec + i * 6 + j) * ue * ue;
+    }
+    K[(size_t)i * d.ld + k] = s;
+}
+
+template <class P>
+__global__ void k_pv_edge(DevMesh m, DyPar d, LevelDiv Dv, const typename P::TA *__restrict__ qv,
+                          typename P::TA *__restrict__ qe) {
+    using TA = typename P::TA;
+    uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= (uint32_t)m.nE * (uint32_t)d.L) return;
+    int e, k;
+    split_index(n, Dv, e, k);
+    const int2 v = ldg(m.voe + e);
+    qe[(size_t)e * d.ld + k] = (TA)0.5 * (ldg(qv + (size_t)v.x * d.ld + k) + ldg(qv + (size_t)v.y * d.ld + k));
+}
+
+// Eq. 5 momentum tendency and stage update:
+//   PV flux (1/dc) sum w dv' F' (q_e + q_e')/2          [advective type]
+//   - dK/dn - eta-dot du/deta                              [FP64, boxed]
+//   - alpha_e dp/dn - (dp/dpi)_e dphi/dn                   [FP64]
+// with the tendency rounded to the wind's type (Sec. 2.3: boxed terms are
+// computed in double, their tendency saved in single).
+template <class P, bool NH>
+__global__ void k_momentum(DevMesh m, DyPar d, LevelDiv Dv, const typename P::TU *__restrict__ u_s,
+                           const typename P::TU *u_n, typename P::TU *u_out, const typename P::TM *__restrict__ F,
+                           const typename P::TA *__restrict__ qe, const double *__restrict__ K,
+                           const double *__restrict__ Mv, const double *__restrict__ ps_s,
+                           const double *__restrict__ p, const double *__restrict__ al,
+                           const double *__restrict__ phl, const double *__restrict__ dpp, double dts,
+                           uint32_t *status) {
+    using TA = typename P::TA;
+    using TU = typename P::TU;
+    uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= (uint32_t)m.nE * (uint32_t)d.L) return;
+    int e, k;
+    split_index(n, Dv, e, k);
+    const size_t x = (size_t)e * d.ld + k;
+    const int2 c = ldg(m.coe + e);
+    const double rdc = ldg(m.rdc + e);
+    const TA qee = ldg(qe + x);
+    TA pv = 0;
+#pragma unroll
+    for (int j = 0; j < GRIST_MAXEOE; j++) {
+        const int e2 = ldg(m.eoe + e * 10 + j);
+        const size_t y = (size_t)e2 * d.ld + k;
+        pv += ldg(Coef<TA>::wpv(m) + e * 10 + j) * (TA)ldg(F + y) * ((TA)0.5 * (qee + ldg(qe + y)));
+    }
+    const size_t a1 = (size_t)c.x * d.ld + k, a2 = (size_t)c.y * d.ld + k;
+    const double ke = (ldg(K + a2) - ldg(K + a1)) * rdc;
+    const double dpe = 0.5 * ldg(d.dB + k) * ((ldg(ps_s + c.x) - d.pi_top) + (ldg(ps_s + c.y) - d.pi_top));
+    const double uk = (double)ldg(u_s + x);
+    double va = 0.0;
+    if (k < d.L - 1) {
+        const double Mb = 0.5 * (ldg(Mv + (size_t)c.x * d.ldi + k + 1) + ldg(Mv + (size_t)c.y * d.ldi + k + 1));
+        va += Mb * ((double)ldg(u_s + x + 1) - uk);
+    }
+    if (k > 0) {
+        const double Mt = 0.5 * (ldg(Mv + (size_t)c.x * d.ldi + k) + ldg(Mv + (size_t)c.y * d.ldi + k));
+        va += Mt * (uk - (double)ldg(u_s + x - 1));
+    }
+    va /= 2.0 * dpe;
+    const double ae = 0.5 * (ldg(al + a1) + ldg(al + a2));
+    const double de = NH ? 0.5 * (ldg(dpp + a1) + ldg(dpp + a2)) : 1.0;
+    const double pgf = -ae * (ldg(p + a2) - ldg(p + a1)) * rdc - de * (ldg(phl + a2) - ldg(phl + a1)) * rdc;
+    const TA tend = pv + (TA)(pgf - ke - va);
+    const TU v = (TU)((TA)u_n[x] + (TA)dts * tend);
+    if (!isfinite((double)v)) atomicOr(status, GRIST_FLAG_NONFINITE);
+    u_out[x] = v;
+}
+
+// ---------------------------------------------------------------------------
+// Non-hydrostatic pieces (Eqs. 6, 7, 9)
+
+// Eq. 9 at time level n: p = p0 (Rd dpi_theta / (p0 dphi))^gamma.
+__global__ void k_eos(DevMesh m, DyPar d, LevelDiv Dv, const double *__restrict__ th, const double *__restrict__ phi,
+                      double *__restrict__ p) {
+    uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= (uint32_t)m.nC * (uint32_t)d.L) return;
+    int i, k;
+    split_index(n, Dv, i, k);
+    const double dphi = phi[(size_t)i * d.ldi + k] - phi[(size_t)i * d.ldi + k + 1];
+    p[(size_t)i * d.ld + k] = d.p0 * pow(d.rd * th[(size_t)i * d.ld + k] / (d.p0 * dphi), d.gamma);
+}
+
+// Explicit parts of Eqs. 6-7 at every interface: horizontal advection
+// V.grad(x) = (1/A) sum s dv u^int (x_nb - x)/2 and vertical advection
+// M (x_{j+1} - x_{j-1}) / (dpi_{j-1} + dpi_j) of w and phi from the stage
+// input (advective type; differences of the FP64 fields taken in FP64
+// first), plus the (1 - beta) share of g (dp/dpi - 1) and g w at t^n.
+template <class P>
+__global__ void k_nh_explicit(DevMesh m, DyPar d, LevelDiv Dv, const typename P::TU *__restrict__ u_s,
+                              const double *__restrict__ ps_s, const double *__restrict__ ps_n,
+                              const double *__restrict__ Mv, const double *__restrict__ w_s,
+                              const double *__restrict__ phi_s, const double *__restrict__ w_n,
+                              const double *__restrict__ phi_n, const double *__restrict__ p_n,
+                              double *__restrict__ wst, double *__restrict__ phst, double dts) {
+    using TA = typename P::TA;
+    uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+    const int Li = d.L + 1;
+    if (n >= (uint32_t)m.nC * (uint32_t)Li) return;
+    int i, j;
+    split_index(n, Dv, i, j);
+    const size_t xi = (size_t)i * d.ldi + j;
+    if (j == d.L) {
+        wst[xi] = 0.0;
+        phst[xi] = ldg(d.phis + i);
+        return;
+    }
+    const double wi = w_s[xi], pi = phi_s[xi];
+    TA hw = 0, hp = 0;
+#pragma unroll
+    for (int s = 0; s < GRIST_MAXE; s++) {
+        const int e = ldg(m.eoc + i * 6 + s);
+        const int nb = ldg(m.coc + i * 6 + s);
+        TA ui;
+        const size_t ue = (size_t)e * d.ld;
+        if (j == 0) ui = (TA)ldg(u_s + ue);
+        else ui = (TA)0.5 * ((TA)ldg(u_s + ue + j - 1) + (TA)ldg(u_s + ue + j));
+        const TA cu = ldg(Coef<TA>::cdiv(m) + i * 6 + s) * ui * (TA)0.5;
+        const size_t y = (size_t)nb * d.ldi + j;
+        hw += cu * (TA)(ldg(w_s + y) - wi);
+        hp += cu * (TA)(ldg(phi_s + y) - pi);
+    }
+    TA vw = 0, vp = 0;
+    double fw = 0.0;
+    if (j > 0) {
+        const double dps = ldg(ps_s + i) - d.pi_top;
+        const TA r = (TA)(Mv[(size_t)i * d.ldi + j] / ((ldg(d.dB + j - 1) + ldg(d.dB + j)) * dps));
+        vw = r * (TA)(w_s[xi + 1] - w_s[xi - 1]);
+        vp = r * (TA)(phi_s[xi + 1] - phi_s[xi - 1]);
+        const double dpn = 0.5 * (ldg(d.dB + j - 1) + ldg(d.dB + j)) * (ldg(ps_n + i) - d.pi_top);
+        fw = d.g * ((p_n[(size_t)i * d.ld + j] - p_n[(size_t)i * d.ld + j - 1]) / dpn - 1.0);
+    }
+    wst[xi] = w_n[xi] + dts * ((double)(-hw - vw) + (1.0 - d.beta) * fw);
+    phst[xi] = phi_n[xi] + dts * ((double)(-hp - vp) + (1.0 - d.beta) * d.g * w_n[xi]);
+}
+
+// Implicit part of Eqs. 6-7 and Eq. 9, one thread per column, FP64:
+// linearised EOS about phi**, p_k = p**_k - C_k (w_k - w_{k+1}),
+// C_k = gamma p**_k beta dt g / dphi**_k; tridiagonal rows for interior
+// interfaces j = 1..L-1 (w = 0 at top and ground) solved by the Thomas
+// algorithm; phi = phi** + beta dt g w; full EOS for p; then the
+// momentum-side diagnostics alpha = dphi/dpi, layer phi, dp/dpi averaged
+// to layers (interface value 1 at top and bottom).
+__global__ void k_nh_solve(DevMesh m, DyPar d, const double *__restrict__ wst, const double *__restrict__ phst,
+                           const double *__restrict__ th, const double *__restrict__ ps, double dts,
+                           double *__restrict__ w_out, double *__restrict__ phi_out, double *__restrict__ p,
+                           double *__restrict__ al, double *__restrict__ phl, double *__restrict__ dpp) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m.nC) return;
+    const int L = d.L;
+    const size_t ci = (size_t)i * d.ldi, cl = (size_t)i * d.ld;
+    const double bg = d.beta * dts * d.g;
+    const double dps = ps[i] - d.pi_top;
+    double cp[kNHMax], dd[kNHMax];
+    // forward sweep; p** and C of layers j-1 and j are rolled along
+    double dphi0 = phst[ci] - phst[ci + 1];
+    double pst_prev = d.p0 * pow(d.rd * th[cl] / (d.p0 * dphi0), d.gamma);
+    double C_prev = d.gamma * pst_prev * bg / dphi0;
+    for (int j = 1; j < L; j++) {
+        const double dphi = phst[ci + j] - phst[ci + j + 1];
+        const double pst = d.p0 * pow(d.rd * th[cl + j] / (d.p0 * dphi), d.gamma);
+        const double C = d.gamma * pst * bg / dphi;
+        const double aj = bg / (0.5 * (ldg(d.dB + j - 1) + ldg(d.dB + j)) * dps);
+        const double a = (j == 1) ? 0.0 : -aj * C_prev;
+        const double c = (j == L - 1) ? 0.0 : -aj * C;
+        const double b = 1.0 + aj * C_prev + aj * C;
+        const double rhs = wst[ci + j] + aj * (pst - pst_prev) - bg;
+        const int r = j - 1;
+        if (r == 0) {
+            cp[0] = c / b;
+            dd[0] = rhs / b;
+        } else {
+            const double den = b - a * cp[r - 1];
+            cp[r] = c / den;
+            dd[r] = (rhs - a * dd[r - 1]) / den;
+        }
+        pst_prev = pst;
+        C_prev = C;
+    }
+    w_out[ci] = 0.0;
+    w_out[ci + L] = 0.0;
+    double wn = 0.0;
+    for (int r = L - 2; r >= 0; r--) {
+        wn = dd[r] - cp[r] * wn;
+        w_out[ci + r + 1] = wn;
+    }
+    // phi, EOS and momentum diagnostics
+    phi_out[ci] = phst[ci];
+    for (int j = 1; j < L; j++) phi_out[ci + j] = phst[ci + j] + bg * w_out[ci + j];
+    phi_out[ci + L] = ldg(d.phis + i);
+    double p_prev = 0.0, dpdpi_top = 1.0;
+    for (int k = 0; k < L; k++) {
+        const double dphi = phi_out[ci + k] - phi_out[ci + k + 1];
+        const double dpk = ldg(d.dB + k) * dps;
+        const double pk = d.p0 * pow(d.rd * th[cl + k] / (d.p0 * dphi), d.gamma);
+        p[cl + k] = pk;
+        al[cl + k] = dphi / dpk;
+        phl[cl + k] = 0.5 * (phi_out[ci + k] + phi_out[ci + k + 1]);
+        if (k > 0) {
+            const double dint = (pk - p_prev) / (0.5 * (ldg(d.dB + k - 1) + ldg(d.dB + k)) * dps);
+            dpp[cl + k - 1] = 0.5 * (dpdpi_top + dint);
+            dpdpi_top = dint;
+        }
+        p_prev = pk;
+    }
+    dpp[cl + L - 1] = 0.5 * (dpdpi_top + 1.0);
+}
+
+__global__ void k_add_scalar(double *x, double v) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *x += v;
+}
+
+template <class P, bool NH>
+int dycore_step(grist_mesh_s *h, grist_dycore_state *S, const grist_dycore_params *prm, double dt, cudaStream_t st) {
+    using TU = typename P::TU;
+    using TA = typename P::TA;
+    using TM = typename P::TM;
+    const DevMesh &m = dev_mesh(h);
+    const int L = prm->n_levels, ld = prm->ld, ldi = prm->ld_int;
+    const size_t nCL = (size_t)m.nC * ld, nEL = (size_t)m.nE * ld, nVL = (size_t)m.nV * ld, nCI = (size_t)m.nC * ldi;
+
+    // scratch layout
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off += al(bytes); return o; };
+    const size_t o_vg = take(sizeof(double) * (2 * L + 1));
+    const size_t o_uA = take(nEL * sizeof(TU)), o_uB = take(nEL * sizeof(TU));
+    const size_t o_psA = take(m.nC * 8), o_psB = take(m.nC * 8), o_psN = take(m.nC * 8);
+    const size_t o_thA = take(nCL * 8), o_thB = take(nCL * 8);
+    const size_t o_F = take(nEL * sizeof(TM)), o_M = take(nCI * 8);
+    const size_t o_theta = take(nCL * sizeof(TA)), o_Fth = take(nEL * sizeof(TA));
+    const size_t o_p = take(nCL * 8), o_al = take(nCL * 8), o_phl = take(nCL * 8), o_dpp = take(nCL * 8);
+    const size_t o_qv = take(nVL * sizeof(TA)), o_qe = take(nEL * sizeof(TA)), o_K = take(nCL * 8);
+    size_t o_wA = 0, o_wB = 0, o_phA = 0, o_phB = 0, o_wst = 0, o_phst = 0, o_pn = 0;
+    if (NH) {
+        o_wA = take(nCI * 8); o_wB = take(nCI * 8); o_phA = take(nCI * 8); o_phB = take(nCI * 8);
+        o_wst = take(nCI * 8); o_phst = take(nCI * 8); o_pn = take(nCL * 8);
+    }
+    char *s = (char *)scratch(h, 1, off);
+    if (!s) return GRIST_ENOMEM;
+
+    // vertical grid: B at interfaces and dB per layer (copied on the stream)
+    std::vector<double> vg(2 * L + 1);
+    for (int k = 0; k <= L; k++) vg[k] = prm->b_interface[k];
+    for (int k = 0; k < L; k++) vg[L + 1 + k] = prm->b_interface[k + 1] - prm->b_interface[k];
+    double *dvg = (double *)(s + o_vg);
+    GRIST_CUDA_TRY(cudaMemcpyAsync(dvg, vg.data(), vg.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    GRIST_CUDA_TRY(cudaStreamSynchronize(st));  // vg is a host temporary
+
+    DyPar d;
+    d.L = L; d.ld = ld; d.ldi = ldi;
+    d.pi_top = prm->pi_top; d.p0 = prm->p0; d.rd = prm->rd; d.cp = prm->cp; d.g = prm->g;
+    d.beta = prm->offcentre_beta; d.kappa = prm->rd / prm->cp; d.gamma = prm->cp / (prm->cp - prm->rd);
+    d.B = dvg; d.dB = dvg + L + 1; d.phis = prm->phi_surface;
+
+    TU *uA = (TU *)(s + o_uA), *uB = (TU *)(s + o_uB);
+    double *psA = (double *)(s + o_psA), *psB = (double *)(s + o_psB), *psN = (double *)(s + o_psN);
+    double *thA = (double *)(s + o_thA), *thB = (double *)(s + o_thB);
+    TM *F = (TM *)(s + o_F);
+    double *Mv = (double *)(s + o_M);
+    TA *theta = (TA *)(s + o_theta), *Fth = (TA *)(s + o_Fth);
+    double *p = (double *)(s + o_p), *alp = (double *)(s + o_al), *phl = (double *)(s + o_phl),
+           *dpp = (double *)(s + o_dpp);
+    TA *qv = (TA *)(s + o_qv), *qe = (TA *)(s + o_qe);
+    double *K = (double *)(s + o_K);
+    double *wA = (double *)(s + o_wA), *wB = (double *)(s + o_wB), *phA = (double *)(s + o_phA),
+           *phB = (double *)(s + o_phB), *wst = (double *)(s + o_wst), *phst = (double *)(s + o_phst),
+           *pn = (double *)(s + o_pn);
+
+    TU *u = (TU *)S->u;
+    uint32_t *status = status_word(h);
+    const LevelDiv DL = make_div((uint32_t)L), DI = make_div((uint32_t)(L + 1));
+    const unsigned gC = grid_for((long long)m.nC * L, kBlock), gE = grid_for((long long)m.nE * L, kBlock),
+                   gV = grid_for((long long)m.nV * L, kBlock), gW = grid_for((long long)m.nC * 32, kBlock),
+                   gI = grid_for((long long)m.nC * (L + 1), kBlock), gCol = grid_for(m.nC, 128);
+    const double dts[3] = {dt / 3.0, dt / 2.0, dt};
+
+    GRIST_CUDA_TRY(cudaMemcpyAsync(psN, S->ps, m.nC * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (NH) k_eos<<<gC, kBlock, 0, st>>>(m, d, DL, S->dpi_theta, S->phi, pn);
+
+    const TU *u_in = u;
+    const double *ps_in = psN, *th_in = S->dpi_theta, *w_in = S->w, *phi_in = S->phi;
+    TU *u_outs[3] = {uA, uB, u};
+    double *ps_outs[3] = {psA, psB, S->ps};
+    double *th_outs[3] = {thA, thB, S->dpi_theta};
+    double *w_outs[3] = {wA, wB, S->w};
+    double *phi_outs[3] = {phA, phB, S->phi};
+    for (int s3 = 0; s3 < 3; s3++) {
+        const double h3 = dts[s3];
+        k_mass_edge<P><<<gE, kBlock, 0, st>>>(m, d, DL, ps_in, u_in, F, s3 == 2 ? S->mass_flux_accum : nullptr);
+        k_mass_col<P><<<gW, kBlock, 0, st>>>(m, d, F, ps_in, psN, ps_outs[s3], th_in, theta, Mv, h3);
+        k_theta_flux<P><<<gE, kBlock, 0, st>>>(m, d, DL, F, theta, Fth);
+        k_theta_update<P><<<gC, kBlock, 0, st>>>(m, d, DL, Fth, theta, Mv, S->dpi_theta, th_outs[s3], h3);
+        if (NH) {
+            k_nh_explicit<P><<<gI, kBlock, 0, st>>>(m, d, DI, u_in, ps_in, psN, Mv, w_in, phi_in, S->w, S->phi, pn,
+                                                    wst, phst, h3);
+            k_nh_solve<<<gCol, 128, 0, st>>>(m, d, wst, phst, th_outs[s3], ps_outs[s3], h3, w_outs[s3],
+                                            phi_outs[s3], p, alp, phl, dpp);
+        } else {
+            k_hydro_diag<<<gW, kBlock, 0, st>>>(m, d, ps_outs[s3], th_outs[s3], p, alp, phl);
+        }
+        k_vort<P><<<gV, kBlock, 0, st>>>(m, d, DL, u_in, ps_in, qv);
+        k_ke<P><<<gC, kBlock, 0, st>>>(m, d, DL, u_in, K);
+        k_pv_edge<P><<<gE, kBlock, 0, st>>>(m, d, DL, qv, qe);
+        k_momentum<P, NH><<<gE, kBlock, 0, st>>>(m, d, DL, u_in, u, u_outs[s3], F, qe, K, Mv, ps_in, p, alp, phl,
+                                                 dpp, h3, status);
+        u_in = u_outs[s3];
+        ps_in = ps_outs[s3];
+        th_in = th_outs[s3];
+        w_in = w_outs[s3];
+        phi_in = phi_outs[s3];
+    }
+    if (S->accum_weight) k_add_scalar<<<1, 32, 0, st>>>(S->accum_weight, 1.0);
+    return cudaGetLastError() == cudaSuccess ? GRIST_OK : GRIST_ECUDA;
+}
+
+int check(grist_mesh h, grist_dycore_state *S, const grist_dycore_params *prm, grist_precision prec, double dt,
+          bool nh) {
+    if (!h || !S || !prm) return GRIST_EINVAL;
+    if (!(dt > 0) || !std::isfinite(dt)) return GRIST_EINVAL;
+    if (prec != GRIST_FP64 && prec != GRIST_MIX && prec != GRIST_MIX_DBL_MASS) return GRIST_EINVAL;
+    const int L = prm->n_levels;
+    if (L < 2 || L > GRIST_MAXL || prm->ld < L || prm->ld_int < L + 1) return GRIST_EINVAL;
+    if (nh && L > kNHMax) return GRIST_EUNSUPPORTED;
+    if (!S->u || !S->ps || !S->dpi_theta || !prm->b_interface || !prm->phi_surface) return GRIST_EINVAL;
+    if (nh && (!S->w || !S->phi)) return GRIST_EINVAL;
+    if (prm->b_interface[0] != 0.0 || prm->b_interface[L] != 1.0) return GRIST_EINVAL;
+    for (int k = 0; k < L; k++)
+        if (!(prm->b_interface[k + 1] > prm->b_interface[k])) return GRIST_EINVAL;
+    if (!(prm->pi_top >= 0) || !(prm->p0 > 0) || !(prm->rd > 0) || !(prm->cp > prm->rd) || !(prm->g > 0))
+        return GRIST_EINVAL;
+    if (nh && !(prm->offcentre_beta > 0 && prm->offcentre_beta <= 1)) return GRIST_EINVAL;
+    return GRIST_OK;
+}
+
+}  // namespace
+}  // namespace grist
+
+using namespace grist;
+
+extern "C" int grist_dycore_step_hydro(grist_mesh h, grist_dycore_state *S, const grist_dycore_params *prm,
+                                       grist_precision prec, double dt, void *stream) {
+    int rc = check(h, S, prm, prec, dt, false);
+    if (rc != GRIST_OK) return rc;
+    if (cudaSetDevice(mesh_device(h)) != cudaSuccess) return GRIST_ECUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (prec) {
+        case GRIST_FP64: return dycore_step<PolFP64, false>(h, S, prm, dt, st);
+        case GRIST_MIX: return dycore_step<PolMIX, false>(h, S, prm, dt, st);
+        default: return dycore_step<PolMIXDBL, false>(h, S, prm, dt, st);
+    }
+}
+
+extern "C" int grist_dycore_step_nh(grist_mesh h, grist_dycore_state *S, const grist_dycore_params *prm,
+                                    grist_precision prec, double dt, void *stream) {
+    int rc = check(h, S, prm, prec, dt, true);
+    if (rc != GRIST_OK) return rc;
+    if (cudaSetDevice(mesh_device(h)) != cudaSuccess) return GRIST_ECUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (prec) {
+        case GRIST_FP64: return dycore_step<PolFP64, true>(h, S, prm, dt, st);
+        case GRIST_MIX: return dycore_step<PolMIX, true>(h, S, prm, dt, st);
+        default: return dycore_step<PolMIXDBL, true>(h, S, prm, dt, st);
+    }
+}
