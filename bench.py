@@ -1,0 +1,426 @@
+#!/usr/bin/env python
+"""Throughput of the GRIST hot path on one GB300 (and N independent replicas).
+
+Workload (default ``g9nh``): the mixed-precision non-hydrostatic dycore plus
+four tracers on the level-9 icosahedral mesh (2,621,442 cells, 7,864,320
+edges, 5,242,880 vertices), 60 levels on a stretched 30 km-top grid, dt =
+30 s, seeded jet + perturbation + warm bubble, tracers = bell / slotted
+cylinder / 2 Gaussians.  One step = one NH dycore step (which accumulates the
+mass flux and hands dpi to the tracer solver) + one tracer step (RK3 + FCT)
+of the 4 tracers with that flux.  The FP64 GPU path runs the same step on the
+same inputs side by side.
+
+Metric: cell-level-steps/s = n_cells * n_levels * steps / time.
+
+Output: one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle instead (the reference arm), on host cores, on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "cell-level-steps/s mixed vs FP64 on 1 GB300 at stated error; HBM GB/s vs peak"
+UNIT = "cell-level-steps/s"
+
+WORKLOADS = {
+    # name: mesh level, levels, non-hydrostatic, tracers, dt
+    "g9nh": dict(level=9, L=60, nh=True, T=4, dt=30.0,
+                 desc="NH dycore + 4 tracers (FCT), L9 mesh 2621442 cells, 60 levels, dt 30 s"),
+    "g8nh": dict(level=8, L=60, nh=True, T=0, dt=60.0,
+                 desc="NH dycore, L8 mesh 655362 cells, 60 levels, dt 60 s"),
+    "g6hdc": dict(level=6, L=30, nh=False, T=0, dt=300.0,
+                  desc="hydrostatic dycore, L6 mesh 40962 cells, 30 levels, dt 300 s"),
+}
+
+
+def algorithmic_bytes(name, nC, nE, nV, L, T, prec):
+    """Compulsory bytes of one launch: every array the kernel declares read
+    or written once (stencil re-reads, padding and index tables excluded)."""
+    base = name.split("/")[0]
+    sU = sA = sM = 8
+    if prec in ("mix", "mix_dbl_mass"):
+        sU = sA = 4
+        sM = 8 if prec == "mix_dbl_mass" else 4
+    sQ = sC = 8 if prec == "fp64" else 4
+    CL, EL, VL, CI = nC * L, nE * L, nV * L, nC * (L + 1)
+    table = {
+        "k_mass_edge": 2 * nC * 8 + EL * (sU + sM),                       # + accumulation counted below
+        "k_mass_col": EL * sM + CL * 8 + 2 * nC * 8 + nC * 8 + CL * sA + CI * 8,
+        "k_theta_flux": EL * sM + CL * sA + EL * sA,
+        "k_theta_update": EL * sA + CL * sA + CI * 8 + 2 * CL * 8,
+        "k_hydro_diag": nC * 8 + CL * 8 + 3 * CL * 8,
+        "k_vort": EL * sU + nC * 8 + VL * sA,
+        "k_ke": EL * sU + CL * 8,
+        "k_pv_edge": VL * sA + EL * sA,
+        "k_momentum": 2 * EL * sU + EL * sM + EL * sA + CL * 8 + CI * 8 + nC * 8 + 4 * CL * 8 + EL * sU,
+        "k_eos": CL * 8 + CI * 8 + CL * 8,
+        "k_nh_explicit": EL * sU + 2 * nC * 8 + CI * 8 + 4 * CI * 8 + CL * 8 + 2 * CI * 8,
+        "k_nh_solve": 2 * CI * 8 + CL * 8 + nC * 8 + 2 * CI * 8 + 4 * CL * 8,
+        "k_add_scalar": 16,
+        "k_div_mass": EL * 8 + CL * 8,
+        "k_edge_flux": T * CL * sQ + EL * 8 + T * EL * sC,
+        "k_stage_update": T * EL * sC + T * CL * sQ + 2 * CL * 8 + T * CL * sQ,
+        "k_fct_lowres": T * CL * sQ + EL * 8 + 2 * CL * 8 + T * CL * sQ,
+        "k_fct_ratios": 2 * T * CL * sQ + T * EL * sC + EL * 8 + 2 * CL * 8 + 2 * T * CL * sC,
+        "k_fct_final": T * CL * sQ + T * EL * sC + EL * 8 + 2 * CL * 8 + 2 * T * CL * sC + T * CL * sQ,
+        "k_copy": 2 * T * CL * sQ,
+    }
+    return table.get(base)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", "grist_clocks_%d_%d.csv" % (os.getpid(), gpu_index))
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+
+def setup_case(G, torch, wl, seed, device):
+    from grist_inputs import states as S
+    from grist_inputs.mesh import get_mesh
+    m = get_mesh(wl["level"])
+    mesh = G.Mesh(m, device=device)
+    L, T = wl["L"], wl["T"]
+    st = S.dycore_jet_case(m, L, nonhydrostatic=wl["nh"], bubble=wl["nh"], seed=seed)
+    q = S.tracer_mixture(m, T, L, np.random.default_rng(seed + 7)) if T else None
+    host = {"u": mesh.to_internal(st["u"], "edge"), "ps": mesh.to_internal(st["ps"]),
+            "dpi_theta": mesh.to_internal(st["dpi_theta"])}
+    if wl["nh"]:
+        host["w"] = mesh.to_internal(st["w"])
+        host["phi"] = mesh.to_internal(st["phi"])
+    if T:
+        host["q"] = mesh.to_internal(q, "cell", 1)
+    phis = torch.from_numpy(mesh.to_internal(st["phi_s"])).to(device)
+    P = G.DycoreParams(L, st["b_int"], st["pi_top"], phis)
+    return m, mesh, host, P
+
+
+def make_state(torch, host, prec, device, nE, nC, L, T, nh):
+    fdt = torch.float64 if prec == "fp64" else torch.float32
+    s = {"u": torch.from_numpy(host["u"]).to(device=device, dtype=fdt),
+         "ps": torch.from_numpy(host["ps"]).to(device),
+         "dpi_theta": torch.from_numpy(host["dpi_theta"]).to(device)}
+    if nh:
+        s["w"] = torch.from_numpy(host["w"]).to(device)
+        s["phi"] = torch.from_numpy(host["phi"]).to(device)
+    if T:
+        s["q"] = torch.from_numpy(host["q"]).to(device=device, dtype=fdt)
+        s["mass_flux_accum"] = torch.zeros((nE, L), dtype=torch.float64, device=device)
+        s["dpi_start"] = torch.zeros((nC, L), dtype=torch.float64, device=device)
+    return s
+
+
+def step(mesh, s, P, wl, prec):
+    """One step of the workload: dycore (accumulating the mass flux and
+    handing dpi^n to the tracer solver) then the tracers."""
+    if "mass_flux_accum" in s:
+        s["mass_flux_accum"].zero_()
+    if wl["nh"]:
+        mesh.dycore_step_nh(s, P, wl["dt"], prec=prec)
+    else:
+        mesh.dycore_step_hydro(s, P, wl["dt"], prec=prec)
+    if wl["T"]:
+        mesh.tracer_step([{"q": s["q"], "dpi": s["dpi_start"], "mass_flux": s["mass_flux_accum"],
+                           "n_levels": wl["L"]}], wl["dt"], prec=prec, limiter=True)
+
+
+def timed(torch, fn, K, dist=None):
+    st = torch.cuda.current_stream()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(K):
+        fn()
+    e1.record(st)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def gpu_arm(args, wl):
+    import torch
+    import paper_2404_08849_gb300 as G
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        torch.cuda.set_device(local)
+        dist_mod.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist = dist_mod
+    device = local
+    torch.cuda.set_device(device)
+    G.load()
+    from grist_inputs import states as S
+    seed = S.SEED + rank      # each rank: an independent ensemble member
+    m, mesh, host, P = setup_case(G, torch, wl, seed, device)
+    nC, nE, nV, L, T = mesh.nC, mesh.nE, mesh.nV, wl["L"], wl["T"]
+    K, W = args.steps, args.warmup
+
+    def run_prec(prec, sample_clocks=False):
+        s = make_state(torch, host, prec, device, nE, nC, L, T, wl["nh"])
+        for _ in range(W):
+            step(mesh, s, P, wl, prec)
+        torch.cuda.synchronize()
+        cs = ClockSampler(device) if sample_clocks else None
+        if cs:
+            cs.start()
+        secs = timed(torch, lambda: step(mesh, s, P, wl, prec), K, dist)
+        clocks = cs.stop() if cs else None
+        status = mesh.last_status()
+        # per-kernel event timing over a second pass of K steps
+        mesh.profile(True)
+        for _ in range(K):
+            step(mesh, s, P, wl, prec)
+        prof = mesh.profile_read()
+        mesh.profile(False)
+        # conservation check at the end of the run
+        dry = mesh.global_sum(G.GRIST_SUM_DRY_MASS, s["ps"], offset=float(P.c.pi_top))[0]
+        del s
+        torch.cuda.empty_cache()
+        return secs, clocks, prof, status, dry
+
+    secs_mix, clocks, prof_mix, st_mix, dry_mix = run_prec(args.prec, sample_clocks=True)
+    secs_64, _, prof_64, st_64, dry_64 = (run_prec("fp64") if not args.no_fp64 else (None, None, {}, 0, None))
+
+    # end to end through the public API with host buffers: pinned H2D of the
+    # state, the step, D2H of the new state, every step
+    e2e = None
+    if not args.no_e2e:
+        s = make_state(torch, host, args.prec, device, nE, nC, L, T, wl["nh"])
+        pinned = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True).copy_(v)
+                  for k, v in s.items() if k in ("u", "ps", "dpi_theta", "w", "phi", "q")}
+        h2d = sum(v.numel() * v.element_size() for v in pinned.values())
+
+        def e2e_step():
+            for k, v in pinned.items():
+                s[k].copy_(v, non_blocking=True)
+            step(mesh, s, P, wl, args.prec)
+            for k, v in pinned.items():
+                v.copy_(s[k], non_blocking=True)
+        for _ in range(W):
+            e2e_step()
+        secs_e2e = timed(torch, e2e_step, K, dist)
+        e2e = {"value": nC * L * K / secs_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(h2d)}
+        del s, pinned
+
+    # max over ranks
+    def allmax(x):
+        if dist is None or x is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+    secs_mix = allmax(secs_mix)
+    secs_64 = allmax(secs_64)
+    if e2e is not None and dist is not None:
+        e2e["value"] = world * nC * L * K / allmax(nC * L * K / e2e["value"])
+    elif e2e is not None:
+        pass
+
+    total_units = world * nC * L * K
+    value = total_units / secs_mix
+
+    # roofline of the dominant kernel of the mixed step
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    kernels = []
+    for name, (launches, ms) in sorted(prof_mix.items(), key=lambda kv: -kv[1][1]):
+        b = algorithmic_bytes(name, nC, nE, nV, L, T, args.prec)
+        avg = ms / max(launches, 1)
+        kernels.append({"kernel": name, "launches": launches, "total_ms": round(ms, 3),
+                        "avg_ms": round(avg, 4), "share": None,
+                        "gbs": round(b / (avg * 1e-3) / 1e9, 1) if b else None})
+    tot = sum(k["total_ms"] for k in kernels) or 1.0
+    for k in kernels:
+        k["share"] = round(k["total_ms"] / tot, 4)
+    dom = kernels[0] if kernels else None
+    roofline = None
+    if dom and dom["gbs"] is not None:
+        roofline = {"bound": "hbm", "kernel": dom["kernel"], "achieved": dom["gbs"], "peak": hbm_peak,
+                    "unit": "GB/s", "frac": round(dom["gbs"] / hbm_peak, 4), "traffic": None,
+                    "peak_source": peak_src}
+    launches_per_step = sum(k["launches"] for k in kernels) / max(K, 1)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(wl, level=args.cpu_level)
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+               "ms_per_step": secs_mix / K * 1e3, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "mixed f32/f64" if args.prec != "fp64" else "f64",
+               "data": "synthetic (seeded jet + perturbation + warm bubble, tracer mixture)",
+               "config": {"workload": wl["desc"], "precision": args.prec, "n_cells": nC, "n_edges": nE,
+                          "n_levels": L, "n_tracers": T, "dt_s": wl["dt"],
+                          "l2_policy": "inputs larger than L2 (state >> 129 MB), no flush",
+                          "parallelism": "independent ensemble member per GPU" if world > 1 else "single GPU"},
+               "fp64": ({"value": total_units / secs_64, "ms_per_step": secs_64 / K * 1e3,
+                         "speedup_mix_over_fp64": secs_64 / secs_mix} if secs_64 else None),
+               "roofline": roofline, "kernels": kernels[:12], "gpu_launches": int(round(launches_per_step * K)),
+               "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
+               "status_flags": {"mix": st_mix, "fp64": st_64},
+               "dry_mass_end": {"mix": dry_mix, "fp64": dry_64}}
+        print(json.dumps(out))
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline / reference arm)
+
+def oracle_step_rate(wl, level, steps=1):
+    """Time the FP64 CPU oracle on `steps` steps of the workload's physics on
+    the given mesh level; returns (cell-level-steps/s, threads, sample)."""
+    import oracle as O
+    from grist_inputs import states as S
+    from grist_inputs.mesh import get_mesh
+    m = get_mesh(level)
+    M = O.Mesh(m)
+    L, T = wl["L"], wl["T"]
+    st = S.dycore_jet_case(m, L, nonhydrostatic=wl["nh"], bubble=wl["nh"])
+    P = O.Params(L, st["b_int"], st["pi_top"], st["phi_s"])
+    q = S.tracer_mixture(m, T, L, np.random.default_rng(S.SEED + 7)) if T else None
+    s = st
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        fa = np.zeros((m["n_edges"], L))
+        dpi = st["dpi"] if s is st else None
+        if wl["nh"]:
+            s2 = O.dycore_step_nh(M, P, s, wl["dt"], flux_accum=fa)
+        else:
+            s2 = O.dycore_step_hydro(M, P, s, wl["dt"], flux_accum=fa)
+        if T:
+            pint = st["pi_top"] + st["b_int"][None, :] * (s["ps"][:, None] - st["pi_top"])
+            q = O.tracer_step(M, q, np.diff(pint, axis=1), fa, wl["dt"])
+        s = dict(s, **{k: s2[k] for k in s2 if k != "accum_weight"})
+    secs = time.perf_counter() - t0
+    sample = "%d step(s) of the same %s physics on the level-%d mesh (%d cells x %d levels)" % (
+        steps, "NH dycore + %d tracers" % T if wl["nh"] else "HDC", level, m["n_cells"], L)
+    return m["n_cells"] * L * steps / secs, O.num_threads(), sample
+
+
+def cpu_baseline(wl, level):
+    rate, cores, sample = oracle_step_rate(wl, level)
+    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+
+def reference_arm(args, wl):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    level = args.ref_level
+    for _ in range(args.warmup):
+        oracle_step_rate(wl, level)
+    rates = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r, cores, sample = oracle_step_rate(wl, level)
+        rates.append(r)
+    secs = time.perf_counter() - t0
+    value = statistics.median(rates)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": wl["desc"], "precision": "fp64 oracle"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="g9nh", choices=sorted(WORKLOADS))
+    ap.add_argument("--prec", default="mix", choices=["mix", "mix_dbl_mass", "fp64"])
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-level", type=int, default=8)
+    ap.add_argument("--ref-level", type=int, default=7)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gb300":
+        args.warmup = 3
+    os.environ.setdefault("GRIST_MESH_CACHE", "/tmp/grist_mesh_cache")
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        reference_arm(args, wl)
+    else:
+        gpu_arm(args, wl)
+
+
+if __name__ == "__main__":
+    main()

@@ -363,8 +363,28 @@ def lonlat(xyz):
 _CACHE: dict = {}
 
 
-def get_mesh(level: int):
-    """Memoised ``build_mesh(level)`` for the default Earth radius."""
-    if level not in _CACHE:
-        _CACHE[level] = build_mesh(level)
-    return _CACHE[level]
+def get_mesh(level: int, cache_dir: str | None = None):
+    """Memoised ``build_mesh(level)`` for the default Earth radius; with
+    ``cache_dir`` (or the GRIST_MESH_CACHE environment variable) the tables
+    are also kept on disk as one uncompressed .npz per level."""
+    import os
+    if level in _CACHE:
+        return _CACHE[level]
+    cache_dir = cache_dir or os.environ.get("GRIST_MESH_CACHE")
+    path = os.path.join(cache_dir, "grist_mesh_L%d.npz" % level) if cache_dir else None
+    if path and os.path.exists(path):
+        with np.load(path) as z:
+            m = {k: (z[k] if z[k].ndim else z[k].item()) for k in z.files}
+        for k in ("level", "n_cells", "n_edges", "n_vertices", "max_edges"):
+            m[k] = int(m[k])
+        for k in ("radius", "omega"):
+            m[k] = float(m[k])
+    else:
+        m = build_mesh(level)
+        if path:
+            os.makedirs(cache_dir, exist_ok=True)
+            tmp = path + ".%d.tmp.npz" % os.getpid()
+            np.savez(tmp, **m)
+            os.replace(tmp, path)
+    _CACHE[level] = m
+    return m

@@ -191,7 +191,9 @@ typedef struct {
  *   mass_flux_accum [nE][ld] double or NULL: the final-stage mass flux of
  *               the step is added to it (time-mean flux for the tracer,
  *               Sec. 2.3 "accumulated and averaged")
- *   accum_weight device double or NULL: incremented by 1 per step. */
+ *   accum_weight device double or NULL: incremented by 1 per step.
+ *   dpi_start   [nC][ld] double or NULL: receives the layer mass dpi at
+ *               the start of the step (the tracer solver's dpi^n). */
 typedef struct {
     void *u;
     double *ps;
@@ -200,6 +202,7 @@ typedef struct {
     double *phi;
     double *mass_flux_accum;
     double *accum_weight;
+    double *dpi_start;
 } grist_dycore_state;
 
 /* Hydrostatic step: WS-RK3, Mesinger forward-backward inside each stage
@@ -235,6 +238,24 @@ typedef enum {
 int grist_global_sums(grist_mesh mesh, grist_sum_kind kind, const void *field, const double *dpi,
                       int32_t n_levels, int32_t ld, grist_precision field_prec, double offset,
                       double *out_sum_and_err, void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* Measurement aid (no counterpart in the paper)                           */
+/* ---------------------------------------------------------------------- */
+
+/* Enable (1) or disable (0) per-kernel timing on this handle.  While
+ * enabled, every kernel launch of the step calls is bracketed by a pair of
+ * CUDA events on the launching stream; enabling clears earlier totals.
+ * Costs about one event record per launch; leave it off for production. */
+int grist_profile_enable(grist_mesh mesh, int enable);
+
+/* Synchronise the device and report the per-kernel totals gathered since
+ * the last grist_profile_enable(mesh, 1): for entry j < *n_entries,
+ * names + 64*j is a NUL-terminated kernel name, launches[j] the launch
+ * count and total_ms[j] the summed event time in milliseconds.  At most
+ * max_entries entries are written (host arrays, caller-owned). */
+int grist_profile_read(grist_mesh mesh, int32_t max_entries, char *names, int32_t *launches, double *total_ms,
+                       int32_t *n_entries);
 
 /* ---------------------------------------------------------------------- */
 /* Status                                                                  */

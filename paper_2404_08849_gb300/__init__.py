@@ -145,6 +145,7 @@ class Mesh:
         s.w, s.phi = _ptr(state.get("w")), _ptr(state.get("phi"))
         s.mass_flux_accum = _ptr(state.get("mass_flux_accum"))
         s.accum_weight = _ptr(state.get("accum_weight"))
+        s.dpi_start = _ptr(state.get("dpi_start"))
         _lib.check(fn, getattr(lib, fn)(self.handle, ctypes.byref(s), ctypes.byref(params.c), _prec(prec),
                                         float(dt), _stream_handle(stream)))
 
@@ -165,6 +166,25 @@ class Mesh:
             self.handle, int(kind), _ptr(field), _ptr(dpi), int(n_levels), ld, prec, float(offset), out,
             _stream_handle(stream)))
         return float(out[0]), float(out[1])
+
+    def profile(self, enable: bool):
+        """Turn per-kernel CUDA-event timing on (clears totals) or off."""
+        _lib.check("grist_profile_enable", _lib.load().grist_profile_enable(self.handle, 1 if enable else 0))
+
+    def profile_read(self, max_entries: int = 128):
+        """{kernel name: (launches, total_ms)} since profiling was enabled."""
+        lib = _lib.load()
+        names = ctypes.create_string_buffer(64 * max_entries)
+        launches = (ctypes.c_int32 * max_entries)()
+        ms = (ctypes.c_double * max_entries)()
+        n = ctypes.c_int32()
+        _lib.check("grist_profile_read", lib.grist_profile_read(self.handle, max_entries, names, launches, ms,
+                                                                ctypes.byref(n)))
+        out = {}
+        for j in range(n.value):
+            nm = names.raw[64 * j:64 * (j + 1)].split(b"\0", 1)[0].decode()
+            out[nm] = (int(launches[j]), float(ms[j]))
+        return out
 
     def last_status(self):
         lib = _lib.load()

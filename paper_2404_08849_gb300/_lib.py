@@ -47,7 +47,7 @@ class DycoreParams(ctypes.Structure):
 
 class DycoreState(ctypes.Structure):
     _fields_ = [("u", _V), ("ps", _V), ("dpi_theta", _V), ("w", _V), ("phi", _V), ("mass_flux_accum", _V),
-                ("accum_weight", _V)]
+                ("accum_weight", _V), ("dpi_start", _V)]
 
 
 EXPORTS = {
@@ -61,6 +61,8 @@ EXPORTS = {
     "grist_global_sums": ([_V, ctypes.c_int, _V, _V, _I, _I, ctypes.c_int, _D, _P(_D), _V], ctypes.c_int),
     "grist_last_step_status": ([_V, _P(ctypes.c_uint32)], ctypes.c_int),
     "grist_status_string": ([ctypes.c_int], ctypes.c_char_p),
+    "grist_profile_enable": ([_V, ctypes.c_int], ctypes.c_int),
+    "grist_profile_read": ([_V, _I, ctypes.c_char_p, _P(_I), _P(_D), _P(_I)], ctypes.c_int),
 }
 
 _lib = None

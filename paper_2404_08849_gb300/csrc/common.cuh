@@ -121,7 +121,23 @@ int mesh_device(grist_mesh_s *m);
 // needs more than the current size.  slot separates independent users.
 void *scratch(grist_mesh_s *m, int slot, size_t bytes);
 uint32_t *status_word(grist_mesh_s *m);
+
+// Per-kernel event timing (grist_profile_enable): when profiling is on, the
+// scope records an event before and after the launch it encloses.
+struct ProfScope {
+    grist_mesh_s *h;
+    int slot;
+    cudaStream_t st;
+    ProfScope(grist_mesh_s *h, const char *name, cudaStream_t st);
+    ~ProfScope();
+};
 }  // namespace grist
+
+#define GRIST_LAUNCH(h, name, st, ...)                     \
+    do {                                                   \
+        ::grist::ProfScope prof_scope_(h, name, st);       \
+        __VA_ARGS__;                                       \
+    } while (0)
 
 #define GRIST_CUDA_TRY(x)                                  \
     do {                                                   \

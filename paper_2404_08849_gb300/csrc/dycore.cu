@@ -15,6 +15,8 @@
 
 #include "common.cuh"
 
+#define PN(n) (sizeof(TA) == 4 ? (sizeof(TM) == 8 ? n "/mixdbl" : n "/mix") : n "/fp64")
+
 namespace grist {
 namespace {
 
@@ -67,7 +69,7 @@ template <class P>
 __global__ void k_mass_col(DevMesh m, DyPar d, const typename P::TM *__restrict__ F, const double *__restrict__ ps_s,
                            const double *__restrict__ ps_n, double *__restrict__ ps_out,
                            const double *__restrict__ th_s, typename P::TA *__restrict__ theta,
-                           double *__restrict__ Mv, double dts) {
+                           double *__restrict__ Mv, double dts, double *__restrict__ dpi_out) {
     using TM = typename P::TM;
     using TA = typename P::TA;
     const int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -101,7 +103,9 @@ __global__ void k_mass_col(DevMesh m, DyPar d, const typename P::TM *__restrict_
                 }
                 Dk[ch] = (double)s;
                 const size_t x = (size_t)i * d.ld + k;
-                theta[x] = (TA)(th_s[x] / (ldg(d.dB + k) * dps));
+                const double dpk = ldg(d.dB + k) * dps;
+                theta[x] = (TA)(th_s[x] / dpk);
+                if (dpi_out) dpi_out[x] = dpk;
             }
         }
     }
@@ -539,23 +543,24 @@ int dycore_step(grist_mesh_s *h, grist_dycore_state *S, const grist_dycore_param
     double *phi_outs[3] = {phA, phB, S->phi};
     for (int s3 = 0; s3 < 3; s3++) {
         const double h3 = dts[s3];
-        k_mass_edge<P><<<gE, kBlock, 0, st>>>(m, d, DL, ps_in, u_in, F, s3 == 2 ? S->mass_flux_accum : nullptr);
-        k_mass_col<P><<<gW, kBlock, 0, st>>>(m, d, F, ps_in, psN, ps_outs[s3], th_in, theta, Mv, h3);
-        k_theta_flux<P><<<gE, kBlock, 0, st>>>(m, d, DL, F, theta, Fth);
-        k_theta_update<P><<<gC, kBlock, 0, st>>>(m, d, DL, Fth, theta, Mv, S->dpi_theta, th_outs[s3], h3);
+        GRIST_LAUNCH(h, PN("k_mass_edge"), st, k_mass_edge<P><<<gE, kBlock, 0, st>>>(m, d, DL, ps_in, u_in, F, s3 == 2 ? S->mass_flux_accum : nullptr));
+        GRIST_LAUNCH(h, PN("k_mass_col"), st, k_mass_col<P><<<gW, kBlock, 0, st>>>(m, d, F, ps_in, psN, ps_outs[s3], th_in, theta, Mv, h3,
+                                                  s3 == 0 ? S->dpi_start : nullptr));
+        GRIST_LAUNCH(h, PN("k_theta_flux"), st, k_theta_flux<P><<<gE, kBlock, 0, st>>>(m, d, DL, F, theta, Fth));
+        GRIST_LAUNCH(h, PN("k_theta_update"), st, k_theta_update<P><<<gC, kBlock, 0, st>>>(m, d, DL, Fth, theta, Mv, S->dpi_theta, th_outs[s3], h3));
         if (NH) {
-            k_nh_explicit<P><<<gI, kBlock, 0, st>>>(m, d, DI, u_in, ps_in, psN, Mv, w_in, phi_in, S->w, S->phi, pn,
-                                                    wst, phst, h3);
-            k_nh_solve<<<gCol, 128, 0, st>>>(m, d, wst, phst, th_outs[s3], ps_outs[s3], h3, w_outs[s3],
-                                            phi_outs[s3], p, alp, phl, dpp);
+            GRIST_LAUNCH(h, PN("k_nh_explicit"), st, k_nh_explicit<P><<<gI, kBlock, 0, st>>>(m, d, DI, u_in, ps_in, psN, Mv, w_in, phi_in, S->w, S->phi, pn,
+                                                    wst, phst, h3));
+            GRIST_LAUNCH(h, PN("k_nh_solve"), st, k_nh_solve<<<gCol, 128, 0, st>>>(m, d, wst, phst, th_outs[s3], ps_outs[s3], h3, w_outs[s3],
+                                            phi_outs[s3], p, alp, phl, dpp));
         } else {
-            k_hydro_diag<<<gW, kBlock, 0, st>>>(m, d, ps_outs[s3], th_outs[s3], p, alp, phl);
+            GRIST_LAUNCH(h, PN("k_hydro_diag"), st, k_hydro_diag<<<gW, kBlock, 0, st>>>(m, d, ps_outs[s3], th_outs[s3], p, alp, phl));
         }
-        k_vort<P><<<gV, kBlock, 0, st>>>(m, d, DL, u_in, ps_in, qv);
-        k_ke<P><<<gC, kBlock, 0, st>>>(m, d, DL, u_in, K);
-        k_pv_edge<P><<<gE, kBlock, 0, st>>>(m, d, DL, qv, qe);
-        k_momentum<P, NH><<<gE, kBlock, 0, st>>>(m, d, DL, u_in, u, u_outs[s3], F, qe, K, Mv, ps_in, p, alp, phl,
-                                                 dpp, h3, status);
+        GRIST_LAUNCH(h, PN("k_vort"), st, k_vort<P><<<gV, kBlock, 0, st>>>(m, d, DL, u_in, ps_in, qv));
+        GRIST_LAUNCH(h, PN("k_ke"), st, k_ke<P><<<gC, kBlock, 0, st>>>(m, d, DL, u_in, K));
+        GRIST_LAUNCH(h, PN("k_pv_edge"), st, k_pv_edge<P><<<gE, kBlock, 0, st>>>(m, d, DL, qv, qe));
+        GRIST_LAUNCH(h, PN("k_momentum"), st, k_momentum<P, NH><<<gE, kBlock, 0, st>>>(m, d, DL, u_in, u, u_outs[s3], F, qe, K, Mv, ps_in, p, alp, phl,
+                                                 dpp, h3, status));
         u_in = u_outs[s3];
         ps_in = ps_outs[s3];
         th_in = th_outs[s3];

@@ -7,6 +7,7 @@
 #include <mutex>
 #include <new>
 #include <numeric>
+#include <string>
 #include <vector>
 
 #include "common.cuh"
@@ -22,12 +23,55 @@ struct grist_mesh_s {
     void *scr[8] = {nullptr};
     size_t scr_bytes[8] = {0};
     uint32_t *status = nullptr;
+    // profiling
+    bool prof_on = false;
+    std::vector<cudaEvent_t> ev;            // pool, pairs (2j, 2j+1)
+    std::vector<int> pend_name;             // name id of each pending pair
+    std::vector<std::string> prof_names;
+    std::vector<double> prof_ms;
+    std::vector<int> prof_count;
 };
 
 namespace grist {
 const DevMesh &dev_mesh(grist_mesh_s *m) { return m->d; }
 int mesh_device(grist_mesh_s *m) { return m->device; }
 uint32_t *status_word(grist_mesh_s *m) { return m->status; }
+
+static const int kEventPairs = 4096;
+
+static void prof_drain(grist_mesh_s *m) {
+    if (m->pend_name.empty()) return;
+    cudaDeviceSynchronize();
+    for (size_t j = 0; j < m->pend_name.size(); j++) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, m->ev[2 * j], m->ev[2 * j + 1]) == cudaSuccess) {
+            m->prof_ms[m->pend_name[j]] += ms;
+            m->prof_count[m->pend_name[j]] += 1;
+        }
+    }
+    m->pend_name.clear();
+}
+
+ProfScope::ProfScope(grist_mesh_s *h_, const char *name, cudaStream_t st_) : h(h_), slot(-1), st(st_) {
+    if (!h || !h->prof_on) return;
+    if ((int)h->pend_name.size() >= kEventPairs) prof_drain(h);
+    int id = -1;
+    for (size_t j = 0; j < h->prof_names.size(); j++)
+        if (h->prof_names[j] == name) { id = (int)j; break; }
+    if (id < 0) {
+        h->prof_names.push_back(name);
+        h->prof_ms.push_back(0.0);
+        h->prof_count.push_back(0);
+        id = (int)h->prof_names.size() - 1;
+    }
+    slot = (int)h->pend_name.size();
+    h->pend_name.push_back(id);
+    cudaEventRecord(h->ev[2 * slot], st);
+}
+
+ProfScope::~ProfScope() {
+    if (slot >= 0) cudaEventRecord(h->ev[2 * slot + 1], st);
+}
 
 void *scratch(grist_mesh_s *m, int slot, size_t bytes) {
     if (slot < 0 || slot >= 8) return nullptr;
@@ -344,10 +388,46 @@ extern "C" int grist_mesh_create(const grist_mesh_desc *desc, int device, grist_
     return GRIST_OK;
 }
 
+extern "C" int grist_profile_enable(grist_mesh m, int enable) {
+    if (!m) return GRIST_EINVAL;
+    if (cudaSetDevice(m->device) != cudaSuccess) return GRIST_ECUDA;
+    if (enable && m->ev.empty()) {
+        m->ev.resize(2 * kEventPairs);
+        for (auto &e : m->ev)
+            if (cudaEventCreate(&e) != cudaSuccess) return GRIST_ECUDA;
+    }
+    if (cudaDeviceSynchronize() != cudaSuccess) return GRIST_ECUDA;
+    m->pend_name.clear();
+    m->prof_names.clear();
+    m->prof_ms.clear();
+    m->prof_count.clear();
+    m->prof_on = enable != 0;
+    return GRIST_OK;
+}
+
+extern "C" int grist_profile_read(grist_mesh m, int32_t max_entries, char *names, int32_t *launches,
+                                  double *total_ms, int32_t *n_entries) {
+    if (!m || !n_entries || max_entries < 0) return GRIST_EINVAL;
+    if (cudaSetDevice(m->device) != cudaSuccess) return GRIST_ECUDA;
+    prof_drain(m);
+    int n = (int)std::min<size_t>(m->prof_names.size(), (size_t)max_entries);
+    for (int j = 0; j < n; j++) {
+        if (names) {
+            std::strncpy(names + 64 * j, m->prof_names[j].c_str(), 63);
+            names[64 * j + 63] = 0;
+        }
+        if (launches) launches[j] = m->prof_count[j];
+        if (total_ms) total_ms[j] = m->prof_ms[j];
+    }
+    *n_entries = n;
+    return GRIST_OK;
+}
+
 extern "C" int grist_mesh_destroy(grist_mesh m) {
     if (!m) return GRIST_OK;
     cudaSetDevice(m->device);
     cudaDeviceSynchronize();
+    for (auto &e : m->ev) cudaEventDestroy(e);
     for (int s = 0; s < 8; s++)
         if (m->scr[s]) cudaFree(m->scr[s]);
     if (m->arena) cudaFree(m->arena);

@@ -13,6 +13,8 @@
 
 #include "common.cuh"
 
+#define PN(n) (sizeof(TC) == 4 ? n "/mix" : n "/fp64")
+
 namespace grist {
 namespace {
 
@@ -299,29 +301,29 @@ int member_step(grist_mesh_s *h, const grist_tracer_member &mb, int limiter, dou
     const bool b1 = beta == 1.0;
     const double dts[3] = {dt / 3.0, dt / 2.0, dt};
 
-    k_div_mass<<<gC, kBlock, 0, st>>>(m, L, ld, D, mb.mass_flux, divF);
+    GRIST_LAUNCH(h, PN("k_div_mass"), st, k_div_mass<<<gC, kBlock, 0, st>>>(m, L, ld, D, mb.mass_flux, divF));
     const TQ *in = q;
     TQ *outs[2] = {qA, qB};
     for (int s3 = 0; s3 < 3; s3++) {
         if (b1)
-            k_edge_flux<TQ, TC, true><<<gE, kBlock, 0, st>>>(m, T, L, ld, D, in, qs, mb.mass_flux, (TC)beta, FH, fs);
+            GRIST_LAUNCH(h, PN("k_edge_flux"), st, k_edge_flux<TQ, TC, true><<<gE, kBlock, 0, st>>>(m, T, L, ld, D, in, qs, mb.mass_flux, (TC)beta, FH, fs));
         else
-            k_edge_flux<TQ, TC, false><<<gE, kBlock, 0, st>>>(m, T, L, ld, D, in, qs, mb.mass_flux, (TC)beta, FH, fs);
+            GRIST_LAUNCH(h, PN("k_edge_flux"), st, k_edge_flux<TQ, TC, false><<<gE, kBlock, 0, st>>>(m, T, L, ld, D, in, qs, mb.mass_flux, (TC)beta, FH, fs));
         if (s3 < 2) {
-            k_stage_update<TQ, TC><<<gC, kBlock, 0, st>>>(m, T, L, ld, D, q, outs[s3], qs, FH, fs, mb.dpi, divF,
-                                                         dts[s3], status);
+            GRIST_LAUNCH(h, PN("k_stage_update"), st, k_stage_update<TQ, TC><<<gC, kBlock, 0, st>>>(m, T, L, ld, D, q, outs[s3], qs, FH, fs, mb.dpi, divF,
+                                                         dts[s3], status));
             in = outs[s3];
         } else if (!limiter) {
             // final stage without limiter: each thread reads only its own q^n
-            k_stage_update<TQ, TC><<<gC, kBlock, 0, st>>>(m, T, L, ld, D, q, q, qs, FH, fs, mb.dpi, divF, dt,
-                                                         status);
+            GRIST_LAUNCH(h, PN("k_stage_update"), st, k_stage_update<TQ, TC><<<gC, kBlock, 0, st>>>(m, T, L, ld, D, q, q, qs, FH, fs, mb.dpi, divF, dt,
+                                                         status));
         } else {
-            k_fct_lowres<TQ, TC><<<gC, kBlock, 0, st>>>(m, T, L, ld, D, q, qs, mb.mass_flux, mb.dpi, divF, dt, qA);
-            k_fct_ratios<TQ, TC><<<gC, kBlock, 0, st>>>(m, T, L, ld, D, q, qA, qs, FH, fs, mb.mass_flux, mb.dpi,
-                                                       divF, dt, Rp, Rm);
-            k_fct_final<TQ, TC><<<gC, kBlock, 0, st>>>(m, T, L, ld, D, q, qB, qs, FH, fs, mb.mass_flux, mb.dpi,
-                                                      divF, dt, Rp, Rm, status);
-            k_copy<TQ><<<1024, kBlock, 0, st>>>(qB, q, (size_t)T * qs);
+            GRIST_LAUNCH(h, PN("k_fct_lowres"), st, k_fct_lowres<TQ, TC><<<gC, kBlock, 0, st>>>(m, T, L, ld, D, q, qs, mb.mass_flux, mb.dpi, divF, dt, qA));
+            GRIST_LAUNCH(h, PN("k_fct_ratios"), st, k_fct_ratios<TQ, TC><<<gC, kBlock, 0, st>>>(m, T, L, ld, D, q, qA, qs, FH, fs, mb.mass_flux, mb.dpi,
+                                                       divF, dt, Rp, Rm));
+            GRIST_LAUNCH(h, PN("k_fct_final"), st, k_fct_final<TQ, TC><<<gC, kBlock, 0, st>>>(m, T, L, ld, D, q, qB, qs, FH, fs, mb.mass_flux, mb.dpi,
+                                                      divF, dt, Rp, Rm, status));
+            GRIST_LAUNCH(h, PN("k_copy"), st, k_copy<TQ><<<1024, kBlock, 0, st>>>(qB, q, (size_t)T * qs));
         }
     }
     return cudaGetLastError() == cudaSuccess ? GRIST_OK : GRIST_ECUDA;
