@@ -10,6 +10,12 @@
 // (entity, level) for the horizontal stencils, one warp per column for the
 // vertical scans (continuity prefix, hydrostatic integral) and one thread
 // per column for the tridiagonal solve.
+//
+// FP64 arithmetic is the scarce resource on this GPU (about 1/60 of the FP32
+// rate), so divisions by layer masses are replaced by products with
+// reciprocals formed once per column / edge / vertex (1/(ps - pi_top)) and
+// once per level (1/dB), and the equation of state inside a stage is
+// evaluated relative to the stage-input state (see pow_near1).
 #include <cmath>
 #include <vector>
 
@@ -27,9 +33,11 @@ constexpr int kNHMax = 128;  // levels supported by the column solver
 struct DyPar {
     int L, ld, ldi;
     double pi_top, p0, rd, cp, g, beta, kappa, gamma;
-    const double *B;    // [L+1] interface coordinate
-    const double *dB;   // [L]   layer thickness in B
-    const double *phis; // [nC]  surface geopotential
+    const double *B;      // [L+1] interface coordinate
+    const double *dB;     // [L]   layer thickness in B
+    const double *rdB;    // [L]   1/dB
+    const double *rdBi;   // [L+1] 2/(dB[j-1] + dB[j]) at interior interfaces j
+    const double *phis;   // [nC]  surface geopotential
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -38,25 +46,59 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+__device__ __forceinline__ double rcp(double x) { return __drcp_rn(x); }
+
+// r^g for a ratio r close to 1: log(1+x) by its Mercator series
+// x - x^2/2 + ... + x^9/9 and exp(y) by its Taylor series to y^8/8!, both in
+// FP64; for |x| <= 2^-6 the truncation errors are below 1e-17 relative.
+// Outside that range the library pow() is used.
+__device__ __forceinline__ double pow_near1(double r, double g) {
+    const double x = r - 1.0;
+    if (fabs(x) > 0.015625) return pow(r, g);
+    double l = 1.0 / 9.0;
+    l = fma(l, x, -1.0 / 8.0);
+    l = fma(l, x, 1.0 / 7.0);
+    l = fma(l, x, -1.0 / 6.0);
+    l = fma(l, x, 1.0 / 5.0);
+    l = fma(l, x, -1.0 / 4.0);
+    l = fma(l, x, 1.0 / 3.0);
+    l = fma(l, x, -1.0 / 2.0);
+    l = fma(l, x, 1.0);
+    const double y = g * (l * x);
+    double e = 1.0 / 40320.0;
+    e = fma(e, y, 1.0 / 5040.0);
+    e = fma(e, y, 1.0 / 720.0);
+    e = fma(e, y, 1.0 / 120.0);
+    e = fma(e, y, 1.0 / 24.0);
+    e = fma(e, y, 1.0 / 6.0);
+    e = fma(e, y, 0.5);
+    e = fma(e, y, 1.0);
+    return fma(e, y, 1.0);
+}
+
 // ---------------------------------------------------------------------------
-// Eq. 3: mass flux at edges F = dpi_e u, dpi_e = mean of the two cells.
+// Eq. 3: mass flux at edges F = dpi_e u, dpi_e = mean of the two cells'
+// layer mass = dB_k (ps1 + ps2 - 2 pi_top)/2.  The column factor is formed in
+// FP64 once per edge and the product in the mass-flux type.  The edge's
+// reciprocal 1/(ps1 + ps2 - 2 pi_top) is kept for the momentum equation.
 // In the final stage the flux is also accumulated for the tracer solver
 // (Sec. 2.3: single computed, saved double).
 template <class P>
 __global__ void k_mass_edge(DevMesh m, DyPar d, LevelDiv Dv, const double *__restrict__ ps_s,
                             const typename P::TU *__restrict__ u_s, typename P::TM *__restrict__ F,
-                            double *__restrict__ Facc) {
+                            double *__restrict__ Facc, double *__restrict__ rsum_e) {
     using TM = typename P::TM;
     uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= (uint32_t)m.nE * (uint32_t)d.L) return;
     int e, k;
     split_index(n, Dv, e, k);
     const int2 c = ldg(m.coe + e);
-    const double dpe = 0.5 * ldg(d.dB + k) * ((ldg(ps_s + c.x) - d.pi_top) + (ldg(ps_s + c.y) - d.pi_top));
+    const double sum = (ldg(ps_s + c.x) - d.pi_top) + (ldg(ps_s + c.y) - d.pi_top);
     const size_t x = (size_t)e * d.ld + k;
-    const TM f = (TM)dpe * (TM)u_s[x];
+    const TM f = (TM)(0.5 * ldg(d.dB + k)) * (TM)sum * (TM)u_s[x];
     F[x] = f;
     if (Facc) Facc[x] += (double)f;
+    if (k == 0) rsum_e[e] = rcp(sum);
 }
 
 // Eq. 3 column part, one warp per cell: layer divergence D_k, surface
@@ -64,12 +106,14 @@ __global__ void k_mass_edge(DevMesh m, DyPar d, LevelDiv Dv, const double *__res
 // column sum is formed identically by both of its cells, so the global sum
 // of the tendency cancels to round-off), vertical mass flux
 // M_{k+1/2} = -B_{k+1/2} dps/dt - sum_{l<=k} D_l by a warp scan, the stage
-// update of ps, and theta = (dpi theta)/dpi of the stage input for Eq. 4.
+// update of ps, theta = (dpi theta)/dpi of the stage input for Eq. 4, and
+// the column reciprocal 1/(ps - pi_top) of the stage input.
 template <class P>
 __global__ void k_mass_col(DevMesh m, DyPar d, const typename P::TM *__restrict__ F, const double *__restrict__ ps_s,
                            const double *__restrict__ ps_n, double *__restrict__ ps_out,
                            const double *__restrict__ th_s, typename P::TA *__restrict__ theta,
-                           double *__restrict__ Mv, double dts, double *__restrict__ dpi_out) {
+                           double *__restrict__ Mv, double dts, double *__restrict__ dpi_out,
+                           double *__restrict__ rdps_out) {
     using TM = typename P::TM;
     using TA = typename P::TA;
     const int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -85,6 +129,7 @@ __global__ void k_mass_col(DevMesh m, DyPar d, const typename P::TM *__restrict_
         cw[j] = (TM)cw64[j];
     }
     const double dps = ldg(ps_s + i) - d.pi_top;
+    const double rdps = rcp(dps);
     double col[GRIST_MAXE] = {0, 0, 0, 0, 0, 0};
     double Dk[kMaxChunks];
     const int nch = (d.L + 31) >> 5;
@@ -103,9 +148,8 @@ __global__ void k_mass_col(DevMesh m, DyPar d, const typename P::TM *__restrict_
                 }
                 Dk[ch] = (double)s;
                 const size_t x = (size_t)i * d.ld + k;
-                const double dpk = ldg(d.dB + k) * dps;
-                theta[x] = (TA)(th_s[x] / dpk);
-                if (dpi_out) dpi_out[x] = dpk;
+                theta[x] = (TA)(th_s[x] * ldg(d.rdB + k) * rdps);
+                if (dpi_out) dpi_out[x] = ldg(d.dB + k) * dps;
             }
         }
     }
@@ -114,6 +158,7 @@ __global__ void k_mass_col(DevMesh m, DyPar d, const typename P::TM *__restrict_
     for (int j = 0; j < GRIST_MAXE; j++) pst -= cw64[j] * warp_sum(col[j]);
     if (lane == 0) {
         ps_out[i] = ps_n[i] + dts * pst;
+        rdps_out[i] = rdps;
         Mv[(size_t)i * d.ldi] = 0.0;
         Mv[(size_t)i * d.ldi + d.L] = 0.0;
     }
@@ -190,6 +235,7 @@ __global__ void k_hydro_diag(DevMesh m, DyPar d, const double *__restrict__ ps, 
     const int lane = threadIdx.x & 31;
     if (i >= m.nC) return;
     const double dps = ps[i] - d.pi_top;
+    const double rdps = rcp(dps);
     const int nch = (d.L + 31) >> 5;
     double carry = ldg(d.phis + i);
     for (int ch = nch - 1; ch >= 0; ch--) {
@@ -199,7 +245,7 @@ __global__ void k_hydro_diag(DevMesh m, DyPar d, const double *__restrict__ ps, 
             const double pt = d.pi_top + ldg(d.B + k) * dps, pb = d.pi_top + ldg(d.B + k + 1) * dps;
             const double dp = pb - pt;
             pk = 0.5 * (pt + pb);
-            a = d.rd * (th[(size_t)i * d.ld + k] / dp) * pow(pk / d.p0, d.kappa) / pk;
+            a = d.rd * (th[(size_t)i * d.ld + k] * ldg(d.rdB + k) * rdps) * pow(pk / d.p0, d.kappa) / pk;
             contrib = a * dp;
         }
         // inclusive suffix sum within the chunk
@@ -219,26 +265,33 @@ __global__ void k_hydro_diag(DevMesh m, DyPar d, const double *__restrict__ ps, 
     }
 }
 
+// Column reciprocal of the kite-remapped vertex layer mass:
+// 1 / sum_i kite(i,v)/A_v (ps_i - pi_top); the layer value is dB_k times it.
+__global__ void k_vertex_mass(DevMesh m, DyPar d, const double *__restrict__ ps_s, double *__restrict__ rdpv) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= m.nV) return;
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < 3; j++) s += ldg(m.ckite + v * 3 + j) * (ldg(ps_s + ldg(m.cov + v * 3 + j)) - d.pi_top);
+    rdpv[v] = rcp(s);
+}
+
 // Vertex PV, Sec. 2.3: zeta_p = (zeta + f) / dpi_v, the relative vorticity
 // from the circulation of u (advective type), dpi_v the kite-weighted remap
 // of the FP64 layer mass (dpi must be double for zeta_p).
 template <class P>
 __global__ void k_vort(DevMesh m, DyPar d, LevelDiv Dv, const typename P::TU *__restrict__ u,
-                       const double *__restrict__ ps_s, typename P::TA *__restrict__ qv) {
+                       const double *__restrict__ rdpv, typename P::TA *__restrict__ qv) {
     using TA = typename P::TA;
     uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= (uint32_t)m.nV * (uint32_t)d.L) return;
     int v, k;
     split_index(n, Dv, v, k);
     TA z = 0;
-    double dpv = 0.0;
 #pragma unroll
-    for (int j = 0; j < 3; j++) {
+    for (int j = 0; j < 3; j++)
         z += ldg(Coef<TA>::ccurl(m) + v * 3 + j) * (TA)ldg(u + (size_t)ldg(m.eov + v * 3 + j) * d.ld + k);
-        dpv += ldg(m.ckite + v * 3 + j) * (ldg(ps_s + ldg(m.cov + v * 3 + j)) - d.pi_top);
-    }
-    dpv *= ldg(d.dB + k);
-    qv[(size_t)v * d.ld + k] = (TA)(((double)z + ldg(m.fv + v)) / dpv);
+    qv[(size_t)v * d.ld + k] = (TA)(((double)z + ldg(m.fv + v)) * (ldg(d.rdB + k) * ldg(rdpv + v)));
 }
 
 // Cell kinetic energy K = sum (dc dv / 4A) u^2 (FP64: boxed term of Eq. 5).
@@ -274,12 +327,14 @@ __global__ void k_pv_edge(DevMesh m, DyPar d, LevelDiv Dv, const typename P::TA 
 //   - dK/dn - eta-dot du/deta                              [FP64, boxed]
 //   - alpha_e dp/dn - (dp/dpi)_e dphi/dn                   [FP64]
 // with the tendency rounded to the wind's type (Sec. 2.3: boxed terms are
-// computed in double, their tendency saved in single).
+// computed in double, their tendency saved in single).  The edge layer mass
+// in the vertical advection is dB_k (ps1 + ps2 - 2 pi_top)/2, entered as
+// the product of the per-level and per-edge reciprocals.
 template <class P, bool NH>
 __global__ void k_momentum(DevMesh m, DyPar d, LevelDiv Dv, const typename P::TU *__restrict__ u_s,
                            const typename P::TU *u_n, typename P::TU *u_out, const typename P::TM *__restrict__ F,
                            const typename P::TA *__restrict__ qe, const double *__restrict__ K,
-                           const double *__restrict__ Mv, const double *__restrict__ ps_s,
+                           const double *__restrict__ Mv, const double *__restrict__ rsum_e,
                            const double *__restrict__ p, const double *__restrict__ al,
                            const double *__restrict__ phl, const double *__restrict__ dpp, double dts,
                            uint32_t *status) {
@@ -291,7 +346,6 @@ __global__ void k_momentum(DevMesh m, DyPar d, LevelDiv Dv, const typename P::TU
     split_index(n, Dv, e, k);
     const size_t x = (size_t)e * d.ld + k;
     const int2 c = ldg(m.coe + e);
-    const double rdc = ldg(m.rdc + e);
     const TA qee = ldg(qe + x);
     TA pv = 0;
 #pragma unroll
@@ -301,23 +355,22 @@ __global__ void k_momentum(DevMesh m, DyPar d, LevelDiv Dv, const typename P::TU
         pv += ldg(Coef<TA>::wpv(m) + e * 10 + j) * (TA)ldg(F + y) * ((TA)0.5 * (qee + ldg(qe + y)));
     }
     const size_t a1 = (size_t)c.x * d.ld + k, a2 = (size_t)c.y * d.ld + k;
-    const double ke = (ldg(K + a2) - ldg(K + a1)) * rdc;
-    const double dpe = 0.5 * ldg(d.dB + k) * ((ldg(ps_s + c.x) - d.pi_top) + (ldg(ps_s + c.y) - d.pi_top));
     const double uk = (double)ldg(u_s + x);
     double va = 0.0;
-    if (k < d.L - 1) {
-        const double Mb = 0.5 * (ldg(Mv + (size_t)c.x * d.ldi + k + 1) + ldg(Mv + (size_t)c.y * d.ldi + k + 1));
-        va += Mb * ((double)ldg(u_s + x + 1) - uk);
-    }
-    if (k > 0) {
-        const double Mt = 0.5 * (ldg(Mv + (size_t)c.x * d.ldi + k) + ldg(Mv + (size_t)c.y * d.ldi + k));
-        va += Mt * (uk - (double)ldg(u_s + x - 1));
-    }
-    va /= 2.0 * dpe;
-    const double ae = 0.5 * (ldg(al + a1) + ldg(al + a2));
-    const double de = NH ? 0.5 * (ldg(dpp + a1) + ldg(dpp + a2)) : 1.0;
-    const double pgf = -ae * (ldg(p + a2) - ldg(p + a1)) * rdc - de * (ldg(phl + a2) - ldg(phl + a1)) * rdc;
-    const TA tend = pv + (TA)(pgf - ke - va);
+    if (k < d.L - 1)
+        va = (ldg(Mv + (size_t)c.x * d.ldi + k + 1) + ldg(Mv + (size_t)c.y * d.ldi + k + 1)) *
+             ((double)ldg(u_s + x + 1) - uk);
+    if (k > 0)
+        va = fma(ldg(Mv + (size_t)c.x * d.ldi + k) + ldg(Mv + (size_t)c.y * d.ldi + k), uk - (double)ldg(u_s + x - 1),
+                 va);
+    // [M sums](du) / (2 dpi_e) with dpi_e = dB (sum)/2 and M_e = (M1 + M2)/2
+    va *= 0.5 * ldg(d.rdB + k) * ldg(rsum_e + e);
+    const double de = NH ? ldg(dpp + a1) + ldg(dpp + a2) : 2.0;
+    // dK/dn + alpha_e dp/dn + (dp/dpi)_e dphi/dn, the two means folded into 1/2
+    const double grad = fma(ldg(al + a1) + ldg(al + a2), ldg(p + a2) - ldg(p + a1),
+                            fma(de, ldg(phl + a2) - ldg(phl + a1), 2.0 * (ldg(K + a2) - ldg(K + a1))));
+    const double slow = -0.5 * ldg(m.rdc + e) * grad - va;
+    const TA tend = pv + (TA)slow;
     const TU v = (TU)((TA)u_n[x] + (TA)dts * tend);
     if (!isfinite((double)v)) atomicOr(status, GRIST_FLAG_NONFINITE);
     u_out[x] = v;
@@ -326,7 +379,8 @@ __global__ void k_momentum(DevMesh m, DyPar d, LevelDiv Dv, const typename P::TU
 // ---------------------------------------------------------------------------
 // Non-hydrostatic pieces (Eqs. 6, 7, 9)
 
-// Eq. 9 at time level n: p = p0 (Rd dpi_theta / (p0 dphi))^gamma.
+// Eq. 9 at time level n: p = p0 (Rd dpi_theta / (p0 dphi))^gamma, as
+// p0 exp(gamma log(.)).
 __global__ void k_eos(DevMesh m, DyPar d, LevelDiv Dv, const double *__restrict__ th, const double *__restrict__ phi,
                       double *__restrict__ p) {
     uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
@@ -334,21 +388,23 @@ __global__ void k_eos(DevMesh m, DyPar d, LevelDiv Dv, const double *__restrict_
     int i, k;
     split_index(n, Dv, i, k);
     const double dphi = phi[(size_t)i * d.ldi + k] - phi[(size_t)i * d.ldi + k + 1];
-    p[(size_t)i * d.ld + k] = d.p0 * pow(d.rd * th[(size_t)i * d.ld + k] / (d.p0 * dphi), d.gamma);
+    p[(size_t)i * d.ld + k] = d.p0 * exp(d.gamma * log(d.rd * th[(size_t)i * d.ld + k] / (d.p0 * dphi)));
 }
 
 // Explicit parts of Eqs. 6-7 at every interface: horizontal advection
 // V.grad(x) = (1/A) sum s dv u^int (x_nb - x)/2 and vertical advection
 // M (x_{j+1} - x_{j-1}) / (dpi_{j-1} + dpi_j) of w and phi from the stage
 // input (advective type; differences of the FP64 fields taken in FP64
-// first), plus the (1 - beta) share of g (dp/dpi - 1) and g w at t^n.
-template <class P>
+// first), plus the (1 - beta) share of g (dp/dpi - 1) and g w at t^n.  The
+// t^n forcing g (dp/dpi - 1) is formed in the first stage (FIRST) from the
+// t^n pressure and kept for the later stages.
+template <class P, bool FIRST>
 __global__ void k_nh_explicit(DevMesh m, DyPar d, LevelDiv Dv, const typename P::TU *__restrict__ u_s,
-                              const double *__restrict__ ps_s, const double *__restrict__ ps_n,
-                              const double *__restrict__ Mv, const double *__restrict__ w_s,
-                              const double *__restrict__ phi_s, const double *__restrict__ w_n,
-                              const double *__restrict__ phi_n, const double *__restrict__ p_n,
-                              double *__restrict__ wst, double *__restrict__ phst, double dts) {
+                              const double *__restrict__ rdps_s, const double *__restrict__ Mv,
+                              const double *__restrict__ w_s, const double *__restrict__ phi_s,
+                              const double *__restrict__ w_n, const double *__restrict__ phi_n,
+                              const double *__restrict__ p_n, double *__restrict__ fw_n, double *__restrict__ wst,
+                              double *__restrict__ phst, double dts) {
     using TA = typename P::TA;
     uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
     const int Li = d.L + 1;
@@ -379,85 +435,110 @@ __global__ void k_nh_explicit(DevMesh m, DyPar d, LevelDiv Dv, const typename P:
     TA vw = 0, vp = 0;
     double fw = 0.0;
     if (j > 0) {
-        const double dps = ldg(ps_s + i) - d.pi_top;
-        const TA r = (TA)(Mv[(size_t)i * d.ldi + j] / ((ldg(d.dB + j - 1) + ldg(d.dB + j)) * dps));
+        const double rd2 = 0.5 * ldg(d.rdBi + j) * ldg(rdps_s + i);   // 1/(dpi_{j-1} + dpi_j)
+        const TA r = (TA)(Mv[(size_t)i * d.ldi + j] * rd2);
         vw = r * (TA)(w_s[xi + 1] - w_s[xi - 1]);
         vp = r * (TA)(phi_s[xi + 1] - phi_s[xi - 1]);
-        const double dpn = 0.5 * (ldg(d.dB + j - 1) + ldg(d.dB + j)) * (ldg(ps_n + i) - d.pi_top);
-        fw = d.g * ((p_n[(size_t)i * d.ld + j] - p_n[(size_t)i * d.ld + j - 1]) / dpn - 1.0);
+        if (FIRST) {
+            // first stage: the stage input is t^n, so rdps_s is 1/(ps^n - pi_top)
+            fw = d.g * fma(p_n[(size_t)i * d.ld + j] - p_n[(size_t)i * d.ld + j - 1], 2.0 * rd2, -1.0);
+            fw_n[xi] = fw;
+        } else {
+            fw = fw_n[xi];
+        }
     }
     wst[xi] = w_n[xi] + dts * ((double)(-hw - vw) + (1.0 - d.beta) * fw);
     phst[xi] = phi_n[xi] + dts * ((double)(-hp - vp) + (1.0 - d.beta) * d.g * w_n[xi]);
 }
 
-// Implicit part of Eqs. 6-7 and Eq. 9, one thread per column, FP64:
-// linearised EOS about phi**, p_k = p**_k - C_k (w_k - w_{k+1}),
+// Implicit part of Eqs. 6-7 and Eq. 9, one thread per column, FP64.
+// Equation of state relative to the stage-input state (th_r, phi_r, p_r):
+//   p** = p_r ((th dphi_r) / (th_r dphi**))^gamma     (pow_near1)
+// linearised about phi**: p_k = p**_k - C_k (w_k - w_{k+1}),
 // C_k = gamma p**_k beta dt g / dphi**_k; tridiagonal rows for interior
 // interfaces j = 1..L-1 (w = 0 at top and ground) solved by the Thomas
-// algorithm; phi = phi** + beta dt g w; full EOS for p; then the
-// momentum-side diagnostics alpha = dphi/dpi, layer phi, dp/dpi averaged
-// to layers (interface value 1 at top and bottom).
-__global__ void k_nh_solve(DevMesh m, DyPar d, const double *__restrict__ wst, const double *__restrict__ phst,
-                           const double *__restrict__ th, const double *__restrict__ ps, double dts,
-                           double *__restrict__ w_out, double *__restrict__ phi_out, double *__restrict__ p,
-                           double *__restrict__ al, double *__restrict__ phl, double *__restrict__ dpp) {
+// algorithm; phi = phi** + beta dt g w; the full EOS then gives
+//   p = p** (dphi / dphi**)^(-gamma),  dphi = dphi** + beta dt g (w_k - w_{k+1});
+// finally alpha = dphi/dpi, layer phi and dp/dpi averaged to layers
+// (interface value 1 at top and bottom) for the momentum equation.
+__global__ void __launch_bounds__(128) k_nh_solve(DevMesh m, DyPar d, const double *__restrict__ wst,
+                                                  const double *__restrict__ phst, const double *__restrict__ th,
+                                                  const double *__restrict__ th_r, const double *__restrict__ phi_r,
+                                                  const double *p_r, const double *__restrict__ ps, double dts,
+                                                  double *__restrict__ w_out, double *__restrict__ phi_out, double *p,
+                                                  double *__restrict__ al, double *__restrict__ phl,
+                                                  double *__restrict__ dpp) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m.nC) return;
     const int L = d.L;
     const size_t ci = (size_t)i * d.ldi, cl = (size_t)i * d.ld;
     const double bg = d.beta * dts * d.g;
-    const double dps = ps[i] - d.pi_top;
-    double cp[kNHMax], dd[kNHMax];
+    const double gbg = d.gamma * bg;
+    const double rdps = rcp(ps[i] - d.pi_top);
+    double cp[kNHMax], dd[kNHMax], pst[kNHMax], rdf[kNHMax];
     // forward sweep; p** and C of layers j-1 and j are rolled along
-    double dphi0 = phst[ci] - phst[ci + 1];
-    double pst_prev = d.p0 * pow(d.rd * th[cl] / (d.p0 * dphi0), d.gamma);
-    double C_prev = d.gamma * pst_prev * bg / dphi0;
+    double ftop = phst[ci], fbot = phst[ci + 1];
+    double rtop = phi_r[ci], rbot = phi_r[ci + 1];
+    double rdf0 = rcp(ftop - fbot);
+    double p0s = p_r[cl] * pow_near1(th[cl] * rcp(th_r[cl]) * ((rtop - rbot) * rdf0), d.gamma);
+    pst[0] = p0s;
+    rdf[0] = rdf0;
+    double pst_prev = p0s, C_prev = gbg * p0s * rdf0;
     for (int j = 1; j < L; j++) {
-        const double dphi = phst[ci + j] - phst[ci + j + 1];
-        const double pst = d.p0 * pow(d.rd * th[cl + j] / (d.p0 * dphi), d.gamma);
-        const double C = d.gamma * pst * bg / dphi;
-        const double aj = bg / (0.5 * (ldg(d.dB + j - 1) + ldg(d.dB + j)) * dps);
+        ftop = fbot;
+        fbot = phst[ci + j + 1];
+        rtop = rbot;
+        rbot = phi_r[ci + j + 1];
+        const double rdfj = rcp(ftop - fbot);
+        const double pstj = p_r[cl + j] * pow_near1(th[cl + j] * rcp(th_r[cl + j]) * ((rtop - rbot) * rdfj), d.gamma);
+        pst[j] = pstj;
+        rdf[j] = rdfj;
+        const double C = gbg * pstj * rdfj;
+        const double aj = bg * ldg(d.rdBi + j) * rdps;
         const double a = (j == 1) ? 0.0 : -aj * C_prev;
         const double c = (j == L - 1) ? 0.0 : -aj * C;
-        const double b = 1.0 + aj * C_prev + aj * C;
-        const double rhs = wst[ci + j] + aj * (pst - pst_prev) - bg;
+        const double b = fma(aj, C_prev + C, 1.0);
+        const double rhs = wst[ci + j] + fma(aj, pstj - pst_prev, -bg);
         const int r = j - 1;
         if (r == 0) {
-            cp[0] = c / b;
-            dd[0] = rhs / b;
+            const double rb = rcp(b);
+            cp[0] = c * rb;
+            dd[0] = rhs * rb;
         } else {
-            const double den = b - a * cp[r - 1];
-            cp[r] = c / den;
-            dd[r] = (rhs - a * dd[r - 1]) / den;
+            const double rden = rcp(fma(-a, cp[r - 1], b));
+            cp[r] = c * rden;
+            dd[r] = fma(-a, dd[r - 1], rhs) * rden;
         }
-        pst_prev = pst;
+        pst_prev = pstj;
         C_prev = C;
     }
+    // back substitution into w (interfaces 1..L-1), w = 0 at 0 and L
     w_out[ci] = 0.0;
     w_out[ci + L] = 0.0;
     double wn = 0.0;
     for (int r = L - 2; r >= 0; r--) {
-        wn = dd[r] - cp[r] * wn;
+        wn = fma(-cp[r], wn, dd[r]);
         w_out[ci + r + 1] = wn;
     }
-    // phi, EOS and momentum diagnostics
-    phi_out[ci] = phst[ci];
-    for (int j = 1; j < L; j++) phi_out[ci + j] = phst[ci + j] + bg * w_out[ci + j];
-    phi_out[ci + L] = ldg(d.phis + i);
-    double p_prev = 0.0, dpdpi_top = 1.0;
+    // phi, EOS and momentum diagnostics, top to bottom
+    double w_top = 0.0, phi_top = phst[ci], p_prev = 0.0, dpdpi_top = 1.0;
+    phi_out[ci] = phi_top;
     for (int k = 0; k < L; k++) {
-        const double dphi = phi_out[ci + k] - phi_out[ci + k + 1];
-        const double dpk = ldg(d.dB + k) * dps;
-        const double pk = d.p0 * pow(d.rd * th[cl + k] / (d.p0 * dphi), d.gamma);
+        const double w_bot = (k + 1 < L) ? w_out[ci + k + 1] : 0.0;
+        const double phi_bot = (k + 1 < L) ? fma(bg, w_bot, phst[ci + k + 1]) : ldg(d.phis + i);
+        phi_out[ci + k + 1] = phi_bot;
+        const double pk = pst[k] * pow_near1(fma(bg * (w_top - w_bot), rdf[k], 1.0), -d.gamma);
         p[cl + k] = pk;
-        al[cl + k] = dphi / dpk;
-        phl[cl + k] = 0.5 * (phi_out[ci + k] + phi_out[ci + k + 1]);
+        al[cl + k] = (phi_top - phi_bot) * (ldg(d.rdB + k) * rdps);
+        phl[cl + k] = 0.5 * (phi_top + phi_bot);
         if (k > 0) {
-            const double dint = (pk - p_prev) / (0.5 * (ldg(d.dB + k - 1) + ldg(d.dB + k)) * dps);
+            const double dint = (pk - p_prev) * (ldg(d.rdBi + k) * rdps);
             dpp[cl + k - 1] = 0.5 * (dpdpi_top + dint);
             dpdpi_top = dint;
         }
         p_prev = pk;
+        w_top = w_bot;
+        phi_top = phi_bot;
     }
     dpp[cl + L - 1] = 0.5 * (dpdpi_top + 1.0);
 }
@@ -479,26 +560,33 @@ int dycore_step(grist_mesh_s *h, grist_dycore_state *S, const grist_dycore_param
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off += al(bytes); return o; };
-    const size_t o_vg = take(sizeof(double) * (2 * L + 1));
+    const size_t nvg = 4 * (size_t)L + 2;
+    const size_t o_vg = take(sizeof(double) * nvg);
     const size_t o_uA = take(nEL * sizeof(TU)), o_uB = take(nEL * sizeof(TU));
     const size_t o_psA = take(m.nC * 8), o_psB = take(m.nC * 8), o_psN = take(m.nC * 8);
+    const size_t o_rdps = take(m.nC * 8), o_rsum = take(m.nE * 8), o_rdpv = take(m.nV * 8);
     const size_t o_thA = take(nCL * 8), o_thB = take(nCL * 8);
     const size_t o_F = take(nEL * sizeof(TM)), o_M = take(nCI * 8);
     const size_t o_theta = take(nCL * sizeof(TA)), o_Fth = take(nEL * sizeof(TA));
     const size_t o_p = take(nCL * 8), o_al = take(nCL * 8), o_phl = take(nCL * 8), o_dpp = take(nCL * 8);
     const size_t o_qv = take(nVL * sizeof(TA)), o_qe = take(nEL * sizeof(TA)), o_K = take(nCL * 8);
-    size_t o_wA = 0, o_wB = 0, o_phA = 0, o_phB = 0, o_wst = 0, o_phst = 0, o_pn = 0;
+    size_t o_wA = 0, o_wB = 0, o_phA = 0, o_phB = 0, o_wst = 0, o_phst = 0, o_pn = 0, o_fw = 0;
     if (NH) {
         o_wA = take(nCI * 8); o_wB = take(nCI * 8); o_phA = take(nCI * 8); o_phB = take(nCI * 8);
-        o_wst = take(nCI * 8); o_phst = take(nCI * 8); o_pn = take(nCL * 8);
+        o_wst = take(nCI * 8); o_phst = take(nCI * 8); o_pn = take(nCL * 8); o_fw = take(nCI * 8);
     }
     char *s = (char *)scratch(h, 1, off);
     if (!s) return GRIST_ENOMEM;
 
-    // vertical grid: B at interfaces and dB per layer (copied on the stream)
-    std::vector<double> vg(2 * L + 1);
-    for (int k = 0; k <= L; k++) vg[k] = prm->b_interface[k];
-    for (int k = 0; k < L; k++) vg[L + 1 + k] = prm->b_interface[k + 1] - prm->b_interface[k];
+    // vertical grid: B (L+1) | dB (L) | 1/dB (L) | 2/(dB[j-1]+dB[j]) (L+1)
+    std::vector<double> vg(nvg, 0.0);
+    double *hB = vg.data(), *hdB = hB + L + 1, *hrdB = hdB + L, *hrdBi = hrdB + L;
+    for (int k = 0; k <= L; k++) hB[k] = prm->b_interface[k];
+    for (int k = 0; k < L; k++) {
+        hdB[k] = prm->b_interface[k + 1] - prm->b_interface[k];
+        hrdB[k] = 1.0 / hdB[k];
+    }
+    for (int j = 1; j < L; j++) hrdBi[j] = 2.0 / (hdB[j - 1] + hdB[j]);
     double *dvg = (double *)(s + o_vg);
     GRIST_CUDA_TRY(cudaMemcpyAsync(dvg, vg.data(), vg.size() * sizeof(double), cudaMemcpyHostToDevice, st));
     GRIST_CUDA_TRY(cudaStreamSynchronize(st));  // vg is a host temporary
@@ -507,10 +595,11 @@ int dycore_step(grist_mesh_s *h, grist_dycore_state *S, const grist_dycore_param
     d.L = L; d.ld = ld; d.ldi = ldi;
     d.pi_top = prm->pi_top; d.p0 = prm->p0; d.rd = prm->rd; d.cp = prm->cp; d.g = prm->g;
     d.beta = prm->offcentre_beta; d.kappa = prm->rd / prm->cp; d.gamma = prm->cp / (prm->cp - prm->rd);
-    d.B = dvg; d.dB = dvg + L + 1; d.phis = prm->phi_surface;
+    d.B = dvg; d.dB = dvg + L + 1; d.rdB = dvg + 2 * L + 1; d.rdBi = dvg + 3 * L + 1; d.phis = prm->phi_surface;
 
     TU *uA = (TU *)(s + o_uA), *uB = (TU *)(s + o_uB);
     double *psA = (double *)(s + o_psA), *psB = (double *)(s + o_psB), *psN = (double *)(s + o_psN);
+    double *rdps = (double *)(s + o_rdps), *rsum = (double *)(s + o_rsum), *rdpv = (double *)(s + o_rdpv);
     double *thA = (double *)(s + o_thA), *thB = (double *)(s + o_thB);
     TM *F = (TM *)(s + o_F);
     double *Mv = (double *)(s + o_M);
@@ -521,18 +610,19 @@ int dycore_step(grist_mesh_s *h, grist_dycore_state *S, const grist_dycore_param
     double *K = (double *)(s + o_K);
     double *wA = (double *)(s + o_wA), *wB = (double *)(s + o_wB), *phA = (double *)(s + o_phA),
            *phB = (double *)(s + o_phB), *wst = (double *)(s + o_wst), *phst = (double *)(s + o_phst),
-           *pn = (double *)(s + o_pn);
+           *pn = (double *)(s + o_pn), *fwn = (double *)(s + o_fw);
 
     TU *u = (TU *)S->u;
     uint32_t *status = status_word(h);
     const LevelDiv DL = make_div((uint32_t)L), DI = make_div((uint32_t)(L + 1));
     const unsigned gC = grid_for((long long)m.nC * L, kBlock), gE = grid_for((long long)m.nE * L, kBlock),
                    gV = grid_for((long long)m.nV * L, kBlock), gW = grid_for((long long)m.nC * 32, kBlock),
-                   gI = grid_for((long long)m.nC * (L + 1), kBlock), gCol = grid_for(m.nC, 128);
+                   gI = grid_for((long long)m.nC * (L + 1), kBlock), gCol = grid_for(m.nC, 128),
+                   gVx = grid_for(m.nV, kBlock);
     const double dts[3] = {dt / 3.0, dt / 2.0, dt};
 
     GRIST_CUDA_TRY(cudaMemcpyAsync(psN, S->ps, m.nC * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    if (NH) k_eos<<<gC, kBlock, 0, st>>>(m, d, DL, S->dpi_theta, S->phi, pn);
+    if (NH) GRIST_LAUNCH(h, PN("k_eos"), st, k_eos<<<gC, kBlock, 0, st>>>(m, d, DL, S->dpi_theta, S->phi, pn));
 
     const TU *u_in = u;
     const double *ps_in = psN, *th_in = S->dpi_theta, *w_in = S->w, *phi_in = S->phi;
@@ -543,31 +633,40 @@ int dycore_step(grist_mesh_s *h, grist_dycore_state *S, const grist_dycore_param
     double *phi_outs[3] = {phA, phB, S->phi};
     for (int s3 = 0; s3 < 3; s3++) {
         const double h3 = dts[s3];
-        GRIST_LAUNCH(h, PN("k_mass_edge"), st, k_mass_edge<P><<<gE, kBlock, 0, st>>>(m, d, DL, ps_in, u_in, F, s3 == 2 ? S->mass_flux_accum : nullptr));
-        GRIST_LAUNCH(h, PN("k_mass_col"), st, k_mass_col<P><<<gW, kBlock, 0, st>>>(m, d, F, ps_in, psN, ps_outs[s3], th_in, theta, Mv, h3,
-                                                  s3 == 0 ? S->dpi_start : nullptr));
+        GRIST_LAUNCH(h, PN("k_mass_edge"), st, k_mass_edge<P><<<gE, kBlock, 0, st>>>(
+            m, d, DL, ps_in, u_in, F, s3 == 2 ? S->mass_flux_accum : nullptr, rsum));
+        GRIST_LAUNCH(h, PN("k_mass_col"), st, k_mass_col<P><<<gW, kBlock, 0, st>>>(
+            m, d, F, ps_in, psN, ps_outs[s3], th_in, theta, Mv, h3, s3 == 0 ? S->dpi_start : nullptr, rdps));
         GRIST_LAUNCH(h, PN("k_theta_flux"), st, k_theta_flux<P><<<gE, kBlock, 0, st>>>(m, d, DL, F, theta, Fth));
-        GRIST_LAUNCH(h, PN("k_theta_update"), st, k_theta_update<P><<<gC, kBlock, 0, st>>>(m, d, DL, Fth, theta, Mv, S->dpi_theta, th_outs[s3], h3));
+        GRIST_LAUNCH(h, PN("k_theta_update"), st, k_theta_update<P><<<gC, kBlock, 0, st>>>(
+            m, d, DL, Fth, theta, Mv, S->dpi_theta, th_outs[s3], h3));
         if (NH) {
-            GRIST_LAUNCH(h, PN("k_nh_explicit"), st, k_nh_explicit<P><<<gI, kBlock, 0, st>>>(m, d, DI, u_in, ps_in, psN, Mv, w_in, phi_in, S->w, S->phi, pn,
-                                                    wst, phst, h3));
-            GRIST_LAUNCH(h, PN("k_nh_solve"), st, k_nh_solve<<<gCol, 128, 0, st>>>(m, d, wst, phst, th_outs[s3], ps_outs[s3], h3, w_outs[s3],
-                                            phi_outs[s3], p, alp, phl, dpp));
+            if (s3 == 0)
+                GRIST_LAUNCH(h, PN("k_nh_explicit"), st, k_nh_explicit<P, true><<<gI, kBlock, 0, st>>>(
+                    m, d, DI, u_in, rdps, Mv, w_in, phi_in, S->w, S->phi, pn, fwn, wst, phst, h3));
+            else
+                GRIST_LAUNCH(h, PN("k_nh_explicit"), st, k_nh_explicit<P, false><<<gI, kBlock, 0, st>>>(
+                    m, d, DI, u_in, rdps, Mv, w_in, phi_in, S->w, S->phi, pn, fwn, wst, phst, h3));
+            GRIST_LAUNCH(h, PN("k_nh_solve"), st, k_nh_solve<<<gCol, 128, 0, st>>>(
+                m, d, wst, phst, th_outs[s3], th_in, phi_in, s3 == 0 ? pn : p, ps_outs[s3], h3, w_outs[s3],
+                phi_outs[s3], p, alp, phl, dpp));
         } else {
-            GRIST_LAUNCH(h, PN("k_hydro_diag"), st, k_hydro_diag<<<gW, kBlock, 0, st>>>(m, d, ps_outs[s3], th_outs[s3], p, alp, phl));
+            GRIST_LAUNCH(h, PN("k_hydro_diag"), st, k_hydro_diag<<<gW, kBlock, 0, st>>>(
+                m, d, ps_outs[s3], th_outs[s3], p, alp, phl));
         }
-        GRIST_LAUNCH(h, PN("k_vort"), st, k_vort<P><<<gV, kBlock, 0, st>>>(m, d, DL, u_in, ps_in, qv));
+        GRIST_LAUNCH(h, PN("k_vertex_mass"), st, k_vertex_mass<<<gVx, kBlock, 0, st>>>(m, d, ps_in, rdpv));
+        GRIST_LAUNCH(h, PN("k_vort"), st, k_vort<P><<<gV, kBlock, 0, st>>>(m, d, DL, u_in, rdpv, qv));
         GRIST_LAUNCH(h, PN("k_ke"), st, k_ke<P><<<gC, kBlock, 0, st>>>(m, d, DL, u_in, K));
         GRIST_LAUNCH(h, PN("k_pv_edge"), st, k_pv_edge<P><<<gE, kBlock, 0, st>>>(m, d, DL, qv, qe));
-        GRIST_LAUNCH(h, PN("k_momentum"), st, k_momentum<P, NH><<<gE, kBlock, 0, st>>>(m, d, DL, u_in, u, u_outs[s3], F, qe, K, Mv, ps_in, p, alp, phl,
-                                                 dpp, h3, status));
+        GRIST_LAUNCH(h, PN("k_momentum"), st, k_momentum<P, NH><<<gE, kBlock, 0, st>>>(
+            m, d, DL, u_in, u, u_outs[s3], F, qe, K, Mv, rsum, p, alp, phl, dpp, h3, status));
         u_in = u_outs[s3];
         ps_in = ps_outs[s3];
         th_in = th_outs[s3];
         w_in = w_outs[s3];
         phi_in = phi_outs[s3];
     }
-    if (S->accum_weight) k_add_scalar<<<1, 32, 0, st>>>(S->accum_weight, 1.0);
+    if (S->accum_weight) GRIST_LAUNCH(h, PN("k_add_scalar"), st, k_add_scalar<<<1, 32, 0, st>>>(S->accum_weight, 1.0));
     return cudaGetLastError() == cudaSuccess ? GRIST_OK : GRIST_ECUDA;
 }
 
