@@ -258,6 +258,35 @@ int grist_profile_read(grist_mesh mesh, int32_t max_entries, char *names, int32_
                        int32_t *n_entries);
 
 /* ---------------------------------------------------------------------- */
+/* Allocation-free weighted sum (no counterpart in the paper)              */
+/* ---------------------------------------------------------------------- */
+
+/* Upper bound on n for grist_weighted_sum_noalloc, and the number of terms
+ * one block of its kernel sums. */
+#define GRIST_NOALLOC_CHUNK 65536
+#define GRIST_NOALLOC_MAX_TERMS (4096 * 65536)
+
+/* sum_i w[i] * x[i] (w NULL: sum_i x[i]) over n device doubles, with the
+ * same compensated, fixed-order summation as grist_global_sums, without
+ * allocating any memory.  For callers that cannot allocate device memory:
+ * programs whose device memory is owned by another allocator that reserves
+ * it up front, and code that must not pay the device-wide synchronisation a
+ * cudaMalloc / cudaFree can imply.  No mesh handle is needed.
+ *   x, w             device, in, n doubles (w may be NULL).
+ *   n                0 <= n <= GRIST_NOALLOC_MAX_TERMS, else GRIST_EINVAL
+ *                    (checked before anything is launched).
+ *   out_sum_and_err  device, out, 2 doubles = {sum, compensation term},
+ *                    written on `stream`; the call does not wait.
+ * Partial sums live in one fixed device array per device (about 64 KB,
+ * kept until the process exits) that every call shares: calls whose GPU
+ * work overlaps race on it, so serialise them.  Each call writes every
+ * partial it reads, so nothing needs clearing between calls.  The first
+ * call on a device looks up the array's address with that device current;
+ * make that first call before any stream capture.  Uses the current device
+ * (cudaSetDevice). */
+int grist_weighted_sum_noalloc(const double *x, const double *w, int64_t n, double *out_sum_and_err, void *stream);
+
+/* ---------------------------------------------------------------------- */
 /* Status                                                                  */
 /* ---------------------------------------------------------------------- */
 

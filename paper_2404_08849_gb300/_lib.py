@@ -63,6 +63,7 @@ EXPORTS = {
     "grist_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "grist_profile_enable": ([_V, ctypes.c_int], ctypes.c_int),
     "grist_profile_read": ([_V, _I, ctypes.c_char_p, _P(_I), _P(_D), _P(_I)], ctypes.c_int),
+    "grist_weighted_sum_noalloc": ([_V, _V, ctypes.c_int64, _V, _V], ctypes.c_int),
 }
 
 _lib = None
