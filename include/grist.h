@@ -162,9 +162,45 @@ typedef struct {
 
 /* Advance every member by dt with Wicker-Skamarock RK3 (dt/3, dt/2, dt),
  * the third-order upwind flux each stage and, if limiter, the Zalesak FCT
- * on the final stage.  Asynchronous on `stream`.  GRIST_EINVAL on bad
- * sizes or NULL pointers. */
+ * on the final stage.  All members advance together: each phase of the
+ * step is one pass over a work list of (member, tracer group, entity,
+ * level), either as one kernel launch per phase or as one persistent
+ * cooperative launch per step (see grist_tracer_tuning).  At most
+ * GRIST_MAX_MEMBERS members.  Asynchronous on `stream`.  GRIST_EINVAL on
+ * bad sizes or NULL pointers; a persistent launch whose bounded grid
+ * barrier gave up raises GRIST_FLAG_TIMEOUT (grist_last_step_status). */
+#define GRIST_MAX_MEMBERS 64
 int grist_tracer_step(grist_mesh mesh, const grist_tracer_batch *batch, double dt, void *stream);
+
+/* Launch configuration of the tracer step (the batching design of this
+ * library; no counterpart in the paper).
+ *   block               threads per block (64..1024, multiple of 32)
+ *   tracers_per_thread  tracers one thread carries through a phase (>= 1)
+ *   persistent          0 = one launch per phase; 1 = one cooperative
+ *                       persistent launch per step with grid barriers
+ *   use_graph           1 = capture the step's launches in a CUDA graph on
+ *                       the first call with a given batch (same buffers,
+ *                       sizes, dt, precision, limiter, beta) and replay it
+ *                       afterwards; the first call must not itself be
+ *                       inside a stream capture. */
+typedef struct {
+    int32_t block, tracers_per_thread, persistent, use_graph;
+} grist_tracer_tuning;
+
+/* Set / get the tuning used by later grist_tracer_step calls on the mesh
+ * (default: block 256, tracers_per_thread 4, persistent 0, use_graph 0).
+ * GRIST_EINVAL for out-of-range values. */
+int grist_tracer_set_tuning(grist_mesh mesh, const grist_tracer_tuning *tuning);
+int grist_tracer_get_tuning(grist_mesh mesh, grist_tracer_tuning *tuning);
+
+/* Autotuner: time candidate tunings (block sizes, tracers per thread,
+ * per-phase vs persistent launch, graph on/off) on `steps` tracer steps of
+ * the given batch, keep the fastest as the mesh's tuning and return it in
+ * *best (and its mean step time in milliseconds in *best_ms, may be NULL).
+ * Works on private copies of the tracer arrays (allocates them), so the
+ * caller's q is unchanged; synchronises `stream`. */
+int grist_tracer_autotune(grist_mesh mesh, const grist_tracer_batch *batch, double dt, int32_t steps, void *stream,
+                          grist_tracer_tuning *best, double *best_ms);
 
 /* ---------------------------------------------------------------------- */
 /* Dycore (Eqs. 3-9; Sec. 2.1, Sec. 2.3)                                   */
@@ -292,6 +328,14 @@ int grist_weighted_sum_noalloc(const double *x, const double *w, int64_t n, doub
 
 #define GRIST_FLAG_NONFINITE 0x1u  /* a step wrote NaN or Inf */
 #define GRIST_FLAG_TIMEOUT 0x2u    /* a bounded device wait gave up */
+
+/* Diagnostic: launch one thread that waits, with at most spin_limit polls
+ * (about 64 ns apart; 1 <= spin_limit <= 1e8), for a device word that
+ * nothing writes - the same bounded wait the persistent tracer launch uses
+ * at its grid barriers.  The kernel always ends; afterwards
+ * grist_last_step_status reports GRIST_FLAG_TIMEOUT and the context stays
+ * usable.  Asynchronous on `stream`.  No counterpart in the paper. */
+int grist_selftest_bounded_wait(grist_mesh mesh, int64_t spin_limit, void *stream);
 
 /* Flags raised by the steps since the previous call (read after the stream
  * has been synchronised; synchronises the device and clears the flags). */

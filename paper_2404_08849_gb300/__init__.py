@@ -115,11 +115,8 @@ class Mesh:
         return np.ascontiguousarray(np.take(np.asarray(a), self._new(kind), axis=axis))
 
     # ---- steps ---------------------------------------------------------------
-    def tracer_step(self, members, dt, prec="fp64", limiter=True, beta=1.0, stream=None):
-        """members: list of dicts with torch CUDA tensors q [T][nC][ld]
-        (float64 for fp64, float32 for the mixed policies), dpi [nC][ld]
-        and mass_flux [nE][ld] (float64), and int n_levels."""
-        lib = _lib.load()
+    @staticmethod
+    def _batch(members, prec, limiter, beta):
         arr = (_lib.TracerMember * max(1, len(members)))()
         for i, mb in enumerate(members):
             q = mb["q"]
@@ -135,8 +132,62 @@ class Mesh:
         b.prec = _prec(prec)
         b.limiter = 1 if limiter else 0
         b.beta_upwind = float(beta)
+        return b, arr
+
+    def tracer_step(self, members, dt, prec="fp64", limiter=True, beta=1.0, stream=None):
+        """members: list of dicts with torch CUDA tensors q [T][nC][ld]
+        (float64 for fp64, float32 for the mixed policies), dpi [nC][ld]
+        and mass_flux [nE][ld] (float64), and int n_levels."""
+        lib = _lib.load()
+        b, keep = self._batch(members, prec, limiter, beta)
         _lib.check("grist_tracer_step", lib.grist_tracer_step(self.handle, ctypes.byref(b), float(dt),
                                                               _stream_handle(stream)))
+
+    def set_tracer_tuning(self, block=256, tracers_per_thread=4, persistent=False, use_graph=False):
+        t = _lib.TracerTuning(int(block), int(tracers_per_thread), int(bool(persistent)), int(bool(use_graph)))
+        _lib.check("grist_tracer_set_tuning", _lib.load().grist_tracer_set_tuning(self.handle, ctypes.byref(t)))
+
+    def tracer_tuning(self):
+        t = _lib.TracerTuning()
+        _lib.check("grist_tracer_get_tuning", _lib.load().grist_tracer_get_tuning(self.handle, ctypes.byref(t)))
+        return {"block": t.block, "tracers_per_thread": t.tracers_per_thread, "persistent": bool(t.persistent),
+                "use_graph": bool(t.use_graph)}
+
+    def autotune_tracer(self, members, dt, prec="mix", limiter=True, beta=1.0, steps=3, stream=None,
+                        cache_path=None, cache_key=None):
+        """Run the library's autotuner on this batch (or reuse the choice
+        stored in the JSON file cache_path under cache_key) and make it the
+        mesh's tracer tuning.  Returns (tuning dict, ms per step or None)."""
+        import json
+        import os
+        if cache_path and cache_key and os.path.exists(cache_path):
+            with open(cache_path) as f:
+                cache = json.load(f)
+            if cache_key in cache:
+                t = cache[cache_key]["tuning"]
+                self.set_tracer_tuning(**t)
+                return t, cache[cache_key].get("ms")
+        lib = _lib.load()
+        b, keep = self._batch(members, prec, limiter, beta)
+        best = _lib.TracerTuning()
+        ms = ctypes.c_double()
+        _lib.check("grist_tracer_autotune", lib.grist_tracer_autotune(
+            self.handle, ctypes.byref(b), float(dt), int(steps), _stream_handle(stream), ctypes.byref(best),
+            ctypes.byref(ms)))
+        t = self.tracer_tuning()
+        if cache_path and cache_key:
+            cache = {}
+            if os.path.exists(cache_path):
+                with open(cache_path) as f:
+                    cache = json.load(f)
+            cache[cache_key] = {"tuning": t, "ms": ms.value}
+            with open(cache_path, "w") as f:
+                json.dump(cache, f, indent=1, sort_keys=True)
+        return t, ms.value
+
+    def selftest_bounded_wait(self, spin_limit=100000, stream=None):
+        _lib.check("grist_selftest_bounded_wait", _lib.load().grist_selftest_bounded_wait(
+            self.handle, int(spin_limit), _stream_handle(stream)))
 
     def _dycore(self, fn, state, params, prec, dt, stream):
         lib = _lib.load()

@@ -40,6 +40,10 @@ class TracerBatch(ctypes.Structure):
                 ("beta_upwind", _D)]
 
 
+class TracerTuning(ctypes.Structure):
+    _fields_ = [("block", _I), ("tracers_per_thread", _I), ("persistent", _I), ("use_graph", _I)]
+
+
 class DycoreParams(ctypes.Structure):
     _fields_ = [("n_levels", _I), ("ld", _I), ("ld_int", _I), ("pi_top", _D), ("p0", _D), ("rd", _D),
                 ("cp", _D), ("g", _D), ("offcentre_beta", _D), ("b_interface", _P(_D)), ("phi_surface", _V)]
@@ -63,6 +67,10 @@ EXPORTS = {
     "grist_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "grist_profile_enable": ([_V, ctypes.c_int], ctypes.c_int),
     "grist_profile_read": ([_V, _I, ctypes.c_char_p, _P(_I), _P(_D), _P(_I)], ctypes.c_int),
+    "grist_tracer_set_tuning": ([_V, _P(TracerTuning)], ctypes.c_int),
+    "grist_tracer_get_tuning": ([_V, _P(TracerTuning)], ctypes.c_int),
+    "grist_tracer_autotune": ([_V, _P(TracerBatch), _D, _I, _V, _P(TracerTuning), _P(_D)], ctypes.c_int),
+    "grist_selftest_bounded_wait": ([_V, ctypes.c_int64, _V], ctypes.c_int),
     "grist_weighted_sum_noalloc": ([_V, _V, ctypes.c_int64, _V, _V], ctypes.c_int),
 }
 

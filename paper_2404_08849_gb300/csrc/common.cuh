@@ -122,6 +122,12 @@ int mesh_device(grist_mesh_s *m);
 void *scratch(grist_mesh_s *m, int slot, size_t bytes);
 uint32_t *status_word(grist_mesh_s *m);
 
+// Tracer-step context (tuning, device tables, graph cache) kept in the
+// handle; defined in tracer.cu.
+struct TracerCtx;
+TracerCtx *&tracer_ctx(grist_mesh_s *m);
+void tracer_ctx_free(TracerCtx *c);
+
 // Per-kernel event timing (grist_profile_enable): when profiling is on, the
 // scope records an event before and after the launch it encloses.
 struct ProfScope {

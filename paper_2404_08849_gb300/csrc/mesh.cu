@@ -23,6 +23,7 @@ struct grist_mesh_s {
     void *scr[8] = {nullptr};
     size_t scr_bytes[8] = {0};
     uint32_t *status = nullptr;
+    TracerCtx *tctx = nullptr;
     // profiling
     bool prof_on = false;
     std::vector<cudaEvent_t> ev;            // pool, pairs (2j, 2j+1)
@@ -36,6 +37,7 @@ namespace grist {
 const DevMesh &dev_mesh(grist_mesh_s *m) { return m->d; }
 int mesh_device(grist_mesh_s *m) { return m->device; }
 uint32_t *status_word(grist_mesh_s *m) { return m->status; }
+TracerCtx *&tracer_ctx(grist_mesh_s *m) { return m->tctx; }
 
 static const int kEventPairs = 4096;
 
@@ -428,6 +430,7 @@ extern "C" int grist_mesh_destroy(grist_mesh m) {
     cudaSetDevice(m->device);
     cudaDeviceSynchronize();
     for (auto &e : m->ev) cudaEventDestroy(e);
+    tracer_ctx_free(m->tctx);
     for (int s = 0; s < 8; s++)
         if (m->scr[s]) cudaFree(m->scr[s]);
     if (m->arena) cudaFree(m->arena);

@@ -3,56 +3,141 @@
 // final stage; FP64 or single-precision tracers (Sec. 2.3) with an FP64
 // mass flux and FP64 layer mass.
 //
+// Batching (ensembles of uneven members, Sec. 4.3 ensemble runs): every
+// phase of the step is one pass over a flat work list that concatenates,
+// for each member m and tracer group g (tracers_per_thread tracers), the
+// (entity, level) index space of that member; a segment table maps a flat
+// index to (m, g) by binary search, cached per thread across grid-stride
+// iterations.  The phases run either as one launch each or inside one
+// persistent cooperative kernel separated by bounded grid barriers.
+//
 // Data layout: q [T][nC][ld], dpi [nC][ld], mass flux [nE][ld], edge
-// fluxes [T][nE][ld]; one thread per (entity, level) with the level index
-// innermost, so a warp reads consecutive levels of neighbouring entities
-// (coalesced), and a thread loops over the member's tracers so the
-// per-(entity, level) geometry and mass-flux loads are shared by all of
-// them.
+// fluxes [T][nE][ld]; consecutive threads take consecutive levels of one
+// entity (coalesced rows), neighbour rows are gathered through L1/L2.
 #include <cmath>
+#include <cstring>
+#include <vector>
 
 #include "common.cuh"
 
 #define PN(n) (sizeof(TC) == 4 ? n "/mix" : n "/fp64")
 
 namespace grist {
+
+struct MemberDev {
+    void *q;                // [T][nC][ld] caller's tracers (q^n in, q^{n+1} out)
+    const double *dpi;      // [nC][ld]
+    const double *F;        // [nE][ld]
+    double *divF;           // scratch [nC][ld]
+    void *qA, *qB;          // scratch stage tracers [T][nC][ld]
+    void *FH;               // scratch edge fluxes [T][nE][ld]
+    void *Rp, *Rm;          // scratch FCT ratios [T][nC][ld]
+    int L, T, ld, pad;
+    LevelDiv DL;            // division by L
+    unsigned long long qs, fs;  // nC*ld, nE*ld
+};
+
+// A flat work space: segment s covers [start[s], start[s+1]) and belongs to
+// member mg[s].x, tracer group mg[s].y; within a segment the local index r
+// is entity * L + level.
+struct Space {
+    const unsigned long long *start;  // [nseg + 1]
+    const int2 *mg;                   // [nseg]
+    int nseg;
+    unsigned long long total;
+};
+
+struct TracerCtx {
+    grist_tracer_tuning tune{256, 4, 0, 0};
+    // device tables (one allocation), host mirrors
+    char *dtab = nullptr;
+    size_t dtab_bytes = 0;
+    std::vector<char> htab;
+    unsigned *barrier = nullptr;  // [0] arrival count, [1] generation, [2] abort, [3] self-test word
+    // graph cache
+    std::vector<unsigned long long> sig;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    bool graph_failed = false;
+    std::vector<unsigned long long> failed_sig;
+};
+
+void tracer_ctx_free(TracerCtx *c) {
+    if (!c) return;
+    if (c->exec) cudaGraphExecDestroy(c->exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    if (c->dtab) cudaFree(c->dtab);
+    if (c->barrier) cudaFree(c->barrier);
+    delete c;
+}
+
 namespace {
 
-constexpr int kBlock = 256;
+constexpr long long kBarrierSpinLimit = 20000000;  // x ~64 ns sleep: about a second
 
-// Cell divergence of the (time-mean) mass flux, FP64: the tracer solver's
-// own continuity, dpi^(s) = dpi^n - dt_s divF.
-__global__ void k_div_mass(DevMesh m, int L, int ld, LevelDiv D, const double *__restrict__ F,
-                           double *__restrict__ divF) {
-    uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= (uint32_t)m.nC * (uint32_t)L) return;
-    int i, k;
-    split_index(n, D, i, k);
+struct Batch {
+    const MemberDev *mem;
+    int nm;
+    Space D, C, E;  // D: cell x level (no groups); C: cell x level x group; E: edge x level x group
+    int tpt;
+    double dt;
+    int fct;
+    int beta1;
+    double beta;
+};
+
+// Cached segment lookup: returns the segment of flat index n, reusing seg
+// when n still lies inside it.
+__device__ __forceinline__ int find_seg(const Space &S, unsigned long long n, int seg) {
+    if (seg >= 0 && n >= S.start[seg] && n < S.start[seg + 1]) return seg;
+    int lo = 0, hi = S.nseg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (S.start[mid] <= n) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Loads of arrays that a phase writes and a later phase reads.  Inside the
+// persistent kernel such data changes during the launch, so it is read
+// coherently at L2 (ld.global.cg); across separate launches the read-only
+// path is safe.
+template <bool PERS, typename T> __device__ __forceinline__ T lds(const T *p) {
+    return PERS ? __ldcg(p) : __ldg(p);
+}
+
+template <typename TC> __device__ __forceinline__ TC tiny_of();
+template <> __device__ __forceinline__ double tiny_of<double>() { return 2.2250738585072014e-308; }
+template <> __device__ __forceinline__ float tiny_of<float>() { return 1.17549435e-38f; }
+
+// ---------------------------------------------------------------------------
+// phase bodies (one work item each)
+
+// Tracer continuity of the member: divF = div(mass flux), FP64.
+__device__ __forceinline__ void item_div(const DevMesh &m, const MemberDev &mb, int i, int k) {
     double s = 0.0;
 #pragma unroll
     for (int j = 0; j < GRIST_MAXE; j++)
-        s += ldg(m.cdiv + i * 6 + j) * ldg(F + (size_t)ldg(m.eoc + i * 6 + j) * ld + k);
-    divF[(size_t)i * ld + k] = s;
+        s += ldg(m.cdiv + i * 6 + j) * ldg(mb.F + (size_t)ldg(m.eoc + i * 6 + j) * mb.ld + k);
+    mb.divF[(size_t)i * mb.ld + k] = s;
 }
 
 // Third-order upwind edge flux (Skamarock-Gassmann form):
 //   q_e = (q1 + q2)/2 - (dc^2/12)(q''1 + q''2) + sgn(F) beta (dc^2/12)(q''2 - q''1)
-//   F^H = F q_e
-// With beta = 1 only the upwind side's second derivative survives:
-//   q_e = (q1 + q2)/2 - 2 (dc^2/12) q''_upwind.
-template <typename TQ, typename TC, bool BETA1>
-__global__ void k_edge_flux(DevMesh m, int T, int L, int ld, LevelDiv D, const TQ *__restrict__ q, size_t qs,
-                            const double *__restrict__ F, TC beta, TC *__restrict__ FH, size_t fs) {
-    uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= (uint32_t)m.nE * (uint32_t)L) return;
-    int e, k;
-    split_index(n, D, e, k);
+// F^H = F q_e.  With beta = 1 only the upwind side's second derivative
+// survives: q_e = (q1 + q2)/2 - 2 (dc^2/12) q''_upwind.
+template <bool PERS, typename TQ, typename TC>
+__device__ __forceinline__ void item_edge(const DevMesh &m, const MemberDev &mb, const TQ *q, int t0, int t1,
+                                          int e, int k, bool beta1, TC beta) {
+    const int ld = mb.ld;
     const int2 c = ldg(m.coe + e);
-    const TC f = (TC)ldg(F + (size_t)e * ld + k);
+    const TC f = (TC)ldg(mb.F + (size_t)e * ld + k);
     const TC dc2 = ldg(Coef<TC>::dc2(m) + e);
     const int32_t *st = m.d2i + (size_t)e * 14;
     const TC *cf = Coef<TC>::d2c(m) + (size_t)e * 14;
-    if (BETA1) {
+    TC *FH = (TC *)mb.FH;
+    if (beta1) {
         const int side = f >= (TC)0 ? 0 : 1;
         int idx[GRIST_D2P];
         TC w[GRIST_D2P];
@@ -61,28 +146,27 @@ __global__ void k_edge_flux(DevMesh m, int T, int L, int ld, LevelDiv D, const T
             idx[j] = ldg(st + side * GRIST_D2P + j);
             w[j] = ldg(cf + side * GRIST_D2P + j);
         }
-        for (int t = 0; t < T; t++) {
-            const TQ *qt = q + (size_t)t * qs;
+        for (int t = t0; t < t1; t++) {
+            const TQ *qt = q + (size_t)t * mb.qs;
             TC d = 0;
 #pragma unroll
-            for (int j = 0; j < GRIST_D2P; j++) d += w[j] * (TC)ldg(qt + (size_t)idx[j] * ld + k);
-            TC q1 = (TC)ldg(qt + (size_t)c.x * ld + k), q2 = (TC)ldg(qt + (size_t)c.y * ld + k);
-            TC qe = (TC)0.5 * (q1 + q2) - (TC)2 * dc2 * d;
-            FH[(size_t)t * fs + (size_t)e * ld + k] = f * qe;
+            for (int j = 0; j < GRIST_D2P; j++) d += w[j] * (TC)lds<PERS>(qt + (size_t)idx[j] * ld + k);
+            const TC q1 = (TC)lds<PERS>(qt + (size_t)c.x * ld + k), q2 = (TC)lds<PERS>(qt + (size_t)c.y * ld + k);
+            FH[(size_t)t * mb.fs + (size_t)e * ld + k] = f * ((TC)0.5 * (q1 + q2) - (TC)2 * dc2 * d);
         }
     } else {
         const TC sgn = f >= (TC)0 ? (TC)1 : (TC)-1;
-        for (int t = 0; t < T; t++) {
-            const TQ *qt = q + (size_t)t * qs;
+        for (int t = t0; t < t1; t++) {
+            const TQ *qt = q + (size_t)t * mb.qs;
             TC d1 = 0, d2 = 0;
 #pragma unroll
             for (int j = 0; j < GRIST_D2P; j++) {
-                d1 += ldg(cf + j) * (TC)ldg(qt + (size_t)ldg(st + j) * ld + k);
-                d2 += ldg(cf + GRIST_D2P + j) * (TC)ldg(qt + (size_t)ldg(st + GRIST_D2P + j) * ld + k);
+                d1 += ldg(cf + j) * (TC)lds<PERS>(qt + (size_t)ldg(st + j) * ld + k);
+                d2 += ldg(cf + GRIST_D2P + j) * (TC)lds<PERS>(qt + (size_t)ldg(st + GRIST_D2P + j) * ld + k);
             }
-            TC q1 = (TC)ldg(qt + (size_t)c.x * ld + k), q2 = (TC)ldg(qt + (size_t)c.y * ld + k);
-            TC qe = (TC)0.5 * (q1 + q2) - dc2 * (d1 + d2) + sgn * beta * dc2 * (d2 - d1);
-            FH[(size_t)t * fs + (size_t)e * ld + k] = f * qe;
+            const TC q1 = (TC)lds<PERS>(qt + (size_t)c.x * ld + k), q2 = (TC)lds<PERS>(qt + (size_t)c.y * ld + k);
+            const TC qe = (TC)0.5 * (q1 + q2) - dc2 * (d1 + d2) + sgn * beta * dc2 * (d2 - d1);
+            FH[(size_t)t * mb.fs + (size_t)e * ld + k] = f * qe;
         }
     }
 }
@@ -91,17 +175,13 @@ __global__ void k_edge_flux(DevMesh m, int T, int L, int ld, LevelDiv D, const T
 // written as r1 q^n - r2 div with r1 = dpi^n/dpi^(s), r2 = dt_s/dpi^(s)
 // taken once per (cell, level) in FP64 and rounded to the tracer type
 // (Sec. 2.2 (ii): no mixed-kind products inside the tracer loop).
-template <typename TQ, typename TC>
-__global__ void k_stage_update(DevMesh m, int T, int L, int ld, LevelDiv D, const TQ *__restrict__ qn, TQ *qout,
-                               size_t qs, const TC *__restrict__ FH, size_t fs, const double *__restrict__ dpi,
-                               const double *__restrict__ divF, double dts, uint32_t *status) {
-    uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= (uint32_t)m.nC * (uint32_t)L) return;
-    int i, k;
-    split_index(n, D, i, k);
+template <bool PERS, typename TQ, typename TC>
+__device__ __forceinline__ bool item_update(const DevMesh &m, const MemberDev &mb, TQ *qout, int t0, int t1, int i,
+                                            int k, double dts) {
+    const int ld = mb.ld;
     const size_t x = (size_t)i * ld + k;
-    const double dp = dpi[x];
-    const double rinv = 1.0 / (dp - dts * divF[x]);
+    const double dp = mb.dpi[x];
+    const double rinv = 1.0 / (dp - dts * lds<PERS>(mb.divF + x));
     const TC r1 = (TC)(dp * rinv), r2 = (TC)(dts * rinv);
     int eidx[GRIST_MAXE];
     TC cw[GRIST_MAXE];
@@ -110,75 +190,69 @@ __global__ void k_stage_update(DevMesh m, int T, int L, int ld, LevelDiv D, cons
         eidx[j] = ldg(m.eoc + i * 6 + j);
         cw[j] = ldg(Coef<TC>::cdiv(m) + i * 6 + j);
     }
+    const TQ *qn = (const TQ *)mb.q;
+    const TC *FH = (const TC *)mb.FH;
     bool bad = false;
-    for (int t = 0; t < T; t++) {
-        const TC *ft = FH + (size_t)t * fs;
+    for (int t = t0; t < t1; t++) {
+        const TC *ft = FH + (size_t)t * mb.fs;
         TC div = 0;
 #pragma unroll
-        for (int j = 0; j < GRIST_MAXE; j++) div += cw[j] * ldg(ft + (size_t)eidx[j] * ld + k);
-        TC v = r1 * (TC)qn[(size_t)t * qs + x] - r2 * div;
+        for (int j = 0; j < GRIST_MAXE; j++) div += cw[j] * lds<PERS>(ft + (size_t)eidx[j] * ld + k);
+        const TC v = r1 * (TC)qn[(size_t)t * mb.qs + x] - r2 * div;
         bad |= !isfinite(v);
-        qout[(size_t)t * qs + x] = (TQ)v;
+        qout[(size_t)t * mb.qs + x] = (TQ)v;
     }
-    if (bad) atomicOr(status, GRIST_FLAG_NONFINITE);
+    return bad;
 }
 
-// Low-order (first-order upwind) flux of edge j of cell i from q^n.
-// The upwind cell of an edge is c1 when F >= 0, c2 otherwise; cell i is c1
-// of its edge exactly when the divergence coefficient is positive.
-template <typename TQ, typename TC>
+// Low-order (first-order upwind) flux of edge j of cell i from q^n.  The
+// upwind cell is c1 when F >= 0, c2 otherwise; cell i is c1 of its edge
+// exactly when its divergence coefficient is positive.
+template <bool PERS, typename TQ, typename TC>
 __device__ __forceinline__ TC upwind_flux(TC f, TC cw, int i, int nb, const TQ *qt, int ld, int k) {
     const bool i_is_c1 = cw > (TC)0;
     const int up = ((f >= (TC)0) == i_is_c1) ? i : nb;
-    return f * (TC)ldg(qt + (size_t)up * ld + k);
+    return f * (TC)lds<PERS>(qt + (size_t)up * ld + k);
 }
 
-// FCT step 1: low-order solution q^td = (dpi^n q^n - dt div F^L) / dpi^(3).
-template <typename TQ, typename TC>
-__global__ void k_fct_lowres(DevMesh m, int T, int L, int ld, LevelDiv D, const TQ *__restrict__ qn, size_t qs,
-                             const double *__restrict__ F, const double *__restrict__ dpi,
-                             const double *__restrict__ divF, double dt, TQ *__restrict__ qtd) {
-    uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= (uint32_t)m.nC * (uint32_t)L) return;
-    int i, k;
-    split_index(n, D, i, k);
+// FCT 1: low-order solution q^td = (dpi^n q^n - dt div F^L) / dpi^(3).
+template <bool PERS, typename TQ, typename TC>
+__device__ __forceinline__ void item_lowres(const DevMesh &m, const MemberDev &mb, int t0, int t1, int i, int k,
+                                            double dt) {
+    const int ld = mb.ld;
     const size_t x = (size_t)i * ld + k;
-    const double dp = dpi[x];
-    const double rinv = 1.0 / (dp - dt * divF[x]);
+    const double dp = mb.dpi[x];
+    const double rinv = 1.0 / (dp - dt * lds<PERS>(mb.divF + x));
     const TC r1 = (TC)(dp * rinv), r2 = (TC)(dt * rinv);
     int nb[GRIST_MAXE];
     TC cw[GRIST_MAXE], fe[GRIST_MAXE];
 #pragma unroll
     for (int j = 0; j < GRIST_MAXE; j++) {
-        int e = ldg(m.eoc + i * 6 + j);
+        const int e = ldg(m.eoc + i * 6 + j);
         nb[j] = ldg(m.coc + i * 6 + j);
         cw[j] = ldg(Coef<TC>::cdiv(m) + i * 6 + j);
-        fe[j] = (TC)ldg(F + (size_t)e * ld + k);
+        fe[j] = (TC)ldg(mb.F + (size_t)e * ld + k);
     }
-    for (int t = 0; t < T; t++) {
-        const TQ *qt = qn + (size_t)t * qs;
+    const TQ *qn = (const TQ *)mb.q;
+    TQ *qtd = (TQ *)mb.qA;
+    for (int t = t0; t < t1; t++) {
+        const TQ *qt = qn + (size_t)t * mb.qs;
         TC div = 0;
 #pragma unroll
-        for (int j = 0; j < GRIST_MAXE; j++) div += cw[j] * upwind_flux<TQ, TC>(fe[j], cw[j], i, nb[j], qt, ld, k);
-        qtd[(size_t)t * qs + x] = (TQ)(r1 * (TC)qt[x] - r2 * div);
+        for (int j = 0; j < GRIST_MAXE; j++) div += cw[j] * upwind_flux<PERS, TQ, TC>(fe[j], cw[j], i, nb[j], qt, ld, k);
+        qtd[(size_t)t * mb.qs + x] = (TQ)(r1 * (TC)qt[x] - r2 * div);
     }
 }
 
-// FCT step 2: local bounds over the cell and its neighbours of {q^n, q^td};
+// FCT 2: local bounds over the cell and its neighbours of {q^n, q^td};
 // antidiffusive in/out sums P+-, allowed changes Q+-, ratios
 // R+- = min(1, Q / (P + TINY)) (Sec. 2.2 (iii): TINY of the working type).
-template <typename TQ, typename TC>
-__global__ void k_fct_ratios(DevMesh m, int T, int L, int ld, LevelDiv D, const TQ *__restrict__ qn,
-                             const TQ *__restrict__ qtd, size_t qs, const TC *__restrict__ FH, size_t fs,
-                             const double *__restrict__ F, const double *__restrict__ dpi,
-                             const double *__restrict__ divF, double dt, TC *__restrict__ Rp,
-                             TC *__restrict__ Rm) {
-    uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= (uint32_t)m.nC * (uint32_t)L) return;
-    int i, k;
-    split_index(n, D, i, k);
+template <bool PERS, typename TQ, typename TC>
+__device__ __forceinline__ void item_ratios(const DevMesh &m, const MemberDev &mb, int t0, int t1, int i, int k,
+                                            double dt) {
+    const int ld = mb.ld;
     const size_t x = (size_t)i * ld + k;
-    const TC dp3 = (TC)(dpi[x] - dt * divF[x]);
+    const TC dp3 = (TC)(mb.dpi[x] - dt * lds<PERS>(mb.divF + x));
     const TC dtc = (TC)dt;
     int nb[GRIST_MAXE], eidx[GRIST_MAXE];
     TC cw[GRIST_MAXE], fe[GRIST_MAXE];
@@ -187,50 +261,47 @@ __global__ void k_fct_ratios(DevMesh m, int T, int L, int ld, LevelDiv D, const 
         eidx[j] = ldg(m.eoc + i * 6 + j);
         nb[j] = ldg(m.coc + i * 6 + j);
         cw[j] = ldg(Coef<TC>::cdiv(m) + i * 6 + j);
-        fe[j] = (TC)ldg(F + (size_t)eidx[j] * ld + k);
+        fe[j] = (TC)ldg(mb.F + (size_t)eidx[j] * ld + k);
     }
-    for (int t = 0; t < T; t++) {
-        const TQ *qt = qn + (size_t)t * qs;
-        const TQ *qd = qtd + (size_t)t * qs;
-        const TC *ft = FH + (size_t)t * fs;
-        TC qtd_i = (TC)qd[x];
+    const TQ *qn = (const TQ *)mb.q, *qtd = (const TQ *)mb.qA;
+    const TC *FH = (const TC *)mb.FH;
+    TC *Rp = (TC *)mb.Rp, *Rm = (TC *)mb.Rm;
+    for (int t = t0; t < t1; t++) {
+        const TQ *qt = qn + (size_t)t * mb.qs;
+        const TQ *qd = qtd + (size_t)t * mb.qs;
+        const TC *ft = FH + (size_t)t * mb.fs;
+        const TC qtd_i = (TC)lds<PERS>(qd + x);
         TC qmax = fmax_((TC)qt[x], qtd_i), qmin = fmin_((TC)qt[x], qtd_i);
         TC pp = 0, pm = 0;
 #pragma unroll
         for (int j = 0; j < GRIST_MAXE; j++) {
-            size_t y = (size_t)nb[j] * ld + k;
-            TC a = (TC)ldg(qt + y), b = (TC)ldg(qd + y);
+            const size_t y = (size_t)nb[j] * ld + k;
+            const TC a = (TC)qt[y], b = (TC)lds<PERS>(qd + y);
             qmax = fmax_(qmax, fmax_(a, b));
             qmin = fmin_(qmin, fmin_(a, b));
-            TC ae = ldg(ft + (size_t)eidx[j] * ld + k) - upwind_flux<TQ, TC>(fe[j], cw[j], i, nb[j], qt, ld, k);
-            TC out = cw[j] * ae;  // outward antidiffusive flux / A_i (sign and dv folded in)
+            const TC ae = lds<PERS>(ft + (size_t)eidx[j] * ld + k) - upwind_flux<PERS, TQ, TC>(fe[j], cw[j], i, nb[j], qt, ld, k);
+            const TC out = cw[j] * ae;  // outward antidiffusive flux / A_i (sign and dv folded in)
             pp += fmax_((TC)0, -out);
             pm += fmax_((TC)0, out);
         }
         pp *= dtc;
         pm *= dtc;
-        TC Qp = (qmax - qtd_i) * dp3, Qm = (qtd_i - qmin) * dp3;
-        Rp[(size_t)t * qs + x] = fmin_((TC)1, Qp / (pp + Coef<TC>::tiny()));
-        Rm[(size_t)t * qs + x] = fmin_((TC)1, Qm / (pm + Coef<TC>::tiny()));
+        const TC Qp = (qmax - qtd_i) * dp3, Qm = (qtd_i - qmin) * dp3;
+        Rp[(size_t)t * mb.qs + x] = fmin_((TC)1, Qp / (pp + tiny_of<TC>()));
+        Rm[(size_t)t * mb.qs + x] = fmin_((TC)1, Qm / (pm + tiny_of<TC>()));
     }
 }
 
-// FCT step 3: limited flux F^L + C A with C = min(R-(c1), R+(c2)) when the
+// FCT 3: limited flux F^L + C A with C = min(R-(c1), R+(c2)) when the
 // antidiffusive flux A runs c1 -> c2 (A >= 0), min(R+(c1), R-(c2)) else;
-// final update q^{n+1} = (dpi^n q^n - dt div(F^L + C A)) / dpi^(3).
-template <typename TQ, typename TC>
-__global__ void k_fct_final(DevMesh m, int T, int L, int ld, LevelDiv D, const TQ *__restrict__ qn,
-                            TQ *__restrict__ qout, size_t qs, const TC *__restrict__ FH, size_t fs,
-                            const double *__restrict__ F, const double *__restrict__ dpi,
-                            const double *__restrict__ divF, double dt, const TC *__restrict__ Rp,
-                            const TC *__restrict__ Rm, uint32_t *status) {
-    uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= (uint32_t)m.nC * (uint32_t)L) return;
-    int i, k;
-    split_index(n, D, i, k);
+// q^{n+1} = (dpi^n q^n - dt div(F^L + C A)) / dpi^(3) into qB.
+template <bool PERS, typename TQ, typename TC>
+__device__ __forceinline__ bool item_final(const DevMesh &m, const MemberDev &mb, int t0, int t1, int i, int k,
+                                           double dt) {
+    const int ld = mb.ld;
     const size_t x = (size_t)i * ld + k;
-    const double dp = dpi[x];
-    const double rinv = 1.0 / (dp - dt * divF[x]);
+    const double dp = mb.dpi[x];
+    const double rinv = 1.0 / (dp - dt * lds<PERS>(mb.divF + x));
     const TC r1 = (TC)(dp * rinv), r2 = (TC)(dt * rinv);
     int nb[GRIST_MAXE], eidx[GRIST_MAXE];
     TC cw[GRIST_MAXE], fe[GRIST_MAXE];
@@ -239,94 +310,450 @@ __global__ void k_fct_final(DevMesh m, int T, int L, int ld, LevelDiv D, const T
         eidx[j] = ldg(m.eoc + i * 6 + j);
         nb[j] = ldg(m.coc + i * 6 + j);
         cw[j] = ldg(Coef<TC>::cdiv(m) + i * 6 + j);
-        fe[j] = (TC)ldg(F + (size_t)eidx[j] * ld + k);
+        fe[j] = (TC)ldg(mb.F + (size_t)eidx[j] * ld + k);
     }
+    const TQ *qn = (const TQ *)mb.q;
+    const TC *FH = (const TC *)mb.FH;
+    const TC *Rp = (const TC *)mb.Rp, *Rm = (const TC *)mb.Rm;
+    TQ *qout = (TQ *)mb.qB;
     bool bad = false;
-    for (int t = 0; t < T; t++) {
-        const TQ *qt = qn + (size_t)t * qs;
-        const TC *ft = FH + (size_t)t * fs;
-        const TC *rp = Rp + (size_t)t * qs, *rm = Rm + (size_t)t * qs;
-        const TC rp_i = rp[x], rm_i = rm[x];
+    for (int t = t0; t < t1; t++) {
+        const TQ *qt = qn + (size_t)t * mb.qs;
+        const TC *ft = FH + (size_t)t * mb.fs;
+        const TC *rp = Rp + (size_t)t * mb.qs, *rm = Rm + (size_t)t * mb.qs;
+        const TC rp_i = lds<PERS>(rp + x), rm_i = lds<PERS>(rm + x);
         TC div = 0;
 #pragma unroll
         for (int j = 0; j < GRIST_MAXE; j++) {
-            size_t y = (size_t)nb[j] * ld + k;
-            TC fl = upwind_flux<TQ, TC>(fe[j], cw[j], i, nb[j], qt, ld, k);
-            TC ae = ldg(ft + (size_t)eidx[j] * ld + k) - fl;
+            const size_t y = (size_t)nb[j] * ld + k;
+            const TC fl = upwind_flux<PERS, TQ, TC>(fe[j], cw[j], i, nb[j], qt, ld, k);
+            const TC ae = lds<PERS>(ft + (size_t)eidx[j] * ld + k) - fl;
             const bool i_is_c1 = cw[j] > (TC)0;
-            TC rp1 = i_is_c1 ? rp_i : ldg(rp + y), rm1 = i_is_c1 ? rm_i : ldg(rm + y);
-            TC rp2 = i_is_c1 ? ldg(rp + y) : rp_i, rm2 = i_is_c1 ? ldg(rm + y) : rm_i;
-            TC c = ae >= (TC)0 ? fmin_(rm1, rp2) : fmin_(rp1, rm2);
+            const TC rpy = lds<PERS>(rp + y), rmy = lds<PERS>(rm + y);
+            const TC rp1 = i_is_c1 ? rp_i : rpy, rm1 = i_is_c1 ? rm_i : rmy;
+            const TC rp2 = i_is_c1 ? rpy : rp_i, rm2 = i_is_c1 ? rmy : rm_i;
+            const TC c = ae >= (TC)0 ? fmin_(rm1, rp2) : fmin_(rp1, rm2);
             div += cw[j] * (fl + c * ae);
         }
-        TC v = r1 * (TC)qt[x] - r2 * div;
+        const TC v = r1 * (TC)qt[x] - r2 * div;
         bad |= !isfinite(v);
-        qout[(size_t)t * qs + x] = (TQ)v;
+        qout[(size_t)t * mb.qs + x] = (TQ)v;
+    }
+    return bad;
+}
+
+template <bool PERS, typename TQ>
+__device__ __forceinline__ void item_copy(const MemberDev &mb, int t0, int t1, int i, int k) {
+    const size_t x = (size_t)i * mb.ld + k;
+    const TQ *src = (const TQ *)mb.qB;
+    TQ *dst = (TQ *)mb.q;
+    for (int t = t0; t < t1; t++) dst[(size_t)t * mb.qs + x] = lds<PERS>(src + (size_t)t * mb.qs + x);
+}
+
+// ---------------------------------------------------------------------------
+// phases: grid-stride loops over a work space
+
+enum Phase { P_DIV = 0, P_EDGE0, P_UPD0, P_EDGE1, P_UPD1, P_EDGE2, P_UPD2, P_LOWRES, P_RATIOS, P_FINAL, P_COPY };
+
+template <bool PERS, typename TQ, typename TC, int PH>
+__device__ void run_phase(const DevMesh &m, const Batch &B, uint32_t *status) {
+    const Space &S = (PH == P_DIV) ? B.D : (PH == P_EDGE0 || PH == P_EDGE1 || PH == P_EDGE2) ? B.E : B.C;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    int seg = -1;
+    bool bad = false;
+    const double dts = PH <= P_UPD0 ? B.dt / 3.0 : (PH <= P_UPD1 ? B.dt / 2.0 : B.dt);
+    for (unsigned long long n = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; n < S.total; n += stride) {
+        seg = find_seg(S, n, seg);
+        const int2 mg = S.mg[seg];
+        const MemberDev &mb = B.mem[mg.x];
+        int ent, k;
+        split_index((uint32_t)(n - S.start[seg]), mb.DL, ent, k);
+        const int t0 = mg.y * B.tpt;
+        const int t1 = min(mb.T, t0 + B.tpt);
+        if (PH == P_DIV) item_div(m, mb, ent, k);
+        if (PH == P_EDGE0) item_edge<PERS, TQ, TC>(m, mb, (const TQ *)mb.q, t0, t1, ent, k, B.beta1, (TC)B.beta);
+        if (PH == P_EDGE1) item_edge<PERS, TQ, TC>(m, mb, (const TQ *)mb.qA, t0, t1, ent, k, B.beta1, (TC)B.beta);
+        if (PH == P_EDGE2) item_edge<PERS, TQ, TC>(m, mb, (const TQ *)mb.qB, t0, t1, ent, k, B.beta1, (TC)B.beta);
+        if (PH == P_UPD0) bad |= item_update<PERS, TQ, TC>(m, mb, (TQ *)mb.qA, t0, t1, ent, k, dts);
+        if (PH == P_UPD1) bad |= item_update<PERS, TQ, TC>(m, mb, (TQ *)mb.qB, t0, t1, ent, k, dts);
+        if (PH == P_UPD2) bad |= item_update<PERS, TQ, TC>(m, mb, (TQ *)mb.q, t0, t1, ent, k, dts);
+        if (PH == P_LOWRES) item_lowres<PERS, TQ, TC>(m, mb, t0, t1, ent, k, B.dt);
+        if (PH == P_RATIOS) item_ratios<PERS, TQ, TC>(m, mb, t0, t1, ent, k, B.dt);
+        if (PH == P_FINAL) bad |= item_final<PERS, TQ, TC>(m, mb, t0, t1, ent, k, B.dt);
+        if (PH == P_COPY) item_copy<PERS, TQ>(mb, t0, t1, ent, k);
     }
     if (bad) atomicOr(status, GRIST_FLAG_NONFINITE);
 }
 
-template <typename T>
-__global__ void k_copy(const T *__restrict__ src, T *__restrict__ dst, size_t n) {
-    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    size_t stride = (size_t)gridDim.x * blockDim.x;
-    for (; i < n; i += stride) dst[i] = src[i];
+template <typename TQ, typename TC, int PH>
+__global__ void k_tracer_phase(DevMesh m, Batch B, uint32_t *status) {
+    run_phase<false, TQ, TC, PH>(m, B, status);
 }
 
+// Bounded wait until *gen differs from g: at most `limit` polls (~64 ns
+// apart); on giving up (or when another block already gave up) raises
+// GRIST_FLAG_TIMEOUT and returns false.
+__device__ bool bounded_wait_change(volatile unsigned *gen, unsigned g, long long limit, unsigned *abort_word,
+                                    uint32_t *status) {
+    long long it = 0;
+    while (*gen == g) {
+        if (++it > limit || *(volatile unsigned *)abort_word) {
+            atomicExch(abort_word, 1u);
+            atomicOr(status, GRIST_FLAG_TIMEOUT);
+            return false;
+        }
+        __nanosleep(64);
+    }
+    return true;
+}
+
+// Grid barrier for a cooperative launch (all blocks co-resident).  bar[0]
+// counts arrivals, bar[1] is the generation, bar[2] the launch's abort word
+// (both bar[0] and bar[2] are zeroed before every launch).  Thread 0 of each
+// block arrives on the counter; the last arrival resets it and bumps the
+// generation.  The wait is bounded (bounded_wait_change), so the kernel
+// always ends; after a timeout every block returns false.
+__device__ bool grid_sync(unsigned *bar, uint32_t *status) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        volatile unsigned *gen = bar + 1;
+        const unsigned g = *gen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(bar, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else if (!bounded_wait_change(gen, g, kBarrierSpinLimit, bar + 2, status)) {
+            ok = 0;
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// Self-test of the bounded wait: one thread waits on a word nothing writes.
+__global__ void k_wait_selftest(unsigned *word, unsigned *abort_word, long long limit, uint32_t *status) {
+    if (threadIdx.x == 0 && blockIdx.x == 0)
+        bounded_wait_change(word, *(volatile unsigned *)word, limit, abort_word, status);
+}
+
+// One cooperative launch for the whole step: the phases in order with a
+// grid barrier between consecutive ones.
 template <typename TQ, typename TC>
-int member_step(grist_mesh_s *h, const grist_tracer_member &mb, int limiter, double beta, double dt,
+__global__ void k_tracer_persistent(DevMesh m, Batch B, unsigned *bar, uint32_t *status) {
+    run_phase<true, TQ, TC, P_DIV>(m, B, status);
+    if (!grid_sync(bar, status)) return;
+    run_phase<true, TQ, TC, P_EDGE0>(m, B, status);
+    if (!grid_sync(bar, status)) return;
+    run_phase<true, TQ, TC, P_UPD0>(m, B, status);
+    if (!grid_sync(bar, status)) return;
+    run_phase<true, TQ, TC, P_EDGE1>(m, B, status);
+    if (!grid_sync(bar, status)) return;
+    run_phase<true, TQ, TC, P_UPD1>(m, B, status);
+    if (!grid_sync(bar, status)) return;
+    run_phase<true, TQ, TC, P_EDGE2>(m, B, status);
+    if (!grid_sync(bar, status)) return;
+    if (!B.fct) {
+        run_phase<true, TQ, TC, P_UPD2>(m, B, status);
+        return;
+    }
+    run_phase<true, TQ, TC, P_LOWRES>(m, B, status);
+    if (!grid_sync(bar, status)) return;
+    run_phase<true, TQ, TC, P_RATIOS>(m, B, status);
+    if (!grid_sync(bar, status)) return;
+    run_phase<true, TQ, TC, P_FINAL>(m, B, status);
+    if (!grid_sync(bar, status)) return;
+    run_phase<true, TQ, TC, P_COPY>(m, B, status);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+
+size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
+
+struct HostPlan {
+    std::vector<MemberDev> mem;
+    std::vector<unsigned long long> sD, sC, sE;
+    std::vector<int2> mD, mC, mE;
+    size_t scratch_bytes = 0;
+};
+
+template <typename TQ, typename TC>
+int plan_batch(const DevMesh &m, const grist_tracer_batch *b, int tpt, HostPlan &P) {
+    P = HostPlan();
+    size_t off = 0;
+    unsigned long long tD = 0, tC = 0, tE = 0;
+    for (int i = 0; i < b->n_members; i++) {
+        const grist_tracer_member &u = b->members[i];
+        if (u.n_levels == 0 || u.n_tracers == 0) continue;
+        MemberDev d{};
+        d.q = u.q;
+        d.dpi = u.dpi;
+        d.F = u.mass_flux;
+        d.L = u.n_levels;
+        d.T = u.n_tracers;
+        d.ld = u.ld;
+        d.DL = make_div((uint32_t)u.n_levels);
+        d.qs = (unsigned long long)m.nC * u.ld;
+        d.fs = (unsigned long long)m.nE * u.ld;
+        // scratch offsets (relative, resolved after allocation)
+        const size_t bq = (size_t)d.T * d.qs * sizeof(TQ), bf = (size_t)d.T * d.fs * sizeof(TC),
+                     br = (size_t)d.T * d.qs * sizeof(TC), bd = d.qs * sizeof(double);
+        d.divF = (double *)(uintptr_t)off; off += al256(bd);
+        d.qA = (void *)(uintptr_t)off; off += al256(bq);
+        d.qB = (void *)(uintptr_t)off; off += al256(bq);
+        d.FH = (void *)(uintptr_t)off; off += al256(bf);
+        d.Rp = (void *)(uintptr_t)off; off += al256(br);
+        d.Rm = (void *)(uintptr_t)off; off += al256(br);
+        const int idx = (int)P.mem.size();
+        const int G = (d.T + tpt - 1) / tpt;
+        P.sD.push_back(tD); P.mD.push_back(make_int2(idx, 0));
+        tD += (unsigned long long)m.nC * d.L;
+        for (int g = 0; g < G; g++) {
+            P.sC.push_back(tC); P.mC.push_back(make_int2(idx, g));
+            tC += (unsigned long long)m.nC * d.L;
+            P.sE.push_back(tE); P.mE.push_back(make_int2(idx, g));
+            tE += (unsigned long long)m.nE * d.L;
+        }
+        P.mem.push_back(d);
+    }
+    P.sD.push_back(tD);
+    P.sC.push_back(tC);
+    P.sE.push_back(tE);
+    P.scratch_bytes = off;
+    return GRIST_OK;
+}
+
+// Upload the plan's tables (member descriptors with resolved scratch
+// pointers, segment tables) into the context's device table; returns the
+// Batch with device pointers.  Synchronous when the tables change.
+template <typename TQ, typename TC>
+int upload_plan(grist_mesh_s *h, TracerCtx *c, HostPlan &P, const grist_tracer_batch *b, double dt, Batch &B,
                 cudaStream_t st) {
+    char *scr = (char *)scratch(h, 0, P.scratch_bytes + 256);
+    if (!scr) return GRIST_ENOMEM;
+    for (auto &d : P.mem) {
+        d.divF = (double *)(scr + (uintptr_t)d.divF);
+        d.qA = scr + (uintptr_t)d.qA;
+        d.qB = scr + (uintptr_t)d.qB;
+        d.FH = scr + (uintptr_t)d.FH;
+        d.Rp = scr + (uintptr_t)d.Rp;
+        d.Rm = scr + (uintptr_t)d.Rm;
+    }
+    const size_t nm = P.mem.size();
+    size_t o = 0;
+    const size_t o_mem = o; o += al256(nm * sizeof(MemberDev));
+    const size_t o_sD = o; o += al256(P.sD.size() * 8);
+    const size_t o_sC = o; o += al256(P.sC.size() * 8);
+    const size_t o_sE = o; o += al256(P.sE.size() * 8);
+    const size_t o_mD = o; o += al256(P.mD.size() * sizeof(int2));
+    const size_t o_mC = o; o += al256(P.mC.size() * sizeof(int2));
+    const size_t o_mE = o; o += al256(P.mE.size() * sizeof(int2));
+    std::vector<char> ht(o, 0);
+    std::memcpy(ht.data() + o_mem, P.mem.data(), nm * sizeof(MemberDev));
+    std::memcpy(ht.data() + o_sD, P.sD.data(), P.sD.size() * 8);
+    std::memcpy(ht.data() + o_sC, P.sC.data(), P.sC.size() * 8);
+    std::memcpy(ht.data() + o_sE, P.sE.data(), P.sE.size() * 8);
+    std::memcpy(ht.data() + o_mD, P.mD.data(), P.mD.size() * sizeof(int2));
+    std::memcpy(ht.data() + o_mC, P.mC.data(), P.mC.size() * sizeof(int2));
+    std::memcpy(ht.data() + o_mE, P.mE.data(), P.mE.size() * sizeof(int2));
+    if (c->dtab_bytes < o) {
+        if (c->dtab) {
+            cudaDeviceSynchronize();
+            cudaFree(c->dtab);
+            c->dtab = nullptr;
+        }
+        if (cudaMalloc(&c->dtab, o) != cudaSuccess) { c->dtab_bytes = 0; return GRIST_ENOMEM; }
+        c->dtab_bytes = o;
+        c->htab.clear();
+    }
+    if (c->htab.size() != o || std::memcmp(c->htab.data(), ht.data(), o) != 0) {
+        GRIST_CUDA_TRY(cudaStreamSynchronize(st));
+        GRIST_CUDA_TRY(cudaMemcpy(c->dtab, ht.data(), o, cudaMemcpyHostToDevice));
+        c->htab = ht;
+    }
+    if (!c->barrier) {
+        if (cudaMalloc(&c->barrier, 4 * sizeof(unsigned)) != cudaSuccess) return GRIST_ENOMEM;
+        GRIST_CUDA_TRY(cudaMemset(c->barrier, 0, 4 * sizeof(unsigned)));
+    }
+    B.mem = (const MemberDev *)(c->dtab + o_mem);
+    B.nm = (int)nm;
+    B.D = Space{(const unsigned long long *)(c->dtab + o_sD), (const int2 *)(c->dtab + o_mD), (int)P.mD.size(), P.sD.back()};
+    B.C = Space{(const unsigned long long *)(c->dtab + o_sC), (const int2 *)(c->dtab + o_mC), (int)P.mC.size(), P.sC.back()};
+    B.E = Space{(const unsigned long long *)(c->dtab + o_sE), (const int2 *)(c->dtab + o_mE), (int)P.mE.size(), P.sE.back()};
+    B.tpt = c->tune.tracers_per_thread;
+    B.dt = dt;
+    B.fct = b->limiter ? 1 : 0;
+    B.beta1 = b->beta_upwind == 1.0 ? 1 : 0;
+    B.beta = b->beta_upwind;
+    return GRIST_OK;
+}
+
+int sm_count(int dev) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
+// Enqueue the step's kernels (no host synchronisation: capturable).
+template <typename TQ, typename TC>
+int enqueue_step(grist_mesh_s *h, TracerCtx *c, const Batch &B, cudaStream_t st) {
     const DevMesh &m = dev_mesh(h);
-    const int L = mb.n_levels, T = mb.n_tracers, ld = mb.ld;
-    if (T == 0 || L == 0) return GRIST_OK;
-    const size_t qs = (size_t)m.nC * ld, fs = (size_t)m.nE * ld;
-    // scratch: divF | qA | qB | FH | Rp | Rm
-    size_t b_div = qs * sizeof(double), b_q = (size_t)T * qs * sizeof(TQ), b_fh = (size_t)T * fs * sizeof(TC),
-           b_r = (size_t)T * qs * sizeof(TC);
-    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
-    size_t total = al(b_div) + 2 * al(b_q) + al(b_fh) + 2 * al(b_r);
-    char *s = (char *)scratch(h, 0, total);
-    if (!s) return GRIST_ENOMEM;
-    double *divF = (double *)s;
-    TQ *qA = (TQ *)(s + al(b_div));
-    TQ *qB = (TQ *)((char *)qA + al(b_q));
-    TC *FH = (TC *)((char *)qB + al(b_q));
-    TC *Rp = (TC *)((char *)FH + al(b_fh));
-    TC *Rm = (TC *)((char *)Rp + al(b_r));
-    TQ *q = (TQ *)mb.q;
     uint32_t *status = status_word(h);
-
-    const LevelDiv D = make_div((uint32_t)L);
-    const unsigned gC = grid_for((long long)m.nC * L, kBlock), gE = grid_for((long long)m.nE * L, kBlock);
-    const bool b1 = beta == 1.0;
-    const double dts[3] = {dt / 3.0, dt / 2.0, dt};
-
-    GRIST_LAUNCH(h, PN("k_div_mass"), st, k_div_mass<<<gC, kBlock, 0, st>>>(m, L, ld, D, mb.mass_flux, divF));
-    const TQ *in = q;
-    TQ *outs[2] = {qA, qB};
-    for (int s3 = 0; s3 < 3; s3++) {
-        if (b1)
-            GRIST_LAUNCH(h, PN("k_edge_flux"), st, k_edge_flux<TQ, TC, true><<<gE, kBlock, 0, st>>>(m, T, L, ld, D, in, qs, mb.mass_flux, (TC)beta, FH, fs));
-        else
-            GRIST_LAUNCH(h, PN("k_edge_flux"), st, k_edge_flux<TQ, TC, false><<<gE, kBlock, 0, st>>>(m, T, L, ld, D, in, qs, mb.mass_flux, (TC)beta, FH, fs));
-        if (s3 < 2) {
-            GRIST_LAUNCH(h, PN("k_stage_update"), st, k_stage_update<TQ, TC><<<gC, kBlock, 0, st>>>(m, T, L, ld, D, q, outs[s3], qs, FH, fs, mb.dpi, divF,
-                                                         dts[s3], status));
-            in = outs[s3];
-        } else if (!limiter) {
-            // final stage without limiter: each thread reads only its own q^n
-            GRIST_LAUNCH(h, PN("k_stage_update"), st, k_stage_update<TQ, TC><<<gC, kBlock, 0, st>>>(m, T, L, ld, D, q, q, qs, FH, fs, mb.dpi, divF, dt,
-                                                         status));
-        } else {
-            GRIST_LAUNCH(h, PN("k_fct_lowres"), st, k_fct_lowres<TQ, TC><<<gC, kBlock, 0, st>>>(m, T, L, ld, D, q, qs, mb.mass_flux, mb.dpi, divF, dt, qA));
-            GRIST_LAUNCH(h, PN("k_fct_ratios"), st, k_fct_ratios<TQ, TC><<<gC, kBlock, 0, st>>>(m, T, L, ld, D, q, qA, qs, FH, fs, mb.mass_flux, mb.dpi,
-                                                       divF, dt, Rp, Rm));
-            GRIST_LAUNCH(h, PN("k_fct_final"), st, k_fct_final<TQ, TC><<<gC, kBlock, 0, st>>>(m, T, L, ld, D, q, qB, qs, FH, fs, mb.mass_flux, mb.dpi,
-                                                      divF, dt, Rp, Rm, status));
-            GRIST_LAUNCH(h, PN("k_copy"), st, k_copy<TQ><<<1024, kBlock, 0, st>>>(qB, q, (size_t)T * qs));
+    const int block = c->tune.block;
+    const int dev = mesh_device(h);
+    if (B.nm == 0) return GRIST_OK;
+    if (c->tune.persistent) {
+        int per_sm = 0;
+        GRIST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tracer_persistent<TQ, TC>, block, 0));
+        if (per_sm < 1) return GRIST_EUNSUPPORTED;
+        const int grid = per_sm * sm_count(dev);
+        DevMesh mm = m;
+        Batch bb = B;
+        unsigned *bar = c->barrier;
+        GRIST_CUDA_TRY(cudaMemsetAsync(bar, 0, 3 * sizeof(unsigned), st));
+        void *args[] = {&mm, &bb, &bar, &status};
+        GRIST_LAUNCH(h, PN("k_tracer_persistent"), st,
+                     GRIST_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_tracer_persistent<TQ, TC>, grid, block,
+                                                                args, 0, st)));
+        return GRIST_OK;
+    }
+    static const char *names[] = {"k_tr_div", "k_tr_edge", "k_tr_update", "k_tr_edge", "k_tr_update",
+                                  "k_tr_edge", "k_tr_update", "k_tr_lowres", "k_tr_ratios", "k_tr_final",
+                                  "k_tr_copy"};
+    static const char *names_f[] = {"k_tr_div/mix", "k_tr_edge/mix", "k_tr_update/mix", "k_tr_edge/mix",
+                                    "k_tr_update/mix", "k_tr_edge/mix", "k_tr_update/mix", "k_tr_lowres/mix",
+                                    "k_tr_ratios/mix", "k_tr_final/mix", "k_tr_copy/mix"};
+    static const char *names_d[] = {"k_tr_div/fp64", "k_tr_edge/fp64", "k_tr_update/fp64", "k_tr_edge/fp64",
+                                    "k_tr_update/fp64", "k_tr_edge/fp64", "k_tr_update/fp64", "k_tr_lowres/fp64",
+                                    "k_tr_ratios/fp64", "k_tr_final/fp64", "k_tr_copy/fp64"};
+    (void)names;
+    const int sms = sm_count(dev);
+    for (int ph = P_DIV; ph <= P_COPY; ph++) {
+        if (!B.fct && ph > P_UPD2) break;
+        if (B.fct && ph == P_UPD2) continue;
+        const Space &S = (ph == P_DIV) ? B.D : (ph == P_EDGE0 || ph == P_EDGE1 || ph == P_EDGE2) ? B.E : B.C;
+        long long want = (long long)((S.total + block - 1) / block);
+        const long long cap = (long long)sms * 2048 * 32 / block;  // enough blocks to fill every SM many times
+        const unsigned grid = (unsigned)(want < 1 ? 1 : (want > cap ? cap : want));
+        const char *nm = sizeof(TC) == 4 ? names_f[ph] : names_d[ph];
+        switch (ph) {
+#define GRIST_PHASE_CASE(P_) \
+    case P_: GRIST_LAUNCH(h, nm, st, k_tracer_phase<TQ, TC, P_><<<grid, block, 0, st>>>(m, B, status)); break;
+            GRIST_PHASE_CASE(P_DIV)
+            GRIST_PHASE_CASE(P_EDGE0)
+            GRIST_PHASE_CASE(P_UPD0)
+            GRIST_PHASE_CASE(P_EDGE1)
+            GRIST_PHASE_CASE(P_UPD1)
+            GRIST_PHASE_CASE(P_EDGE2)
+            GRIST_PHASE_CASE(P_UPD2)
+            GRIST_PHASE_CASE(P_LOWRES)
+            GRIST_PHASE_CASE(P_RATIOS)
+            GRIST_PHASE_CASE(P_FINAL)
+            GRIST_PHASE_CASE(P_COPY)
+#undef GRIST_PHASE_CASE
         }
     }
     return cudaGetLastError() == cudaSuccess ? GRIST_OK : GRIST_ECUDA;
+}
+
+TracerCtx *ctx_of(grist_mesh_s *h) {
+    TracerCtx *&c = tracer_ctx(h);
+    if (!c) c = new TracerCtx();
+    return c;
+}
+
+template <typename TQ, typename TC>
+int tracer_step_t(grist_mesh_s *h, const grist_tracer_batch *b, double dt, cudaStream_t st) {
+    TracerCtx *c = ctx_of(h);
+    const DevMesh &m = dev_mesh(h);
+    HostPlan P;
+    int rc = plan_batch<TQ, TC>(m, b, c->tune.tracers_per_thread, P);
+    if (rc != GRIST_OK) return rc;
+    Batch B;
+    rc = upload_plan<TQ, TC>(h, c, P, b, dt, B, st);
+    if (rc != GRIST_OK) return rc;
+    if (!c->tune.use_graph) return enqueue_step<TQ, TC>(h, c, B, st);
+    // graph path: signature = batch contents + tuning + dt + stream
+    std::vector<unsigned long long> sig;
+    sig.push_back((unsigned long long)b->prec);
+    sig.push_back((unsigned long long)b->limiter);
+    unsigned long long u;
+    std::memcpy(&u, &b->beta_upwind, 8); sig.push_back(u);
+    std::memcpy(&u, &dt, 8); sig.push_back(u);
+    sig.push_back((unsigned long long)(uintptr_t)st);
+    sig.push_back(((unsigned long long)c->tune.block << 32) | (unsigned)c->tune.tracers_per_thread);
+    sig.push_back((unsigned long long)c->tune.persistent);
+    for (int i = 0; i < b->n_members; i++) {
+        const grist_tracer_member &mm = b->members[i];
+        sig.push_back((unsigned long long)(uintptr_t)mm.q);
+        sig.push_back((unsigned long long)(uintptr_t)mm.dpi);
+        sig.push_back((unsigned long long)(uintptr_t)mm.mass_flux);
+        sig.push_back(((unsigned long long)mm.n_levels << 40) | ((unsigned long long)mm.n_tracers << 20) |
+                      (unsigned long long)mm.ld);
+    }
+    sig.push_back((unsigned long long)(uintptr_t)c->dtab);
+    if (c->exec && sig == c->sig) {
+        GRIST_CUDA_TRY(cudaGraphLaunch(c->exec, st));
+        return GRIST_OK;
+    }
+    if (c->exec) { cudaGraphExecDestroy(c->exec); c->exec = nullptr; }
+    if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+    c->sig.clear();
+    cudaStreamCaptureStatus cs;
+    GRIST_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+    if (cs != cudaStreamCaptureStatusNone || st == nullptr) return enqueue_step<TQ, TC>(h, c, B, st);
+    if (c->graph_failed && sig == c->failed_sig) return enqueue_step<TQ, TC>(h, c, B, st);
+    GRIST_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    int erc = enqueue_step<TQ, TC>(h, c, B, st);
+    cudaGraph_t g = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(st, &g);
+    if (erc != GRIST_OK || ce != cudaSuccess || !g ||
+        cudaGraphInstantiate(&c->exec, g, 0) != cudaSuccess) {
+        // this batch cannot be captured (e.g. the cooperative launch): run
+        // it directly and remember not to retry the capture
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        c->exec = nullptr;
+        c->graph_failed = true;
+        c->failed_sig = sig;
+        return enqueue_step<TQ, TC>(h, c, B, st);
+    }
+    c->graph = g;
+    c->sig = sig;
+    GRIST_CUDA_TRY(cudaGraphLaunch(c->exec, st));
+    return GRIST_OK;
+}
+
+int validate(const grist_tracer_batch *b, double dt) {
+    if (!b || (b->n_members > 0 && !b->members) || b->n_members < 0) return GRIST_EINVAL;
+    if (b->n_members > GRIST_MAX_MEMBERS) return GRIST_EUNSUPPORTED;
+    if (!(dt > 0) || !std::isfinite(dt)) return GRIST_EINVAL;
+    if (b->prec != GRIST_FP64 && b->prec != GRIST_MIX && b->prec != GRIST_MIX_DBL_MASS) return GRIST_EINVAL;
+    if (!std::isfinite(b->beta_upwind)) return GRIST_EINVAL;
+    for (int i = 0; i < b->n_members; i++) {
+        const grist_tracer_member &mb = b->members[i];
+        if (mb.n_levels < 0 || mb.n_tracers < 0 || mb.n_levels > GRIST_MAXL || mb.ld < mb.n_levels) return GRIST_EINVAL;
+        if (mb.n_levels > 0 && mb.n_tracers > 0 && (!mb.q || !mb.dpi || !mb.mass_flux)) return GRIST_EINVAL;
+    }
+    return GRIST_OK;
+}
+
+int dispatch(grist_mesh_s *h, const grist_tracer_batch *b, double dt, cudaStream_t st) {
+    return b->prec == GRIST_FP64 ? tracer_step_t<double, double>(h, b, dt, st) : tracer_step_t<float, float>(h, b, dt, st);
+}
+
+int check_tuning(const grist_tracer_tuning *t) {
+    if (!t) return GRIST_EINVAL;
+    if (t->block < 64 || t->block > 1024 || t->block % 32) return GRIST_EINVAL;
+    if (t->tracers_per_thread < 1 || t->tracers_per_thread > 64) return GRIST_EINVAL;
+    if (t->persistent != 0 && t->persistent != 1) return GRIST_EINVAL;
+    if (t->use_graph != 0 && t->use_graph != 1) return GRIST_EINVAL;
+    return GRIST_OK;
 }
 
 }  // namespace
@@ -335,21 +762,128 @@ int member_step(grist_mesh_s *h, const grist_tracer_member &mb, int limiter, dou
 using namespace grist;
 
 extern "C" int grist_tracer_step(grist_mesh h, const grist_tracer_batch *b, double dt, void *stream) {
-    if (!h || !b || (b->n_members > 0 && !b->members) || b->n_members < 0) return GRIST_EINVAL;
-    if (!(dt > 0) || !std::isfinite(dt)) return GRIST_EINVAL;
-    if (b->prec != GRIST_FP64 && b->prec != GRIST_MIX && b->prec != GRIST_MIX_DBL_MASS) return GRIST_EINVAL;
-    for (int i = 0; i < b->n_members; i++) {
-        const grist_tracer_member &mb = b->members[i];
-        if (mb.n_levels < 0 || mb.n_tracers < 0 || mb.n_levels > GRIST_MAXL || mb.ld < mb.n_levels) return GRIST_EINVAL;
-        if (mb.n_levels > 0 && mb.n_tracers > 0 && (!mb.q || !mb.dpi || !mb.mass_flux)) return GRIST_EINVAL;
+    if (!h) return GRIST_EINVAL;
+    int rc = validate(b, dt);
+    if (rc != GRIST_OK) return rc;
+    if (cudaSetDevice(mesh_device(h)) != cudaSuccess) return GRIST_ECUDA;
+    return dispatch(h, b, dt, (cudaStream_t)stream);
+}
+
+extern "C" int grist_selftest_bounded_wait(grist_mesh h, int64_t spin_limit, void *stream) {
+    if (!h || spin_limit < 1 || spin_limit > 100000000) return GRIST_EINVAL;
+    if (cudaSetDevice(mesh_device(h)) != cudaSuccess) return GRIST_ECUDA;
+    TracerCtx *c = ctx_of(h);
+    if (!c->barrier) {
+        if (cudaMalloc(&c->barrier, 4 * sizeof(unsigned)) != cudaSuccess) return GRIST_ENOMEM;
+        GRIST_CUDA_TRY(cudaMemset(c->barrier, 0, 4 * sizeof(unsigned)));
     }
+    // word 3 is written by no kernel; word 2 is cleared first so the wait
+    // runs to its own limit
+    cudaStream_t st = (cudaStream_t)stream;
+    GRIST_CUDA_TRY(cudaMemsetAsync(c->barrier + 2, 0, sizeof(unsigned), st));
+    k_wait_selftest<<<1, 32, 0, st>>>(c->barrier + 3, c->barrier + 2, (long long)spin_limit, status_word(h));
+    return cudaGetLastError() == cudaSuccess ? GRIST_OK : GRIST_ECUDA;
+}
+
+extern "C" int grist_tracer_set_tuning(grist_mesh h, const grist_tracer_tuning *t) {
+    if (!h) return GRIST_EINVAL;
+    int rc = check_tuning(t);
+    if (rc != GRIST_OK) return rc;
+    TracerCtx *c = ctx_of(h);
+    c->tune = *t;
+    return GRIST_OK;
+}
+
+extern "C" int grist_tracer_get_tuning(grist_mesh h, grist_tracer_tuning *t) {
+    if (!h || !t) return GRIST_EINVAL;
+    *t = ctx_of(h)->tune;
+    return GRIST_OK;
+}
+
+extern "C" int grist_tracer_autotune(grist_mesh h, const grist_tracer_batch *b, double dt, int32_t steps,
+                                     void *stream, grist_tracer_tuning *best, double *best_ms) {
+    if (!h || !best || steps < 1) return GRIST_EINVAL;
+    int rc = validate(b, dt);
+    if (rc != GRIST_OK) return rc;
     if (cudaSetDevice(mesh_device(h)) != cudaSuccess) return GRIST_ECUDA;
     cudaStream_t st = (cudaStream_t)stream;
-    for (int i = 0; i < b->n_members; i++) {
-        int rc = b->prec == GRIST_FP64
-                     ? member_step<double, double>(h, b->members[i], b->limiter, b->beta_upwind, dt, st)
-                     : member_step<float, float>(h, b->members[i], b->limiter, b->beta_upwind, dt, st);
-        if (rc != GRIST_OK) return rc;
+    TracerCtx *c = ctx_of(h);
+    const grist_tracer_tuning saved = c->tune;
+    const DevMesh &m = dev_mesh(h);
+    // private copies of the tracers
+    std::vector<grist_tracer_member> mem(b->members, b->members + b->n_members);
+    std::vector<void *> copies;
+    const size_t es = b->prec == GRIST_FP64 ? 8 : 4;
+    int maxT = 1;
+    for (auto &mb : mem) {
+        if (mb.n_levels == 0 || mb.n_tracers == 0) continue;
+        maxT = mb.n_tracers > maxT ? mb.n_tracers : maxT;
+        const size_t bytes = (size_t)mb.n_tracers * m.nC * mb.ld * es;
+        void *p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            for (void *q : copies) cudaFree(q);
+            return GRIST_ENOMEM;
+        }
+        cudaMemcpyAsync(p, mb.q, bytes, cudaMemcpyDeviceToDevice, st);
+        copies.push_back(p);
+        mb.q = p;
     }
+    grist_tracer_batch bb = *b;
+    bb.members = mem.data();
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    auto time_cfg = [&](const grist_tracer_tuning &t, double *ms) -> int {
+        c->tune = t;
+        int r = dispatch(h, &bb, dt, st);  // warm-up (and graph capture)
+        if (r != GRIST_OK) return r;
+        cudaEventRecord(e0, st);
+        for (int i = 0; i < steps; i++) {
+            r = dispatch(h, &bb, dt, st);
+            if (r != GRIST_OK) return r;
+        }
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) return GRIST_ECUDA;
+        float f = 0.f;
+        cudaEventElapsedTime(&f, e0, e1);
+        *ms = f / steps;
+        return GRIST_OK;
+    };
+    grist_tracer_tuning bestt = saved;
+    double bestms = 1e300;
+    const int blocks[] = {128, 256, 512};
+    const int tpts[] = {1, 2, 4, 8};
+    for (int bl : blocks) {
+        for (int tp : tpts) {
+            if (tp > 1 && tp / 2 >= maxT) continue;
+            grist_tracer_tuning t{bl, tp, 0, 0};
+            double ms = 0;
+            if (time_cfg(t, &ms) == GRIST_OK && ms < bestms) { bestms = ms; bestt = t; }
+        }
+    }
+    for (int pers = 0; pers <= 1; pers++) {
+        for (int gr = 0; gr <= 1; gr++) {
+            if (pers == 0 && gr == 0) continue;
+            grist_tracer_tuning t = bestt;
+            t.persistent = pers;
+            t.use_graph = gr;
+            double ms = 0;
+            if (time_cfg(t, &ms) == GRIST_OK && ms < bestms) { bestms = ms; bestt = t; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamSynchronize(st);
+    for (void *q : copies) cudaFree(q);
+    // the cached graph refers to the freed copies: drop it
+    if (c->exec) { cudaGraphExecDestroy(c->exec); c->exec = nullptr; }
+    if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+    c->sig.clear();
+    c->tune = bestt;
+    *best = bestt;
+    if (best_ms) *best_ms = bestms;
+    uint32_t flags = 0;
+    cudaMemcpy(&flags, status_word(h), sizeof(uint32_t), cudaMemcpyDeviceToHost);
+    if (flags & GRIST_FLAG_TIMEOUT) return GRIST_ETIMEOUT;
     return GRIST_OK;
 }
