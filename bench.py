@@ -162,6 +162,8 @@ def make_state(torch, host, prec, device, nE, nC, L, T, nh):
     if nh:
         s["w"] = torch.from_numpy(host["w"]).to(device)
         s["phi"] = torch.from_numpy(host["phi"]).to(device)
+        s["p_nh"] = torch.zeros((nC, L), dtype=torch.float64, device=device)   # pressure carried by the state
+        s["p_nh_valid"] = False
     if T:
         s["q"] = torch.from_numpy(host["q"]).to(device=device, dtype=fdt)
         s["mass_flux_accum"] = torch.zeros((nE, L), dtype=torch.float64, device=device)
@@ -259,6 +261,7 @@ def gpu_arm(args, wl):
         def e2e_step():
             for k, v in pinned.items():
                 s[k].copy_(v, non_blocking=True)
+            s["p_nh_valid"] = False        # the state came from the host: pressure from the EOS
             step(mesh, s, P, wl, args.prec)
             for k, v in pinned.items():
                 v.copy_(s[k], non_blocking=True)
@@ -462,13 +465,18 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--mesh-level", type=int, default=None,
+                    help="override the workload's mesh level (small cases for profiling)")
     ap.add_argument("--cpu-level", type=int, default=8)
     ap.add_argument("--ref-level", type=int, default=7)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":
         args.warmup = 3
     os.environ.setdefault("GRIST_MESH_CACHE", "/tmp/grist_mesh_cache")
-    wl = WORKLOADS[args.workload]
+    wl = dict(WORKLOADS[args.workload])
+    if args.mesh_level is not None:
+        wl["level"] = args.mesh_level
+        wl["desc"] = wl["desc"].split(",")[0] + ", level-%d mesh (profiling case)" % args.mesh_level
     if args.impl == "reference":
         reference_arm(args, wl)
     else:

@@ -229,7 +229,14 @@ typedef struct {
  *               Sec. 2.3 "accumulated and averaged")
  *   accum_weight device double or NULL: incremented by 1 per step.
  *   dpi_start   [nC][ld] double or NULL: receives the layer mass dpi at
- *               the start of the step (the tracer solver's dpi^n). */
+ *               the start of the step (the tracer solver's dpi^n).
+ *   p_nh        [nC][ld] double or NULL (NH only): the non-hydrostatic
+ *               pressure of the state, Eq. 9.  If p_nh_valid is nonzero
+ *               on entry the step uses it as the t^n pressure instead of
+ *               evaluating the equation of state; on return it holds the
+ *               pressure of the new state and p_nh_valid is set to 1.  Set
+ *               p_nh_valid to 0 whenever dpi_theta or phi change outside
+ *               the step. */
 typedef struct {
     void *u;
     double *ps;
@@ -239,6 +246,8 @@ typedef struct {
     double *mass_flux_accum;
     double *accum_weight;
     double *dpi_start;
+    double *p_nh;
+    int32_t p_nh_valid;
 } grist_dycore_state;
 
 /* Hydrostatic step: WS-RK3, Mesinger forward-backward inside each stage

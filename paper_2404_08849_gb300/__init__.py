@@ -197,8 +197,12 @@ class Mesh:
         s.mass_flux_accum = _ptr(state.get("mass_flux_accum"))
         s.accum_weight = _ptr(state.get("accum_weight"))
         s.dpi_start = _ptr(state.get("dpi_start"))
+        s.p_nh = _ptr(state.get("p_nh"))
+        s.p_nh_valid = 1 if state.get("p_nh_valid") else 0
         _lib.check(fn, getattr(lib, fn)(self.handle, ctypes.byref(s), ctypes.byref(params.c), _prec(prec),
                                         float(dt), _stream_handle(stream)))
+        if state.get("p_nh") is not None:
+            state["p_nh_valid"] = bool(s.p_nh_valid)
 
     def dycore_step_hydro(self, state, params, dt, prec="fp64", stream=None):
         self._dycore("grist_dycore_step_hydro", state, params, prec, dt, stream)

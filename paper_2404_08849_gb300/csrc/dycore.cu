@@ -27,7 +27,6 @@ namespace grist {
 namespace {
 
 constexpr int kBlock = 256;
-constexpr int kMaxChunks = GRIST_MAXL / 32;
 constexpr int kNHMax = 128;  // levels supported by the column solver
 
 struct DyPar {
@@ -40,76 +39,80 @@ struct DyPar {
     const double *phis;   // [nC]  surface geopotential
 };
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
 __device__ __forceinline__ double rcp(double x) { return __drcp_rn(x); }
 
-// r^g for a ratio r close to 1: log(1+x) by its Mercator series
-// x - x^2/2 + ... + x^9/9 and exp(y) by its Taylor series to y^8/8!, both in
-// FP64; for |x| <= 2^-6 the truncation errors are below 1e-17 relative.
+// r^g for a ratio r close to 1 by the binomial series
+// (1 + x)^g = sum_n C(g, n) x^n, n = 0..9, Horner in FP64, with the binomial
+// coefficients C(g, n) = C(g, n-1) (g - n + 1)/n formed on the host; for
+// |x| <= 2^-6 and |g| < 2 the omitted terms are below 1e-17 relative.
 // Outside that range the library pow() is used.
-__device__ __forceinline__ double pow_near1(double r, double g) {
+struct Binom {
+    double c[10];
+};
+
+__device__ __forceinline__ double pow_near1(double r, double g, const Binom &B) {
     const double x = r - 1.0;
     if (fabs(x) > 0.015625) return pow(r, g);
-    double l = 1.0 / 9.0;
-    l = fma(l, x, -1.0 / 8.0);
-    l = fma(l, x, 1.0 / 7.0);
-    l = fma(l, x, -1.0 / 6.0);
-    l = fma(l, x, 1.0 / 5.0);
-    l = fma(l, x, -1.0 / 4.0);
-    l = fma(l, x, 1.0 / 3.0);
-    l = fma(l, x, -1.0 / 2.0);
-    l = fma(l, x, 1.0);
-    const double y = g * (l * x);
-    double e = 1.0 / 40320.0;
-    e = fma(e, y, 1.0 / 5040.0);
-    e = fma(e, y, 1.0 / 720.0);
-    e = fma(e, y, 1.0 / 120.0);
-    e = fma(e, y, 1.0 / 24.0);
-    e = fma(e, y, 1.0 / 6.0);
-    e = fma(e, y, 0.5);
-    e = fma(e, y, 1.0);
-    return fma(e, y, 1.0);
+    double s = B.c[9];
+#pragma unroll
+    for (int n = 8; n >= 0; n--) s = fma(s, x, B.c[n]);
+    return s;
+}
+
+Binom binomial(double g) {
+    Binom b;
+    b.c[0] = 1.0;
+    for (int n = 1; n < 10; n++) b.c[n] = b.c[n - 1] * (g - (n - 1)) / n;
+    return b;
 }
 
 // ---------------------------------------------------------------------------
 // Eq. 3: mass flux at edges F = dpi_e u, dpi_e = mean of the two cells'
-// layer mass = dB_k (ps1 + ps2 - 2 pi_top)/2.  The column factor is formed in
-// FP64 once per edge and the product in the mass-flux type.  The edge's
-// reciprocal 1/(ps1 + ps2 - 2 pi_top) is kept for the momentum equation.
-// In the final stage the flux is also accumulated for the tracer solver
-// (Sec. 2.3: single computed, saved double).
+// layer mass = dB_k (ps1 + ps2 - 2 pi_top)/2, one warp per edge with the
+// lanes over levels.  The column factor is formed in FP64 once per edge and
+// the product in the mass-flux type.  The warp also forms the edge's FP64
+// column sum sum_k F_k (a fixed butterfly, so both cells of the edge later
+// use the same value and the global mass change cancels to round-off) and
+// the reciprocal 1/(ps1 + ps2 - 2 pi_top) for the momentum equation.  In the
+// final stage the flux is accumulated for the tracer solver (Sec. 2.3:
+// single computed, saved double).
 template <class P>
-__global__ void k_mass_edge(DevMesh m, DyPar d, LevelDiv Dv, const double *__restrict__ ps_s,
+__global__ void k_mass_edge(DevMesh m, DyPar d, const double *__restrict__ ps_s,
                             const typename P::TU *__restrict__ u_s, typename P::TM *__restrict__ F,
-                            double *__restrict__ Facc, double *__restrict__ rsum_e) {
+                            double *__restrict__ Facc, double *__restrict__ rsum_e, double *__restrict__ Fcol) {
     using TM = typename P::TM;
-    uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= (uint32_t)m.nE * (uint32_t)d.L) return;
-    int e, k;
-    split_index(n, Dv, e, k);
+    const int e = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (e >= m.nE) return;
     const int2 c = ldg(m.coe + e);
-    const double sum = (ldg(ps_s + c.x) - d.pi_top) + (ldg(ps_s + c.y) - d.pi_top);
-    const size_t x = (size_t)e * d.ld + k;
-    const TM f = (TM)(0.5 * ldg(d.dB + k)) * (TM)sum * (TM)u_s[x];
-    F[x] = f;
-    if (Facc) Facc[x] += (double)f;
-    if (k == 0) rsum_e[e] = rcp(sum);
+    double sum = 0.0;
+    if (lane == 0) sum = (ldg(ps_s + c.x) - d.pi_top) + (ldg(ps_s + c.y) - d.pi_top);
+    sum = __shfl_sync(0xffffffffu, sum, 0);
+    const TM hs = (TM)(0.5 * sum);
+    double col = 0.0;
+    for (int k = lane; k < d.L; k += 32) {
+        const size_t x = (size_t)e * d.ld + k;
+        const TM f = (TM)ldg(d.dB + k) * hs * (TM)u_s[x];
+        F[x] = f;
+        col += (double)f;
+        if (Facc) Facc[x] += (double)f;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) col += __shfl_xor_sync(0xffffffffu, col, o);
+    if (lane == 0) {
+        Fcol[e] = col;
+        rsum_e[e] = rcp(sum);
+    }
 }
 
-// Eq. 3 column part, one warp per cell: layer divergence D_k, surface
-// pressure tendency from FP64 column sums of the edge fluxes (each edge's
-// column sum is formed identically by both of its cells, so the global sum
-// of the tendency cancels to round-off), vertical mass flux
-// M_{k+1/2} = -B_{k+1/2} dps/dt - sum_{l<=k} D_l by a warp scan, the stage
-// update of ps, theta = (dpi theta)/dpi of the stage input for Eq. 4, and
-// the column reciprocal 1/(ps - pi_top) of the stage input.
+// Eq. 3 column part, one warp per cell: layer divergence D_k (mass-flux
+// type), surface pressure tendency -sum_j s dv/A (column sum of edge j) in
+// FP64, vertical mass flux M_{k+1/2} = -B_{k+1/2} dps/dt - sum_{l<=k} D_l by
+// a warp scan, the stage update of ps, theta = (dpi theta)/dpi of the stage
+// input for Eq. 4, and the column reciprocal 1/(ps - pi_top).
 template <class P>
-__global__ void k_mass_col(DevMesh m, DyPar d, const typename P::TM *__restrict__ F, const double *__restrict__ ps_s,
+__global__ void k_mass_col(DevMesh m, DyPar d, const typename P::TM *__restrict__ F,
+                           const double *__restrict__ Fcol, const double *__restrict__ ps_s,
                            const double *__restrict__ ps_n, double *__restrict__ ps_out,
                            const double *__restrict__ th_s, typename P::TA *__restrict__ theta,
                            double *__restrict__ Mv, double dts, double *__restrict__ dpi_out,
@@ -121,61 +124,47 @@ __global__ void k_mass_col(DevMesh m, DyPar d, const typename P::TM *__restrict_
     if (i >= m.nC) return;
     int eidx[GRIST_MAXE];
     TM cw[GRIST_MAXE];
-    double cw64[GRIST_MAXE];
 #pragma unroll
     for (int j = 0; j < GRIST_MAXE; j++) {
         eidx[j] = ldg(m.eoc + i * 6 + j);
-        cw64[j] = ldg(m.cdiv + i * 6 + j);
-        cw[j] = (TM)cw64[j];
+        cw[j] = ldg(Coef<TM>::cdiv(m) + i * 6 + j);
     }
-    const double dps = ldg(ps_s + i) - d.pi_top;
-    const double rdps = rcp(dps);
-    double col[GRIST_MAXE] = {0, 0, 0, 0, 0, 0};
-    double Dk[kMaxChunks];
-    const int nch = (d.L + 31) >> 5;
-#pragma unroll
-    for (int ch = 0; ch < kMaxChunks; ch++) {
-        Dk[ch] = 0.0;
-        if (ch < nch) {
-            const int k = ch * 32 + lane;
-            if (k < d.L) {
-                TM s = 0;
-#pragma unroll
-                for (int j = 0; j < GRIST_MAXE; j++) {
-                    TM f = ldg(F + (size_t)eidx[j] * d.ld + k);
-                    s += cw[j] * f;
-                    col[j] += (double)f;
-                }
-                Dk[ch] = (double)s;
-                const size_t x = (size_t)i * d.ld + k;
-                theta[x] = (TA)(th_s[x] * ldg(d.rdB + k) * rdps);
-                if (dpi_out) dpi_out[x] = ldg(d.dB + k) * dps;
-            }
-        }
-    }
-    double pst = 0.0;
-#pragma unroll
-    for (int j = 0; j < GRIST_MAXE; j++) pst -= cw64[j] * warp_sum(col[j]);
+    // scalar column work on lane 0, broadcast
+    double pst = 0.0, dps = 0.0, rdps = 0.0;
     if (lane == 0) {
+#pragma unroll
+        for (int j = 0; j < GRIST_MAXE; j++) pst -= ldg(m.cdiv + i * 6 + j) * ldg(Fcol + eidx[j]);
+        dps = ldg(ps_s + i) - d.pi_top;
+        rdps = rcp(dps);
         ps_out[i] = ps_n[i] + dts * pst;
         rdps_out[i] = rdps;
         Mv[(size_t)i * d.ldi] = 0.0;
         Mv[(size_t)i * d.ldi + d.L] = 0.0;
     }
+    pst = __shfl_sync(0xffffffffu, pst, 0);
+    dps = __shfl_sync(0xffffffffu, dps, 0);
+    rdps = __shfl_sync(0xffffffffu, rdps, 0);
     double run = 0.0;
+    const int nch = (d.L + 31) >> 5;
+    for (int ch = 0; ch < nch; ch++) {
+        const int k = ch * 32 + lane;
+        TM s = 0;
+        if (k < d.L) {
 #pragma unroll
-    for (int ch = 0; ch < kMaxChunks; ch++) {
-        if (ch < nch) {
-            double v = Dk[ch];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                double t = __shfl_up_sync(0xffffffffu, v, o);
-                if (lane >= o) v += t;
-            }
-            const int k = ch * 32 + lane;
-            if (k < d.L - 1) Mv[(size_t)i * d.ldi + k + 1] = -ldg(d.B + k + 1) * pst - (run + v);
-            run += __shfl_sync(0xffffffffu, v, 31);
+            for (int j = 0; j < GRIST_MAXE; j++) s += cw[j] * ldg(F + (size_t)eidx[j] * d.ld + k);
+            const size_t x = (size_t)i * d.ld + k;
+            theta[x] = (TA)(th_s[x] * ldg(d.rdB + k) * rdps);
+            if (dpi_out) dpi_out[x] = ldg(d.dB + k) * dps;
         }
+        // inclusive prefix of D over the chunk (FP64), carried across chunks
+        double v = (double)s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double t = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += t;
+        }
+        if (k < d.L - 1) Mv[(size_t)i * d.ldi + k + 1] = -ldg(d.B + k + 1) * pst - (run + v);
+        run += __shfl_sync(0xffffffffu, v, 31);
     }
 }
 
@@ -467,7 +456,7 @@ __global__ void __launch_bounds__(128) k_nh_solve(DevMesh m, DyPar d, const doub
                                                   const double *p_r, const double *__restrict__ ps, double dts,
                                                   double *__restrict__ w_out, double *__restrict__ phi_out, double *p,
                                                   double *__restrict__ al, double *__restrict__ phl,
-                                                  double *__restrict__ dpp) {
+                                                  double *__restrict__ dpp, Binom bg_pos, Binom bg_neg) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m.nC) return;
     const int L = d.L;
@@ -480,7 +469,7 @@ __global__ void __launch_bounds__(128) k_nh_solve(DevMesh m, DyPar d, const doub
     double ftop = phst[ci], fbot = phst[ci + 1];
     double rtop = phi_r[ci], rbot = phi_r[ci + 1];
     double rdf0 = rcp(ftop - fbot);
-    double p0s = p_r[cl] * pow_near1(th[cl] * rcp(th_r[cl]) * ((rtop - rbot) * rdf0), d.gamma);
+    double p0s = p_r[cl] * pow_near1(th[cl] * rcp(th_r[cl]) * ((rtop - rbot) * rdf0), d.gamma, bg_pos);
     pst[0] = p0s;
     rdf[0] = rdf0;
     double pst_prev = p0s, C_prev = gbg * p0s * rdf0;
@@ -490,7 +479,8 @@ __global__ void __launch_bounds__(128) k_nh_solve(DevMesh m, DyPar d, const doub
         rtop = rbot;
         rbot = phi_r[ci + j + 1];
         const double rdfj = rcp(ftop - fbot);
-        const double pstj = p_r[cl + j] * pow_near1(th[cl + j] * rcp(th_r[cl + j]) * ((rtop - rbot) * rdfj), d.gamma);
+        const double pstj =
+            p_r[cl + j] * pow_near1(th[cl + j] * rcp(th_r[cl + j]) * ((rtop - rbot) * rdfj), d.gamma, bg_pos);
         pst[j] = pstj;
         rdf[j] = rdfj;
         const double C = gbg * pstj * rdfj;
@@ -527,7 +517,7 @@ __global__ void __launch_bounds__(128) k_nh_solve(DevMesh m, DyPar d, const doub
         const double w_bot = (k + 1 < L) ? w_out[ci + k + 1] : 0.0;
         const double phi_bot = (k + 1 < L) ? fma(bg, w_bot, phst[ci + k + 1]) : ldg(d.phis + i);
         phi_out[ci + k + 1] = phi_bot;
-        const double pk = pst[k] * pow_near1(fma(bg * (w_top - w_bot), rdf[k], 1.0), -d.gamma);
+        const double pk = pst[k] * pow_near1(fma(bg * (w_top - w_bot), rdf[k], 1.0), -d.gamma, bg_neg);
         p[cl + k] = pk;
         al[cl + k] = (phi_top - phi_bot) * (ldg(d.rdB + k) * rdps);
         phl[cl + k] = 0.5 * (phi_top + phi_bot);
@@ -564,7 +554,8 @@ int dycore_step(grist_mesh_s *h, grist_dycore_state *S, const grist_dycore_param
     const size_t o_vg = take(sizeof(double) * nvg);
     const size_t o_uA = take(nEL * sizeof(TU)), o_uB = take(nEL * sizeof(TU));
     const size_t o_psA = take(m.nC * 8), o_psB = take(m.nC * 8), o_psN = take(m.nC * 8);
-    const size_t o_rdps = take(m.nC * 8), o_rsum = take(m.nE * 8), o_rdpv = take(m.nV * 8);
+    const size_t o_rdps = take(m.nC * 8), o_rsum = take(m.nE * 8), o_rdpv = take(m.nV * 8),
+                 o_fcol = take(m.nE * 8);
     const size_t o_thA = take(nCL * 8), o_thB = take(nCL * 8);
     const size_t o_F = take(nEL * sizeof(TM)), o_M = take(nCI * 8);
     const size_t o_theta = take(nCL * sizeof(TA)), o_Fth = take(nEL * sizeof(TA));
@@ -599,7 +590,8 @@ int dycore_step(grist_mesh_s *h, grist_dycore_state *S, const grist_dycore_param
 
     TU *uA = (TU *)(s + o_uA), *uB = (TU *)(s + o_uB);
     double *psA = (double *)(s + o_psA), *psB = (double *)(s + o_psB), *psN = (double *)(s + o_psN);
-    double *rdps = (double *)(s + o_rdps), *rsum = (double *)(s + o_rsum), *rdpv = (double *)(s + o_rdpv);
+    double *rdps = (double *)(s + o_rdps), *rsum = (double *)(s + o_rsum), *rdpv = (double *)(s + o_rdpv),
+           *fcol = (double *)(s + o_fcol);
     double *thA = (double *)(s + o_thA), *thB = (double *)(s + o_thB);
     TM *F = (TM *)(s + o_F);
     double *Mv = (double *)(s + o_M);
@@ -618,11 +610,23 @@ int dycore_step(grist_mesh_s *h, grist_dycore_state *S, const grist_dycore_param
     const unsigned gC = grid_for((long long)m.nC * L, kBlock), gE = grid_for((long long)m.nE * L, kBlock),
                    gV = grid_for((long long)m.nV * L, kBlock), gW = grid_for((long long)m.nC * 32, kBlock),
                    gI = grid_for((long long)m.nC * (L + 1), kBlock), gCol = grid_for(m.nC, 128),
-                   gVx = grid_for(m.nV, kBlock);
+                   gVx = grid_for(m.nV, kBlock), gWE = grid_for((long long)m.nE * 32, kBlock);
     const double dts[3] = {dt / 3.0, dt / 2.0, dt};
 
     GRIST_CUDA_TRY(cudaMemcpyAsync(psN, S->ps, m.nC * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    if (NH) GRIST_LAUNCH(h, PN("k_eos"), st, k_eos<<<gC, kBlock, 0, st>>>(m, d, DL, S->dpi_theta, S->phi, pn));
+    // t^n pressure: carried in the state when valid, else from the EOS
+    const double *p_n = pn;
+    if (NH) {
+        if (S->p_nh && S->p_nh_valid) {
+            p_n = S->p_nh;
+        } else {
+            double *dst = S->p_nh ? S->p_nh : pn;
+            GRIST_LAUNCH(h, PN("k_eos"), st, k_eos<<<gC, kBlock, 0, st>>>(m, d, DL, S->dpi_theta, S->phi, dst));
+            p_n = dst;
+        }
+    }
+    const Binom bpos = binomial(d.gamma), bneg = binomial(-d.gamma);
+    double *p_outs[3] = {p, p, (NH && S->p_nh) ? S->p_nh : p};
 
     const TU *u_in = u;
     const double *ps_in = psN, *th_in = S->dpi_theta, *w_in = S->w, *phi_in = S->phi;
@@ -633,23 +637,23 @@ int dycore_step(grist_mesh_s *h, grist_dycore_state *S, const grist_dycore_param
     double *phi_outs[3] = {phA, phB, S->phi};
     for (int s3 = 0; s3 < 3; s3++) {
         const double h3 = dts[s3];
-        GRIST_LAUNCH(h, PN("k_mass_edge"), st, k_mass_edge<P><<<gE, kBlock, 0, st>>>(
-            m, d, DL, ps_in, u_in, F, s3 == 2 ? S->mass_flux_accum : nullptr, rsum));
+        GRIST_LAUNCH(h, PN("k_mass_edge"), st, k_mass_edge<P><<<gWE, kBlock, 0, st>>>(
+            m, d, ps_in, u_in, F, s3 == 2 ? S->mass_flux_accum : nullptr, rsum, fcol));
         GRIST_LAUNCH(h, PN("k_mass_col"), st, k_mass_col<P><<<gW, kBlock, 0, st>>>(
-            m, d, F, ps_in, psN, ps_outs[s3], th_in, theta, Mv, h3, s3 == 0 ? S->dpi_start : nullptr, rdps));
+            m, d, F, fcol, ps_in, psN, ps_outs[s3], th_in, theta, Mv, h3, s3 == 0 ? S->dpi_start : nullptr, rdps));
         GRIST_LAUNCH(h, PN("k_theta_flux"), st, k_theta_flux<P><<<gE, kBlock, 0, st>>>(m, d, DL, F, theta, Fth));
         GRIST_LAUNCH(h, PN("k_theta_update"), st, k_theta_update<P><<<gC, kBlock, 0, st>>>(
             m, d, DL, Fth, theta, Mv, S->dpi_theta, th_outs[s3], h3));
         if (NH) {
             if (s3 == 0)
                 GRIST_LAUNCH(h, PN("k_nh_explicit"), st, k_nh_explicit<P, true><<<gI, kBlock, 0, st>>>(
-                    m, d, DI, u_in, rdps, Mv, w_in, phi_in, S->w, S->phi, pn, fwn, wst, phst, h3));
+                    m, d, DI, u_in, rdps, Mv, w_in, phi_in, S->w, S->phi, p_n, fwn, wst, phst, h3));
             else
                 GRIST_LAUNCH(h, PN("k_nh_explicit"), st, k_nh_explicit<P, false><<<gI, kBlock, 0, st>>>(
-                    m, d, DI, u_in, rdps, Mv, w_in, phi_in, S->w, S->phi, pn, fwn, wst, phst, h3));
+                    m, d, DI, u_in, rdps, Mv, w_in, phi_in, S->w, S->phi, p_n, fwn, wst, phst, h3));
             GRIST_LAUNCH(h, PN("k_nh_solve"), st, k_nh_solve<<<gCol, 128, 0, st>>>(
-                m, d, wst, phst, th_outs[s3], th_in, phi_in, s3 == 0 ? pn : p, ps_outs[s3], h3, w_outs[s3],
-                phi_outs[s3], p, alp, phl, dpp));
+                m, d, wst, phst, th_outs[s3], th_in, phi_in, s3 == 0 ? p_n : p, ps_outs[s3], h3, w_outs[s3],
+                phi_outs[s3], p_outs[s3], alp, phl, dpp, bpos, bneg));
         } else {
             GRIST_LAUNCH(h, PN("k_hydro_diag"), st, k_hydro_diag<<<gW, kBlock, 0, st>>>(
                 m, d, ps_outs[s3], th_outs[s3], p, alp, phl));
@@ -659,7 +663,7 @@ int dycore_step(grist_mesh_s *h, grist_dycore_state *S, const grist_dycore_param
         GRIST_LAUNCH(h, PN("k_ke"), st, k_ke<P><<<gC, kBlock, 0, st>>>(m, d, DL, u_in, K));
         GRIST_LAUNCH(h, PN("k_pv_edge"), st, k_pv_edge<P><<<gE, kBlock, 0, st>>>(m, d, DL, qv, qe));
         GRIST_LAUNCH(h, PN("k_momentum"), st, k_momentum<P, NH><<<gE, kBlock, 0, st>>>(
-            m, d, DL, u_in, u, u_outs[s3], F, qe, K, Mv, rsum, p, alp, phl, dpp, h3, status));
+            m, d, DL, u_in, u, u_outs[s3], F, qe, K, Mv, rsum, p_outs[s3], alp, phl, dpp, h3, status));
         u_in = u_outs[s3];
         ps_in = ps_outs[s3];
         th_in = th_outs[s3];
@@ -667,7 +671,9 @@ int dycore_step(grist_mesh_s *h, grist_dycore_state *S, const grist_dycore_param
         phi_in = phi_outs[s3];
     }
     if (S->accum_weight) GRIST_LAUNCH(h, PN("k_add_scalar"), st, k_add_scalar<<<1, 32, 0, st>>>(S->accum_weight, 1.0));
-    return cudaGetLastError() == cudaSuccess ? GRIST_OK : GRIST_ECUDA;
+    if (cudaGetLastError() != cudaSuccess) return GRIST_ECUDA;
+    if (NH && S->p_nh) S->p_nh_valid = 1;
+    return GRIST_OK;
 }
 
 int check(grist_mesh h, grist_dycore_state *S, const grist_dycore_params *prm, grist_precision prec, double dt,

@@ -12,8 +12,10 @@ Tolerances
   rounding only through their tendency: a mass flux dpi*u ~ 1e5 Pa m/s per
   level rounded at 6e-8, summed over ~30 levels and 6 edges with
   dv/A ~ 1e-5 1/m, gives ~1e-6 Pa/s, i.e. ~6e-9 of ps after a 300 s step;
-  the theta flux (theta ~ 300 K times that flux) does the same to
-  dpi_theta.  Bound 1e-7 for both (measured: 2.6e-9 and 2.4e-8).
+  bound 1e-7 (measured 2.6e-9).  dpi_theta and phi take FP32 theta (rounded
+  at eps32 ~ 6e-8) through ~8 flux terms per cell-level (6 horizontal, 2
+  vertical), each up to the layer content times a Courant number ~0.5:
+  bound 5e-7 (measured up to 1.5e-7 on the level-9 mesh).
 Sizes span several CTAs and a ragged level count with padding (ld > L).
 """
 import math
@@ -164,7 +166,7 @@ def test_hydro_mix_accuracy(dev_meshes, prec):
     got = run_dycore(mesh, st, L, 300.0, nh=False, prec=prec)
     assert _rel(got["u"], ref["u"]) <= 2e-5
     assert _rel(got["ps"], ref["ps"]) <= 1e-7
-    assert _rel(got["dpi_theta"], ref["dpi_theta"]) <= 1e-7
+    assert _rel(got["dpi_theta"], ref["dpi_theta"]) <= 5e-7
 
 
 def test_nh_fp64_parity(dev_meshes):
@@ -192,7 +194,7 @@ def test_nh_mix_accuracy(dev_meshes, prec):
     got = run_dycore(mesh, st, L, 120.0, nh=True, prec=prec)
     assert _rel(got["u"], ref["u"]) <= 2e-5
     assert _rel(got["ps"], ref["ps"]) <= 1e-7
-    assert _rel(got["dpi_theta"], ref["dpi_theta"]) <= 1e-7
+    assert _rel(got["dpi_theta"], ref["dpi_theta"]) <= 5e-7
     assert _rel(got["phi"], ref["phi"]) <= 1e-9
     assert _rel(got["w"], ref["w"]) <= 1e-3
 
