@@ -182,19 +182,25 @@ int grist_tracer_step(grist_mesh mesh, const grist_tracer_batch *batch, double d
  *                       the first call with a given batch (same buffers,
  *                       sizes, dt, precision, limiter, beta) and replay it
  *                       afterwards; the first call must not itself be
- *                       inside a stream capture. */
+ *                       inside a stream capture.
+ *   fused               1 = RK stages without the limiter run as one tiled
+ *                       kernel each (edge fluxes of a tile of cells kept in
+ *                       shared memory, never written to global memory);
+ *                       ignored when persistent = 1. */
 typedef struct {
-    int32_t block, tracers_per_thread, persistent, use_graph;
+    int32_t block, tracers_per_thread, persistent, use_graph, fused;
 } grist_tracer_tuning;
 
 /* Set / get the tuning used by later grist_tracer_step calls on the mesh
- * (default: block 256, tracers_per_thread 4, persistent 0, use_graph 0).
+ * (default: block 256, tracers_per_thread 4, persistent 0, use_graph 0,
+ * fused 0).
  * GRIST_EINVAL for out-of-range values. */
 int grist_tracer_set_tuning(grist_mesh mesh, const grist_tracer_tuning *tuning);
 int grist_tracer_get_tuning(grist_mesh mesh, grist_tracer_tuning *tuning);
 
 /* Autotuner: time candidate tunings (block sizes, tracers per thread,
- * per-phase vs persistent launch, graph on/off) on `steps` tracer steps of
+ * fused tiles on/off, per-phase vs persistent launch, graph on/off) on
+ * `steps` tracer steps of
  * the given batch, keep the fastest as the mesh's tuning and return it in
  * *best (and its mean step time in milliseconds in *best_ms, may be NULL).
  * Works on private copies of the tracer arrays (allocates them), so the

@@ -143,15 +143,16 @@ class Mesh:
         _lib.check("grist_tracer_step", lib.grist_tracer_step(self.handle, ctypes.byref(b), float(dt),
                                                               _stream_handle(stream)))
 
-    def set_tracer_tuning(self, block=256, tracers_per_thread=4, persistent=False, use_graph=False):
-        t = _lib.TracerTuning(int(block), int(tracers_per_thread), int(bool(persistent)), int(bool(use_graph)))
+    def set_tracer_tuning(self, block=256, tracers_per_thread=4, persistent=False, use_graph=False, fused=False):
+        t = _lib.TracerTuning(int(block), int(tracers_per_thread), int(bool(persistent)), int(bool(use_graph)),
+                              int(bool(fused)))
         _lib.check("grist_tracer_set_tuning", _lib.load().grist_tracer_set_tuning(self.handle, ctypes.byref(t)))
 
     def tracer_tuning(self):
         t = _lib.TracerTuning()
         _lib.check("grist_tracer_get_tuning", _lib.load().grist_tracer_get_tuning(self.handle, ctypes.byref(t)))
         return {"block": t.block, "tracers_per_thread": t.tracers_per_thread, "persistent": bool(t.persistent),
-                "use_graph": bool(t.use_graph)}
+                "use_graph": bool(t.use_graph), "fused": bool(t.fused)}
 
     def autotune_tracer(self, members, dt, prec="mix", limiter=True, beta=1.0, steps=3, stream=None,
                         cache_path=None, cache_key=None):

@@ -41,7 +41,7 @@ class TracerBatch(ctypes.Structure):
 
 
 class TracerTuning(ctypes.Structure):
-    _fields_ = [("block", _I), ("tracers_per_thread", _I), ("persistent", _I), ("use_graph", _I)]
+    _fields_ = [("block", _I), ("tracers_per_thread", _I), ("persistent", _I), ("use_graph", _I), ("fused", _I)]
 
 
 class DycoreParams(ctypes.Structure):

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "grist.h"
 
 #define GRIST_MAXE 6
@@ -20,7 +22,7 @@ namespace grist {
 // fixed trip count without branches.  Geometric factors are folded into
 // the coefficient arrays once at mesh creation:
 //   cdiv[i][j]  = s(e,i) dv_e / A_i        (cell divergence)
-//   kec[i][j]   = dc_e dv_e / (4 A_i)      (cell kinetic energy)
+//   kec2[i][j]  = dc_e dv_e / (2 A_i)      (twice the cell kinetic energy)
 //   ccurl[v][j] = t(e,v) dc_e / A_v        (vertex circulation)
 //   ckite[v][j] = kite(i,v) / A_v          (cell -> vertex remap)
 //   wpv[e][j]   = w(e,e') dv_e' / dc_e     (TRiSK tangential flux)
@@ -33,12 +35,13 @@ struct DevMesh {
     const int32_t *coc;   // [nC][6]  pad: i itself
     const double *cdiv;   // [nC][6]
     const float *cdiv_f;
-    const double *kec;    // [nC][6]
+    const double *kec2;   // [nC][6] dc dv / (2 A): twice the kinetic-energy weight
     const double *area;   // [nC]
     // edges
     const int2 *coe;      // [nE] (c1, c2)
     const int2 *voe;      // [nE] (v1, v2)
     const double *rdc;    // [nE] 1/dc
+    const double *hrdc;   // [nE] -1/(2 dc)
     const double *dc2;    // [nE] dc^2/12
     const float *dc2_f;
     const int32_t *d2i;   // [nE][2][7] pad: centre cell
@@ -121,6 +124,16 @@ int mesh_device(grist_mesh_s *m);
 // needs more than the current size.  slot separates independent users.
 void *scratch(grist_mesh_s *m, int slot, size_t bytes);
 uint32_t *status_word(grist_mesh_s *m);
+
+// Host copies of the packed connectivity (internal numbering), kept for
+// building derived tables (tracer tiles) after creation.
+struct HostTables {
+    int nC, nE, nV;
+    std::vector<int32_t> eoc;   // [nC][6]
+    std::vector<int2> coe;      // [nE]
+    std::vector<int32_t> d2i;   // [nE][2][7]
+};
+const HostTables &host_tables(grist_mesh_s *m);
 
 // Tracer-step context (tuning, device tables, graph cache) kept in the
 // handle; defined in tracer.cu.

@@ -36,10 +36,42 @@ struct DyPar {
     const double *dB;     // [L]   layer thickness in B
     const double *rdB;    // [L]   1/dB
     const double *rdBi;   // [L+1] 2/(dB[j-1] + dB[j]) at interior interfaces j
+    const float *dBf;     // [L]   dB rounded to single precision
     const double *phis;   // [nC]  surface geopotential
 };
 
 __device__ __forceinline__ double rcp(double x) { return __drcp_rn(x); }
+
+// Compensated single-precision accumulation (Knuth's TwoSum): a value is
+// hi + lo with |lo| <= ulp(hi)/2, so a sum of FP32 terms carries about 48
+// significant bits - as accurate as FP64 accumulation of the same FP32
+// terms - while running on the FP32 pipe (FP64 instructions, conversions
+// included, are the scarce resource on this GPU).
+struct F2 {
+    float hi, lo;
+};
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    const float e = (a.hi - (s - bb)) + (b.hi - bb);
+    const float lo = e + a.lo + b.lo;
+    const float hi = s + lo;
+    return F2{hi, lo - (hi - s)};
+}
+__device__ __forceinline__ F2 f2_shfl_xor(F2 v, int o) {
+    return F2{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+}
+__device__ __forceinline__ F2 f2_shfl_up(F2 v, int o) {
+    return F2{__shfl_up_sync(0xffffffffu, v.hi, o), __shfl_up_sync(0xffffffffu, v.lo, o)};
+}
+
+// Column sum of a level-indexed value over the warp's lanes: FP64 terms
+// are added in FP64; FP32 terms in compensated FP32, converted once.
+__device__ __forceinline__ double col_reduce(double part) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    return part;
+}
 
 // r^g for a ratio r close to 1 by the binomial series
 // (1 + x)^g = sum_n C(g, n) x^n, n = 0..9, Horner in FP64, with the binomial
@@ -84,24 +116,37 @@ __global__ void k_mass_edge(DevMesh m, DyPar d, const double *__restrict__ ps_s,
     const int e = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (e >= m.nE) return;
-    const int2 c = ldg(m.coe + e);
-    double sum = 0.0;
-    if (lane == 0) sum = (ldg(ps_s + c.x) - d.pi_top) + (ldg(ps_s + c.y) - d.pi_top);
-    sum = __shfl_sync(0xffffffffu, sum, 0);
-    const TM hs = (TM)(0.5 * sum);
-    double col = 0.0;
-    for (int k = lane; k < d.L; k += 32) {
-        const size_t x = (size_t)e * d.ld + k;
-        const TM f = (TM)ldg(d.dB + k) * hs * (TM)u_s[x];
-        F[x] = f;
-        col += (double)f;
-        if (Facc) Facc[x] += (double)f;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) col += __shfl_xor_sync(0xffffffffu, col, o);
+    TM hs = 0;
     if (lane == 0) {
-        Fcol[e] = col;
-        rsum_e[e] = rcp(sum);
+        const int2 c = ldg(m.coe + e);
+        const double sum = (ldg(ps_s + c.x) - d.pi_top) + (ldg(ps_s + c.y) - d.pi_top);
+        hs = (TM)(0.5 * sum);
+        rsum_e[e] = 0.5 * rcp(sum);   // 1 / (2 dpi_e / dB)
+    }
+    hs = __shfl_sync(0xffffffffu, hs, 0);
+    if (sizeof(TM) == 8) {
+        double col = 0.0;
+        for (int k = lane; k < d.L; k += 32) {
+            const size_t x = (size_t)e * d.ld + k;
+            const TM f = (TM)ldg(d.dB + k) * hs * (TM)u_s[x];
+            F[x] = f;
+            col += (double)f;
+            if (Facc) Facc[x] += (double)f;
+        }
+        col = col_reduce(col);
+        if (lane == 0) Fcol[e] = col;
+    } else {
+        F2 col{0.f, 0.f};
+        for (int k = lane; k < d.L; k += 32) {
+            const size_t x = (size_t)e * d.ld + k;
+            const TM f = ldg(d.dBf + k) * hs * (TM)u_s[x];
+            F[x] = f;
+            col = f2_add(col, F2{(float)f, 0.f});
+            if (Facc) Facc[x] += (double)f;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) col = f2_add(col, f2_shfl_xor(col, o));
+        if (lane == 0) Fcol[e] = (double)col.hi + (double)col.lo;
     }
 }
 
@@ -116,7 +161,7 @@ __global__ void k_mass_col(DevMesh m, DyPar d, const typename P::TM *__restrict_
                            const double *__restrict__ ps_n, double *__restrict__ ps_out,
                            const double *__restrict__ th_s, typename P::TA *__restrict__ theta,
                            double *__restrict__ Mv, double dts, double *__restrict__ dpi_out,
-                           double *__restrict__ rdps_out) {
+                           double *__restrict__ rdps_out, double *__restrict__ rth_out) {
     using TM = typename P::TM;
     using TA = typename P::TA;
     const int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -155,16 +200,31 @@ __global__ void k_mass_col(DevMesh m, DyPar d, const typename P::TM *__restrict_
             const size_t x = (size_t)i * d.ld + k;
             theta[x] = (TA)(th_s[x] * ldg(d.rdB + k) * rdps);
             if (dpi_out) dpi_out[x] = ldg(d.dB + k) * dps;
+            if (rth_out) rth_out[x] = rcp(th_s[x]);
         }
-        // inclusive prefix of D over the chunk (FP64), carried across chunks
-        double v = (double)s;
+        // inclusive prefix of D over the chunk, carried across chunks: FP64
+        // terms in FP64, FP32 terms in compensated FP32
+        if (sizeof(TM) == 8) {
+            double v = (double)s;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const double t = __shfl_up_sync(0xffffffffu, v, o);
-            if (lane >= o) v += t;
+            for (int o = 1; o < 32; o <<= 1) {
+                const double t = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += t;
+            }
+            if (k < d.L - 1) Mv[(size_t)i * d.ldi + k + 1] = -ldg(d.B + k + 1) * pst - (run + v);
+            run += __shfl_sync(0xffffffffu, v, 31);
+        } else {
+            F2 v{(float)s, 0.f};
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const F2 t = f2_shfl_up(v, o);
+                if (lane >= o) v = f2_add(v, t);
+            }
+            if (k < d.L - 1)
+                Mv[(size_t)i * d.ldi + k + 1] = -ldg(d.B + k + 1) * pst - (run + ((double)v.hi + (double)v.lo));
+            const F2 last{__shfl_sync(0xffffffffu, v.hi, 31), __shfl_sync(0xffffffffu, v.lo, 31)};
+            run += (double)last.hi + (double)last.lo;
         }
-        if (k < d.L - 1) Mv[(size_t)i * d.ldi + k + 1] = -ldg(d.B + k + 1) * pst - (run + v);
-        run += __shfl_sync(0xffffffffu, v, 31);
     }
 }
 
@@ -283,7 +343,8 @@ __global__ void k_vort(DevMesh m, DyPar d, LevelDiv Dv, const typename P::TU *__
     qv[(size_t)v * d.ld + k] = (TA)(((double)z + ldg(m.fv + v)) * (ldg(d.rdB + k) * ldg(rdpv + v)));
 }
 
-// Cell kinetic energy K = sum (dc dv / 4A) u^2 (FP64: boxed term of Eq. 5).
+// Cell kinetic energy, stored doubled: 2K = sum (dc dv / 2A) u^2 (FP64:
+// boxed term of Eq. 5).
 template <class P>
 __global__ void k_ke(DevMesh m, DyPar d, LevelDiv Dv, const typename P::TU *__restrict__ u, double *__restrict__ K) {
     uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
@@ -294,7 +355,7 @@ __global__ void k_ke(DevMesh m, DyPar d, LevelDiv Dv, const typename P::TU *__re
 #pragma unroll
     for (int j = 0; j < GRIST_MAXE; j++) {
         double ue = (double)ldg(u + (size_t)ldg(m.eoc + i * 6 + j) * d.ld + k);
-        s += ldg(m.kec + i * 6 + j) * ue * ue;
+        s += ldg(m.kec2 + i * 6 + j) * ue * ue;
     }
     K[(size_t)i * d.ld + k] = s;
 }
@@ -352,13 +413,15 @@ __global__ void k_momentum(DevMesh m, DyPar d, LevelDiv Dv, const typename P::TU
     if (k > 0)
         va = fma(ldg(Mv + (size_t)c.x * d.ldi + k) + ldg(Mv + (size_t)c.y * d.ldi + k), uk - (double)ldg(u_s + x - 1),
                  va);
-    // [M sums](du) / (2 dpi_e) with dpi_e = dB (sum)/2 and M_e = (M1 + M2)/2
-    va *= 0.5 * ldg(d.rdB + k) * ldg(rsum_e + e);
+    // [M sums](du) / (2 dpi_e) with dpi_e = dB (sum)/2, M_e = (M1 + M2)/2;
+    // rsum_e holds 1/(2 sum)
+    va *= ldg(d.rdB + k) * ldg(rsum_e + e);
     const double de = NH ? ldg(dpp + a1) + ldg(dpp + a2) : 2.0;
-    // dK/dn + alpha_e dp/dn + (dp/dpi)_e dphi/dn, the two means folded into 1/2
+    // dK/dn + alpha_e dp/dn + (dp/dpi)_e dphi/dn with the two means folded
+    // into -1/(2 dc) (hrdc) and K stored doubled
     const double grad = fma(ldg(al + a1) + ldg(al + a2), ldg(p + a2) - ldg(p + a1),
-                            fma(de, ldg(phl + a2) - ldg(phl + a1), 2.0 * (ldg(K + a2) - ldg(K + a1))));
-    const double slow = -0.5 * ldg(m.rdc + e) * grad - va;
+                            fma(de, ldg(phl + a2) - ldg(phl + a1), ldg(K + a2) - ldg(K + a1)));
+    const double slow = fma(ldg(m.hrdc + e), grad, -va);
     const TA tend = pv + (TA)slow;
     const TU v = (TU)((TA)u_n[x] + (TA)dts * tend);
     if (!isfinite((double)v)) atomicOr(status, GRIST_FLAG_NONFINITE);
@@ -440,8 +503,40 @@ __global__ void k_nh_explicit(DevMesh m, DyPar d, LevelDiv Dv, const typename P:
     phst[xi] = phi_n[xi] + dts * ((double)(-hp - vp) + (1.0 - d.beta) * d.g * w_n[xi]);
 }
 
-// Implicit part of Eqs. 6-7 and Eq. 9, one thread per column, FP64.
-// Equation of state relative to the stage-input state (th_r, phi_r, p_r):
+// Staging of a [32 columns][8 levels] tile between global memory (rows of
+// stride S, one row per column) and shared memory sm[level * 33 + column]:
+// each step moves 8 consecutive levels (64 bytes) of four columns, so the
+// global side is coalesced; the 33-wide rows keep the shared-memory side
+// free of bank conflicts.
+constexpr int kSolveCols = 32;
+constexpr int kSolveKC = 8;
+constexpr int kRow = 33;
+constexpr int kStage = kSolveKC * kRow;
+
+__device__ __forceinline__ void stage_in(const double *X, size_t S, int col0, int ncol, int k0, int nk, double *sm) {
+    const int lane = threadIdx.x & 31, kk = lane & 7;
+#pragma unroll
+    for (int it = 0; it < kSolveCols / 4; it++) {
+        const int col = it * 4 + (lane >> 3);
+        double v = 0.0;
+        if (col < ncol && kk < nk) v = X[(size_t)(col0 + col) * S + k0 + kk];
+        sm[kk * kRow + col] = v;
+    }
+}
+
+__device__ __forceinline__ void stage_out(double *X, size_t S, int col0, int ncol, int k0, int nk, const double *sm) {
+    const int lane = threadIdx.x & 31, kk = lane & 7;
+#pragma unroll
+    for (int it = 0; it < kSolveCols / 4; it++) {
+        const int col = it * 4 + (lane >> 3);
+        if (col < ncol && kk < nk) X[(size_t)(col0 + col) * S + k0 + kk] = sm[kk * kRow + col];
+    }
+}
+
+// Implicit part of Eqs. 6-7 and Eq. 9, one thread per column (a block is
+// one warp of 32 consecutive columns), FP64.  Column data moves through
+// shared memory in 8-level chunks (coalesced global access).
+// Equation of state relative to the t^n state (1/th_r, phi_r, p_r):
 //   p** = p_r ((th dphi_r) / (th_r dphi**))^gamma     (pow_near1)
 // linearised about phi**: p_k = p**_k - C_k (w_k - w_{k+1}),
 // C_k = gamma p**_k beta dt g / dphi**_k; tridiagonal rows for interior
@@ -449,88 +544,137 @@ __global__ void k_nh_explicit(DevMesh m, DyPar d, LevelDiv Dv, const typename P:
 // algorithm; phi = phi** + beta dt g w; the full EOS then gives
 //   p = p** (dphi / dphi**)^(-gamma),  dphi = dphi** + beta dt g (w_k - w_{k+1});
 // finally alpha = dphi/dpi, layer phi and dp/dpi averaged to layers
-// (interface value 1 at top and bottom) for the momentum equation.
-__global__ void __launch_bounds__(128) k_nh_solve(DevMesh m, DyPar d, const double *__restrict__ wst,
-                                                  const double *__restrict__ phst, const double *__restrict__ th,
-                                                  const double *__restrict__ th_r, const double *__restrict__ phi_r,
-                                                  const double *p_r, const double *__restrict__ ps, double dts,
-                                                  double *__restrict__ w_out, double *__restrict__ phi_out, double *p,
-                                                  double *__restrict__ al, double *__restrict__ phl,
-                                                  double *__restrict__ dpp, Binom bg_pos, Binom bg_neg) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m.nC) return;
+// (interface value 1 at top and bottom) for the momentum equation.  phi_out
+// may be phi_r and p may be p_r (the last stage writes the state in place):
+// each block reads all reference values of its columns before writing them.
+__global__ void __launch_bounds__(32) k_nh_solve(DevMesh m, DyPar d, const double *__restrict__ wst,
+                                                 const double *__restrict__ phst, const double *__restrict__ th,
+                                                 const double *__restrict__ rth_r, const double *phi_r,
+                                                 const double *p_r, const double *__restrict__ ps, double dts,
+                                                 double *w_out, double *phi_out, double *p, double *__restrict__ al,
+                                                 double *__restrict__ phl, double *__restrict__ dpp, Binom bg_pos,
+                                                 Binom bg_neg) {
+    __shared__ double sA[6 * kStage + kRow];
+    const int lane = threadIdx.x;
+    const int col0 = blockIdx.x * kSolveCols;
+    const int ncol = min(kSolveCols, m.nC - col0);
+    const int i = col0 + lane;
+    const bool act = lane < ncol;
     const int L = d.L;
-    const size_t ci = (size_t)i * d.ldi, cl = (size_t)i * d.ld;
     const double bg = d.beta * dts * d.g;
     const double gbg = d.gamma * bg;
-    const double rdps = rcp(ps[i] - d.pi_top);
+    const double rdps = act ? rcp(ps[i] - d.pi_top) : 1.0;
     double cp[kNHMax], dd[kNHMax], pst[kNHMax], rdf[kNHMax];
-    // forward sweep; p** and C of layers j-1 and j are rolled along
-    double ftop = phst[ci], fbot = phst[ci + 1];
-    double rtop = phi_r[ci], rbot = phi_r[ci + 1];
-    double rdf0 = rcp(ftop - fbot);
-    double p0s = p_r[cl] * pow_near1(th[cl] * rcp(th_r[cl]) * ((rtop - rbot) * rdf0), d.gamma, bg_pos);
-    pst[0] = p0s;
-    rdf[0] = rdf0;
-    double pst_prev = p0s, C_prev = gbg * p0s * rdf0;
-    for (int j = 1; j < L; j++) {
-        ftop = fbot;
-        fbot = phst[ci + j + 1];
-        rtop = rbot;
-        rbot = phi_r[ci + j + 1];
-        const double rdfj = rcp(ftop - fbot);
-        const double pstj =
-            p_r[cl + j] * pow_near1(th[cl + j] * rcp(th_r[cl + j]) * ((rtop - rbot) * rdfj), d.gamma, bg_pos);
-        pst[j] = pstj;
-        rdf[j] = rdfj;
-        const double C = gbg * pstj * rdfj;
-        const double aj = bg * ldg(d.rdBi + j) * rdps;
-        const double a = (j == 1) ? 0.0 : -aj * C_prev;
-        const double c = (j == L - 1) ? 0.0 : -aj * C;
-        const double b = fma(aj, C_prev + C, 1.0);
-        const double rhs = wst[ci + j] + fma(aj, pstj - pst_prev, -bg);
-        const int r = j - 1;
-        if (r == 0) {
-            const double rb = rcp(b);
-            cp[0] = c * rb;
-            dd[0] = rhs * rb;
-        } else {
-            const double rden = rcp(fma(-a, cp[r - 1], b));
-            cp[r] = c * rden;
-            dd[r] = fma(-a, dd[r - 1], rhs) * rden;
+    double ftop = act ? phst[(size_t)i * d.ldi] : 0.0, rtop = act ? phi_r[(size_t)i * d.ldi] : 0.0;
+    const double phi_top0 = ftop;
+    double pst_prev = 0.0, C_prev = 0.0;
+    // forward sweep
+    for (int k0 = 0; k0 < L; k0 += kSolveKC) {
+        const int nk = min(kSolveKC, L - k0);
+        __syncwarp();
+        stage_in(phst, d.ldi, col0, ncol, k0 + 1, nk, sA + 0 * kStage);
+        stage_in(phi_r, d.ldi, col0, ncol, k0 + 1, nk, sA + 1 * kStage);
+        stage_in(th, d.ld, col0, ncol, k0, nk, sA + 2 * kStage);
+        stage_in(rth_r, d.ld, col0, ncol, k0, nk, sA + 3 * kStage);
+        stage_in(p_r, d.ld, col0, ncol, k0, nk, sA + 4 * kStage);
+        stage_in(wst, d.ldi, col0, ncol, k0, nk, sA + 5 * kStage);
+        __syncwarp();
+        if (act) {
+            for (int kk = 0; kk < nk; kk++) {
+                const int j = k0 + kk;
+                const int o = kk * kRow + lane;
+                const double fbot = sA[0 * kStage + o], rbot = sA[1 * kStage + o];
+                const double rdfj = rcp(ftop - fbot);
+                const double pstj = sA[4 * kStage + o] *
+                                    pow_near1(sA[2 * kStage + o] * sA[3 * kStage + o] * ((rtop - rbot) * rdfj),
+                                              d.gamma, bg_pos);
+                pst[j] = pstj;
+                rdf[j] = rdfj;
+                const double C = gbg * pstj * rdfj;
+                if (j >= 1) {
+                    const double aj = bg * ldg(d.rdBi + j) * rdps;
+                    const double a = (j == 1) ? 0.0 : -aj * C_prev;
+                    const double c = (j == L - 1) ? 0.0 : -aj * C;
+                    const double b = fma(aj, C_prev + C, 1.0);
+                    const double rhs = sA[5 * kStage + o] + fma(aj, pstj - pst_prev, -bg);
+                    const int r = j - 1;
+                    if (r == 0) {
+                        const double rb = rcp(b);
+                        cp[0] = c * rb;
+                        dd[0] = rhs * rb;
+                    } else {
+                        const double rden = rcp(fma(-a, cp[r - 1], b));
+                        cp[r] = c * rden;
+                        dd[r] = fma(-a, dd[r - 1], rhs) * rden;
+                    }
+                }
+                pst_prev = pstj;
+                C_prev = C;
+                ftop = fbot;
+                rtop = rbot;
+            }
         }
-        pst_prev = pstj;
-        C_prev = C;
     }
-    // back substitution into w (interfaces 1..L-1), w = 0 at 0 and L
-    w_out[ci] = 0.0;
-    w_out[ci + L] = 0.0;
+    // back substitution, bottom to top, w written chunk by chunk
+    // (interfaces 0..L; w = 0 at 0 and L)
     double wn = 0.0;
-    for (int r = L - 2; r >= 0; r--) {
-        wn = fma(-cp[r], wn, dd[r]);
-        w_out[ci + r + 1] = wn;
+    for (int k0 = (L / kSolveKC) * kSolveKC; k0 >= 0; k0 -= kSolveKC) {
+        const int nk = min(kSolveKC, L + 1 - k0);
+        __syncwarp();
+        for (int kk = nk - 1; kk >= 0; kk--) {
+            const int jf = k0 + kk;
+            double wv = 0.0;
+            if (act && jf >= 1 && jf <= L - 1) {
+                wn = fma(-cp[jf - 1], wn, dd[jf - 1]);
+                wv = wn;
+            }
+            sA[kk * kRow + lane] = wv;
+        }
+        __syncwarp();
+        stage_out(w_out, d.ldi, col0, ncol, k0, nk, sA);
     }
     // phi, EOS and momentum diagnostics, top to bottom
-    double w_top = 0.0, phi_top = phst[ci], p_prev = 0.0, dpdpi_top = 1.0;
-    phi_out[ci] = phi_top;
-    for (int k = 0; k < L; k++) {
-        const double w_bot = (k + 1 < L) ? w_out[ci + k + 1] : 0.0;
-        const double phi_bot = (k + 1 < L) ? fma(bg, w_bot, phst[ci + k + 1]) : ldg(d.phis + i);
-        phi_out[ci + k + 1] = phi_bot;
-        const double pk = pst[k] * pow_near1(fma(bg * (w_top - w_bot), rdf[k], 1.0), -d.gamma, bg_neg);
-        p[cl + k] = pk;
-        al[cl + k] = (phi_top - phi_bot) * (ldg(d.rdB + k) * rdps);
-        phl[cl + k] = 0.5 * (phi_top + phi_bot);
-        if (k > 0) {
-            const double dint = (pk - p_prev) * (ldg(d.rdBi + k) * rdps);
-            dpp[cl + k - 1] = 0.5 * (dpdpi_top + dint);
-            dpdpi_top = dint;
+    if (act) phi_out[(size_t)i * d.ldi] = phi_top0;
+    double phi_top = phi_top0, dtop = 1.0, pprev = 0.0;
+    for (int k0 = 0; k0 < L; k0 += kSolveKC) {
+        const int nk = min(kSolveKC, L - k0);
+        __syncwarp();
+        stage_in(phst, d.ldi, col0, ncol, k0 + 1, nk, sA + 0 * kStage);
+        stage_in(w_out, d.ldi, col0, ncol, k0, nk, sA + 1 * kStage);   // w at interfaces k0..k0+nk-1
+        if (lane < ncol) sA[6 * kStage + lane] = w_out[(size_t)i * d.ldi + k0 + nk];   // interface k0+nk
+        __syncwarp();
+        if (act) {
+            for (int kk = 0; kk < nk; kk++) {
+                const int k = k0 + kk;
+                const int o = kk * kRow + lane;
+                const double w_top = sA[1 * kStage + o];
+                const double w_bot = (kk + 1 < nk) ? sA[1 * kStage + o + kRow] : sA[6 * kStage + lane];
+                const double phi_bot = (k + 1 < L) ? fma(bg, w_bot, sA[o]) : ldg(d.phis + i);
+                const double pk = pst[k] * pow_near1(fma(bg * (w_top - w_bot), rdf[k], 1.0), -d.gamma, bg_neg);
+                double dcur = 1.0;
+                if (k > 0) {
+                    dcur = (pk - pprev) * (ldg(d.rdBi + k) * rdps);
+                    const double dv = 0.5 * (dtop + dcur);
+                    if (kk > 0) sA[5 * kStage + o - kRow] = dv;   // layer k-1 of this chunk
+                    else dpp[(size_t)i * d.ld + k - 1] = dv;        // layer k-1 of the previous chunk
+                }
+                sA[2 * kStage + o] = pk;
+                sA[3 * kStage + o] = (phi_top - phi_bot) * (ldg(d.rdB + k) * rdps);
+                sA[4 * kStage + o] = 0.5 * (phi_top + phi_bot);
+                sA[1 * kStage + o] = phi_bot;   // w_top of this row is no longer needed
+                dtop = dcur;
+                pprev = pk;
+                phi_top = phi_bot;
+            }
         }
-        p_prev = pk;
-        w_top = w_bot;
-        phi_top = phi_bot;
+        __syncwarp();
+        stage_out(phi_out, d.ldi, col0, ncol, k0 + 1, nk, sA + 1 * kStage);
+        stage_out(p, d.ld, col0, ncol, k0, nk, sA + 2 * kStage);
+        stage_out(al, d.ld, col0, ncol, k0, nk, sA + 3 * kStage);
+        stage_out(phl, d.ld, col0, ncol, k0, nk, sA + 4 * kStage);
+        stage_out(dpp, d.ld, col0, ncol, k0, nk - 1, sA + 5 * kStage);
     }
-    dpp[cl + L - 1] = 0.5 * (dpdpi_top + 1.0);
+    if (act) dpp[(size_t)i * d.ld + L - 1] = 0.5 * (dtop + 1.0);
 }
 
 __global__ void k_add_scalar(double *x, double v) {
@@ -550,7 +694,7 @@ int dycore_step(grist_mesh_s *h, grist_dycore_state *S, const grist_dycore_param
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off += al(bytes); return o; };
-    const size_t nvg = 4 * (size_t)L + 2;
+    const size_t nvg = 4 * (size_t)L + 2 + ((size_t)L + 1) / 2;   // doubles, then L floats
     const size_t o_vg = take(sizeof(double) * nvg);
     const size_t o_uA = take(nEL * sizeof(TU)), o_uB = take(nEL * sizeof(TU));
     const size_t o_psA = take(m.nC * 8), o_psB = take(m.nC * 8), o_psN = take(m.nC * 8);
@@ -561,10 +705,11 @@ int dycore_step(grist_mesh_s *h, grist_dycore_state *S, const grist_dycore_param
     const size_t o_theta = take(nCL * sizeof(TA)), o_Fth = take(nEL * sizeof(TA));
     const size_t o_p = take(nCL * 8), o_al = take(nCL * 8), o_phl = take(nCL * 8), o_dpp = take(nCL * 8);
     const size_t o_qv = take(nVL * sizeof(TA)), o_qe = take(nEL * sizeof(TA)), o_K = take(nCL * 8);
-    size_t o_wA = 0, o_wB = 0, o_phA = 0, o_phB = 0, o_wst = 0, o_phst = 0, o_pn = 0, o_fw = 0;
+    size_t o_wA = 0, o_wB = 0, o_phA = 0, o_phB = 0, o_wst = 0, o_phst = 0, o_pn = 0, o_fw = 0, o_rth = 0;
     if (NH) {
         o_wA = take(nCI * 8); o_wB = take(nCI * 8); o_phA = take(nCI * 8); o_phB = take(nCI * 8);
         o_wst = take(nCI * 8); o_phst = take(nCI * 8); o_pn = take(nCL * 8); o_fw = take(nCI * 8);
+        o_rth = take(nCL * 8);
     }
     char *s = (char *)scratch(h, 1, off);
     if (!s) return GRIST_ENOMEM;
@@ -578,6 +723,8 @@ int dycore_step(grist_mesh_s *h, grist_dycore_state *S, const grist_dycore_param
         hrdB[k] = 1.0 / hdB[k];
     }
     for (int j = 1; j < L; j++) hrdBi[j] = 2.0 / (hdB[j - 1] + hdB[j]);
+    float *hdBf = reinterpret_cast<float *>(hrdBi + L + 1);
+    for (int k = 0; k < L; k++) hdBf[k] = (float)hdB[k];
     double *dvg = (double *)(s + o_vg);
     GRIST_CUDA_TRY(cudaMemcpyAsync(dvg, vg.data(), vg.size() * sizeof(double), cudaMemcpyHostToDevice, st));
     GRIST_CUDA_TRY(cudaStreamSynchronize(st));  // vg is a host temporary
@@ -587,6 +734,7 @@ int dycore_step(grist_mesh_s *h, grist_dycore_state *S, const grist_dycore_param
     d.pi_top = prm->pi_top; d.p0 = prm->p0; d.rd = prm->rd; d.cp = prm->cp; d.g = prm->g;
     d.beta = prm->offcentre_beta; d.kappa = prm->rd / prm->cp; d.gamma = prm->cp / (prm->cp - prm->rd);
     d.B = dvg; d.dB = dvg + L + 1; d.rdB = dvg + 2 * L + 1; d.rdBi = dvg + 3 * L + 1; d.phis = prm->phi_surface;
+    d.dBf = reinterpret_cast<const float *>(dvg + 4 * L + 2);
 
     TU *uA = (TU *)(s + o_uA), *uB = (TU *)(s + o_uB);
     double *psA = (double *)(s + o_psA), *psB = (double *)(s + o_psB), *psN = (double *)(s + o_psN);
@@ -602,14 +750,14 @@ int dycore_step(grist_mesh_s *h, grist_dycore_state *S, const grist_dycore_param
     double *K = (double *)(s + o_K);
     double *wA = (double *)(s + o_wA), *wB = (double *)(s + o_wB), *phA = (double *)(s + o_phA),
            *phB = (double *)(s + o_phB), *wst = (double *)(s + o_wst), *phst = (double *)(s + o_phst),
-           *pn = (double *)(s + o_pn), *fwn = (double *)(s + o_fw);
+           *pn = (double *)(s + o_pn), *fwn = (double *)(s + o_fw), *rthn = (double *)(s + o_rth);
 
     TU *u = (TU *)S->u;
     uint32_t *status = status_word(h);
     const LevelDiv DL = make_div((uint32_t)L), DI = make_div((uint32_t)(L + 1));
     const unsigned gC = grid_for((long long)m.nC * L, kBlock), gE = grid_for((long long)m.nE * L, kBlock),
                    gV = grid_for((long long)m.nV * L, kBlock), gW = grid_for((long long)m.nC * 32, kBlock),
-                   gI = grid_for((long long)m.nC * (L + 1), kBlock), gCol = grid_for(m.nC, 128),
+                   gI = grid_for((long long)m.nC * (L + 1), kBlock), gSolve = grid_for(m.nC, kSolveCols),
                    gVx = grid_for(m.nV, kBlock), gWE = grid_for((long long)m.nE * 32, kBlock);
     const double dts[3] = {dt / 3.0, dt / 2.0, dt};
 
@@ -626,6 +774,7 @@ int dycore_step(grist_mesh_s *h, grist_dycore_state *S, const grist_dycore_param
         }
     }
     const Binom bpos = binomial(d.gamma), bneg = binomial(-d.gamma);
+
     double *p_outs[3] = {p, p, (NH && S->p_nh) ? S->p_nh : p};
 
     const TU *u_in = u;
@@ -640,7 +789,8 @@ int dycore_step(grist_mesh_s *h, grist_dycore_state *S, const grist_dycore_param
         GRIST_LAUNCH(h, PN("k_mass_edge"), st, k_mass_edge<P><<<gWE, kBlock, 0, st>>>(
             m, d, ps_in, u_in, F, s3 == 2 ? S->mass_flux_accum : nullptr, rsum, fcol));
         GRIST_LAUNCH(h, PN("k_mass_col"), st, k_mass_col<P><<<gW, kBlock, 0, st>>>(
-            m, d, F, fcol, ps_in, psN, ps_outs[s3], th_in, theta, Mv, h3, s3 == 0 ? S->dpi_start : nullptr, rdps));
+            m, d, F, fcol, ps_in, psN, ps_outs[s3], th_in, theta, Mv, h3, s3 == 0 ? S->dpi_start : nullptr, rdps,
+            (NH && s3 == 0) ? rthn : nullptr));
         GRIST_LAUNCH(h, PN("k_theta_flux"), st, k_theta_flux<P><<<gE, kBlock, 0, st>>>(m, d, DL, F, theta, Fth));
         GRIST_LAUNCH(h, PN("k_theta_update"), st, k_theta_update<P><<<gC, kBlock, 0, st>>>(
             m, d, DL, Fth, theta, Mv, S->dpi_theta, th_outs[s3], h3));
@@ -651,8 +801,8 @@ int dycore_step(grist_mesh_s *h, grist_dycore_state *S, const grist_dycore_param
             else
                 GRIST_LAUNCH(h, PN("k_nh_explicit"), st, k_nh_explicit<P, false><<<gI, kBlock, 0, st>>>(
                     m, d, DI, u_in, rdps, Mv, w_in, phi_in, S->w, S->phi, p_n, fwn, wst, phst, h3));
-            GRIST_LAUNCH(h, PN("k_nh_solve"), st, k_nh_solve<<<gCol, 128, 0, st>>>(
-                m, d, wst, phst, th_outs[s3], th_in, phi_in, s3 == 0 ? p_n : p, ps_outs[s3], h3, w_outs[s3],
+            GRIST_LAUNCH(h, PN("k_nh_solve"), st, k_nh_solve<<<gSolve, kSolveCols, 0, st>>>(
+                m, d, wst, phst, th_outs[s3], rthn, S->phi, p_n, ps_outs[s3], h3, w_outs[s3],
                 phi_outs[s3], p_outs[s3], alp, phl, dpp, bpos, bneg));
         } else {
             GRIST_LAUNCH(h, PN("k_hydro_diag"), st, k_hydro_diag<<<gW, kBlock, 0, st>>>(

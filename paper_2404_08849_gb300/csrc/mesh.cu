@@ -24,6 +24,7 @@ struct grist_mesh_s {
     size_t scr_bytes[8] = {0};
     uint32_t *status = nullptr;
     TracerCtx *tctx = nullptr;
+    HostTables ht;
     // profiling
     bool prof_on = false;
     std::vector<cudaEvent_t> ev;            // pool, pairs (2j, 2j+1)
@@ -38,6 +39,7 @@ const DevMesh &dev_mesh(grist_mesh_s *m) { return m->d; }
 int mesh_device(grist_mesh_s *m) { return m->device; }
 uint32_t *status_word(grist_mesh_s *m) { return m->status; }
 TracerCtx *&tracer_ctx(grist_mesh_s *m) { return m->tctx; }
+const HostTables &host_tables(grist_mesh_s *m) { return m->ht; }
 
 static const int kEventPairs = 4096;
 
@@ -276,7 +278,7 @@ extern "C" int grist_mesh_create(const grist_mesh_desc *desc, int device, grist_
                 eoc[x] = en[e];
                 coc[x] = cn[desc->cells_on_cell[o * 6 + j]];
                 cdiv[x] = desc->edge_sign_on_cell[o * 6 + j] * desc->edge_dv[e] / A;
-                kec[x] = 0.25 * desc->edge_dc[e] * desc->edge_dv[e] / A;
+                kec[x] = 0.5 * desc->edge_dc[e] * desc->edge_dv[e] / A;
             } else {
                 eoc[x] = en[desc->edges_on_cell[o * 6]];
                 coc[x] = i;
@@ -287,7 +289,7 @@ extern "C" int grist_mesh_create(const grist_mesh_desc *desc, int device, grist_
         }
     }
     std::vector<int2> coe(nE), voe(nE);
-    std::vector<double> rdc(nE), dc2(nE), d2c(14 * (size_t)nE), wpv(10 * (size_t)nE);
+    std::vector<double> rdc(nE), hrdc(nE), dc2(nE), d2c(14 * (size_t)nE), wpv(10 * (size_t)nE);
     std::vector<float> dc2_f(nE), d2c_f(14 * (size_t)nE), wpv_f(10 * (size_t)nE);
     std::vector<int32_t> d2i(14 * (size_t)nE), eoe(10 * (size_t)nE);
     for (int e = 0; e < nE; e++) {
@@ -296,6 +298,7 @@ extern "C" int grist_mesh_create(const grist_mesh_desc *desc, int device, grist_
         voe[e] = make_int2(vn[desc->vertices_on_edge[2 * o]], vn[desc->vertices_on_edge[2 * o + 1]]);
         double dc = desc->edge_dc[o];
         rdc[e] = 1.0 / dc;
+        hrdc[e] = -0.5 / dc;
         dc2[e] = dc * dc / 12.0;
         dc2_f[e] = (float)dc2[e];
         for (int s = 0; s < 2; s++) {
@@ -345,6 +348,7 @@ extern "C" int grist_mesh_create(const grist_mesh_desc *desc, int device, grist_
     size_t o_eoc = ar.add(eoc.size() * 4), o_coc = ar.add(coc.size() * 4), o_cdiv = ar.add(cdiv.size() * 8),
            o_cdivf = ar.add(cdiv_f.size() * 4), o_kec = ar.add(kec.size() * 8), o_area = ar.add(area.size() * 8),
            o_coe = ar.add(coe.size() * 8), o_voe = ar.add(voe.size() * 8), o_rdc = ar.add(rdc.size() * 8),
+           o_hrdc = ar.add(hrdc.size() * 8),
            o_dc2 = ar.add(dc2.size() * 8), o_dc2f = ar.add(dc2_f.size() * 4), o_d2i = ar.add(d2i.size() * 4),
            o_d2c = ar.add(d2c.size() * 8), o_d2cf = ar.add(d2c_f.size() * 4), o_eoe = ar.add(eoe.size() * 4),
            o_wpv = ar.add(wpv.size() * 8), o_wpvf = ar.add(wpv_f.size() * 4), o_eov = ar.add(eov.size() * 4),
@@ -357,6 +361,7 @@ extern "C" int grist_mesh_create(const grist_mesh_desc *desc, int device, grist_
     put(o_kec, kec.data(), kec.size() * 8); put(o_area, area.data(), area.size() * 8);
     put(o_coe, coe.data(), coe.size() * 8); put(o_voe, voe.data(), voe.size() * 8);
     put(o_rdc, rdc.data(), rdc.size() * 8); put(o_dc2, dc2.data(), dc2.size() * 8);
+    put(o_hrdc, hrdc.data(), hrdc.size() * 8);
     put(o_dc2f, dc2_f.data(), dc2_f.size() * 4); put(o_d2i, d2i.data(), d2i.size() * 4);
     put(o_d2c, d2c.data(), d2c.size() * 8); put(o_d2cf, d2c_f.data(), d2c_f.size() * 4);
     put(o_eoe, eoe.data(), eoe.size() * 4); put(o_wpv, wpv.data(), wpv.size() * 8);
@@ -374,13 +379,18 @@ extern "C" int grist_mesh_create(const grist_mesh_desc *desc, int device, grist_
         cudaFree(dev); delete m; return GRIST_ENOMEM;
     }
     m->arena = dev;
+    m->ht.nC = nC; m->ht.nE = nE; m->ht.nV = nV;
+    m->ht.eoc = eoc;
+    m->ht.coe = coe;
+    m->ht.d2i = d2i;
     DevMesh &D = m->d;
     D.nC = nC; D.nE = nE; D.nV = nV;
     D.eoc = place<int32_t>(dev, o_eoc); D.coc = place<int32_t>(dev, o_coc);
     D.cdiv = place<double>(dev, o_cdiv); D.cdiv_f = place<float>(dev, o_cdivf);
-    D.kec = place<double>(dev, o_kec); D.area = place<double>(dev, o_area);
+    D.kec2 = place<double>(dev, o_kec); D.area = place<double>(dev, o_area);
     D.coe = place<int2>(dev, o_coe); D.voe = place<int2>(dev, o_voe);
-    D.rdc = place<double>(dev, o_rdc); D.dc2 = place<double>(dev, o_dc2); D.dc2_f = place<float>(dev, o_dc2f);
+    D.rdc = place<double>(dev, o_rdc); D.hrdc = place<double>(dev, o_hrdc);
+    D.dc2 = place<double>(dev, o_dc2); D.dc2_f = place<float>(dev, o_dc2f);
     D.d2i = place<int32_t>(dev, o_d2i); D.d2c = place<double>(dev, o_d2c); D.d2c_f = place<float>(dev, o_d2cf);
     D.eoe = place<int32_t>(dev, o_eoe); D.wpv = place<double>(dev, o_wpv); D.wpv_f = place<float>(dev, o_wpvf);
     D.eov = place<int32_t>(dev, o_eov); D.cov = place<int32_t>(dev, o_cov);

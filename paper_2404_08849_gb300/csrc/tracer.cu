@@ -14,6 +14,7 @@
 // Data layout: q [T][nC][ld], dpi [nC][ld], mass flux [nE][ld], edge
 // fluxes [T][nE][ld]; consecutive threads take consecutive levels of one
 // entity (coalesced rows), neighbour rows are gathered through L1/L2.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -47,8 +48,28 @@ struct Space {
     unsigned long long total;
 };
 
+// Tiles of consecutive (space-filling-curve) cells for the fused stage
+// kernel: per tile the halo cells its edge fluxes read (the tile, its
+// neighbours and theirs), its edges, and for every tile edge the halo-local
+// indices of c1, c2 and the two deriv-two stencils; per tile cell the
+// tile-local index of each of its six edges.
+constexpr int kTileCells = 32;
+
+struct TileMesh {
+    int ntiles, Hmax, Emax;
+    const int *hoff;           // [ntiles + 1]
+    const int *halo;           // global cell ids
+    const int *eoff;           // [ntiles + 1]
+    const int *tedge;          // global edge ids
+    const uint16_t *eloc;      // [edges][16]: c1, c2, stencil side 0 (7), side 1 (7)
+    const uint16_t *cle;       // [ntiles * kTileCells][6]
+};
+
 struct TracerCtx {
-    grist_tracer_tuning tune{256, 4, 0, 0};
+    grist_tracer_tuning tune{256, 4, 0, 0, 0};
+    // tile tables (built on first use)
+    char *dtile = nullptr;
+    TileMesh tiles{};
     // device tables (one allocation), host mirrors
     char *dtab = nullptr;
     size_t dtab_bytes = 0;
@@ -67,6 +88,7 @@ void tracer_ctx_free(TracerCtx *c) {
     if (c->exec) cudaGraphExecDestroy(c->exec);
     if (c->graph) cudaGraphDestroy(c->graph);
     if (c->dtab) cudaFree(c->dtab);
+    if (c->dtile) cudaFree(c->dtile);
     if (c->barrier) cudaFree(c->barrier);
     delete c;
 }
@@ -79,6 +101,7 @@ struct Batch {
     const MemberDev *mem;
     int nm;
     Space D, C, E;  // D: cell x level (no groups); C: cell x level x group; E: edge x level x group
+    Space T;        // blocks of the fused stage kernel: segment start = first block of (member, group)
     int tpt;
     double dt;
     int fct;
@@ -390,6 +413,111 @@ __global__ void k_tracer_phase(DevMesh m, Batch B, uint32_t *status) {
     run_phase<false, TQ, TC, PH>(m, B, status);
 }
 
+// Fused RK stage (no limiter) on one tile x 32 levels x the tracers of one
+// group: the stage input on the tile's halo goes to shared memory, every
+// tile edge's third-order flux is computed once into shared memory, and the
+// cell update gathers from there (boundary edges of a tile are computed by
+// both tiles that share them).  Same arithmetic as item_edge + item_update.
+template <typename TQ, typename TC, bool BETA1>
+__global__ void __launch_bounds__(256) k_tr_tile_stage(DevMesh m, TileMesh tm, Batch B, int stage,
+                                                       uint32_t *status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TC *qs = (TC *)smem_raw;              // [Hmax][32]
+    TC *fs = qs + (size_t)tm.Hmax * 32;   // [Emax][32]
+    __shared__ int s_seg;
+    if (threadIdx.x == 0) s_seg = find_seg(B.T, blockIdx.x, -1);
+    __syncthreads();
+    const int seg = s_seg;
+    const int2 mg = B.T.mg[seg];
+    const MemberDev &mb = B.mem[mg.x];
+    const unsigned r = blockIdx.x - (unsigned)B.T.start[seg];
+    const int nch = (mb.L + 31) >> 5;
+    const int tile = (int)(r / nch), chunk = (int)(r % nch);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int k = chunk * 32 + lane;
+    const bool kin = k < mb.L;
+    const int ld = mb.ld;
+    const int h0 = tm.hoff[tile], H = tm.hoff[tile + 1] - h0;
+    const int e0 = tm.eoff[tile], E = tm.eoff[tile + 1] - e0;
+    const int c0 = tile * kTileCells;
+    const int nc = min(kTileCells, m.nC - c0);
+    const TQ *qin = stage == 0 ? (const TQ *)mb.q : (stage == 1 ? (const TQ *)mb.qA : (const TQ *)mb.qB);
+    TQ *qout = stage == 0 ? (TQ *)mb.qA : (stage == 1 ? (TQ *)mb.qB : (TQ *)mb.q);
+    const TQ *qn = (const TQ *)mb.q;
+    const double dts = stage == 0 ? B.dt / 3.0 : (stage == 1 ? B.dt / 2.0 : B.dt);
+    const TC beta = (TC)B.beta;
+    // stage ratios of this warp's cells (same for every tracer)
+    constexpr int kCpw = kTileCells / 4;   // cells per warp for blocks of >= 4 warps
+    TC r1v[kCpw], r2v[kCpw];
+#pragma unroll
+    for (int idx = 0; idx < kCpw; idx++) {
+        const int ci = warp + idx * nw;
+        r1v[idx] = r2v[idx] = (TC)0;
+        if (ci < nc && kin) {
+            const size_t x = (size_t)(c0 + ci) * ld + k;
+            const double dp = mb.dpi[x];
+            const double rinv = 1.0 / (dp - dts * mb.divF[x]);
+            r1v[idx] = (TC)(dp * rinv);
+            r2v[idx] = (TC)(dts * rinv);
+        }
+    }
+    const int t0 = mg.y * B.tpt, t1 = min(mb.T, t0 + B.tpt);
+    bool bad = false;
+    for (int t = t0; t < t1; t++) {
+        const TQ *qt = qin + (size_t)t * mb.qs;
+        for (int hh = warp; hh < H; hh += nw)
+            qs[hh * 32 + lane] = kin ? (TC)ldg(qt + (size_t)ldg(tm.halo + h0 + hh) * ld + k) : (TC)0;
+        __syncthreads();
+        for (int j = warp; j < E; j += nw) {
+            if (kin) {
+                const int e = ldg(tm.tedge + e0 + j);
+                const uint16_t *loc = tm.eloc + (size_t)(e0 + j) * 16;
+                const TC f = (TC)ldg(mb.F + (size_t)e * ld + k);
+                const TC dc2 = ldg(Coef<TC>::dc2(m) + e);
+                const TC *cf = Coef<TC>::d2c(m) + (size_t)e * 14;
+                const TC q1 = qs[loc[0] * 32 + lane], q2 = qs[loc[1] * 32 + lane];
+                TC qe;
+                if (BETA1) {
+                    const int side = f >= (TC)0 ? 0 : 1;
+                    TC d = 0;
+#pragma unroll
+                    for (int i = 0; i < GRIST_D2P; i++)
+                        d += ldg(cf + side * GRIST_D2P + i) * qs[loc[2 + side * GRIST_D2P + i] * 32 + lane];
+                    qe = (TC)0.5 * (q1 + q2) - (TC)2 * dc2 * d;
+                } else {
+                    const TC sgn = f >= (TC)0 ? (TC)1 : (TC)-1;
+                    TC d1 = 0, d2 = 0;
+#pragma unroll
+                    for (int i = 0; i < GRIST_D2P; i++) {
+                        d1 += ldg(cf + i) * qs[loc[2 + i] * 32 + lane];
+                        d2 += ldg(cf + GRIST_D2P + i) * qs[loc[2 + GRIST_D2P + i] * 32 + lane];
+                    }
+                    qe = (TC)0.5 * (q1 + q2) - dc2 * (d1 + d2) + sgn * beta * dc2 * (d2 - d1);
+                }
+                fs[j * 32 + lane] = f * qe;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int idx = 0; idx < kCpw; idx++) {
+            const int ci = warp + idx * nw;
+            if (ci < nc && kin) {
+                const int cell = c0 + ci;
+                const uint16_t *le = tm.cle + (size_t)cell * 6;
+                TC div = 0;
+#pragma unroll
+                for (int j = 0; j < GRIST_MAXE; j++) div += ldg(Coef<TC>::cdiv(m) + cell * 6 + j) * fs[le[j] * 32 + lane];
+                const size_t x = (size_t)cell * ld + k;
+                const TC v = r1v[idx] * (TC)qn[(size_t)t * mb.qs + x] - r2v[idx] * div;
+                bad |= !isfinite(v);
+                qout[(size_t)t * mb.qs + x] = (TQ)v;
+            }
+        }
+        __syncthreads();
+    }
+    if (bad) atomicOr(status, GRIST_FLAG_NONFINITE);
+}
+
 // Bounded wait until *gen differs from g: at most `limit` polls (~64 ns
 // apart); on giving up (or when another block already gave up) raises
 // GRIST_FLAG_TIMEOUT and returns false.
@@ -477,8 +605,8 @@ size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
 
 struct HostPlan {
     std::vector<MemberDev> mem;
-    std::vector<unsigned long long> sD, sC, sE;
-    std::vector<int2> mD, mC, mE;
+    std::vector<unsigned long long> sD, sC, sE, sT;
+    std::vector<int2> mD, mC, mE, mT;
     size_t scratch_bytes = 0;
 };
 
@@ -486,7 +614,8 @@ template <typename TQ, typename TC>
 int plan_batch(const DevMesh &m, const grist_tracer_batch *b, int tpt, HostPlan &P) {
     P = HostPlan();
     size_t off = 0;
-    unsigned long long tD = 0, tC = 0, tE = 0;
+    unsigned long long tD = 0, tC = 0, tE = 0, tT = 0;
+    const unsigned long long ntiles = ((unsigned long long)m.nC + kTileCells - 1) / kTileCells;
     for (int i = 0; i < b->n_members; i++) {
         const grist_tracer_member &u = b->members[i];
         if (u.n_levels == 0 || u.n_tracers == 0) continue;
@@ -518,12 +647,15 @@ int plan_batch(const DevMesh &m, const grist_tracer_batch *b, int tpt, HostPlan 
             tC += (unsigned long long)m.nC * d.L;
             P.sE.push_back(tE); P.mE.push_back(make_int2(idx, g));
             tE += (unsigned long long)m.nE * d.L;
+            P.sT.push_back(tT); P.mT.push_back(make_int2(idx, g));
+            tT += ntiles * (unsigned long long)((d.L + 31) / 32);
         }
         P.mem.push_back(d);
     }
     P.sD.push_back(tD);
     P.sC.push_back(tC);
     P.sE.push_back(tE);
+    P.sT.push_back(tT);
     P.scratch_bytes = off;
     return GRIST_OK;
 }
@@ -553,6 +685,8 @@ int upload_plan(grist_mesh_s *h, TracerCtx *c, HostPlan &P, const grist_tracer_b
     const size_t o_mD = o; o += al256(P.mD.size() * sizeof(int2));
     const size_t o_mC = o; o += al256(P.mC.size() * sizeof(int2));
     const size_t o_mE = o; o += al256(P.mE.size() * sizeof(int2));
+    const size_t o_sT = o; o += al256(P.sT.size() * 8);
+    const size_t o_mT = o; o += al256(P.mT.size() * sizeof(int2));
     std::vector<char> ht(o, 0);
     std::memcpy(ht.data() + o_mem, P.mem.data(), nm * sizeof(MemberDev));
     std::memcpy(ht.data() + o_sD, P.sD.data(), P.sD.size() * 8);
@@ -561,6 +695,8 @@ int upload_plan(grist_mesh_s *h, TracerCtx *c, HostPlan &P, const grist_tracer_b
     std::memcpy(ht.data() + o_mD, P.mD.data(), P.mD.size() * sizeof(int2));
     std::memcpy(ht.data() + o_mC, P.mC.data(), P.mC.size() * sizeof(int2));
     std::memcpy(ht.data() + o_mE, P.mE.data(), P.mE.size() * sizeof(int2));
+    std::memcpy(ht.data() + o_sT, P.sT.data(), P.sT.size() * 8);
+    std::memcpy(ht.data() + o_mT, P.mT.data(), P.mT.size() * sizeof(int2));
     if (c->dtab_bytes < o) {
         if (c->dtab) {
             cudaDeviceSynchronize();
@@ -585,6 +721,7 @@ int upload_plan(grist_mesh_s *h, TracerCtx *c, HostPlan &P, const grist_tracer_b
     B.D = Space{(const unsigned long long *)(c->dtab + o_sD), (const int2 *)(c->dtab + o_mD), (int)P.mD.size(), P.sD.back()};
     B.C = Space{(const unsigned long long *)(c->dtab + o_sC), (const int2 *)(c->dtab + o_mC), (int)P.mC.size(), P.sC.back()};
     B.E = Space{(const unsigned long long *)(c->dtab + o_sE), (const int2 *)(c->dtab + o_mE), (int)P.mE.size(), P.sE.back()};
+    B.T = Space{(const unsigned long long *)(c->dtab + o_sT), (const int2 *)(c->dtab + o_mT), (int)P.mT.size(), P.sT.back()};
     B.tpt = c->tune.tracers_per_thread;
     B.dt = dt;
     B.fct = b->limiter ? 1 : 0;
@@ -598,6 +735,8 @@ int sm_count(int dev) {
     cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
     return n > 0 ? n : 1;
 }
+
+int build_tiles(grist_mesh_s *h, TracerCtx *c);
 
 // Enqueue the step's kernels (no host synchronisation: capturable).
 template <typename TQ, typename TC>
@@ -633,9 +772,37 @@ int enqueue_step(grist_mesh_s *h, TracerCtx *c, const Batch &B, cudaStream_t st)
                                     "k_tr_ratios/fp64", "k_tr_final/fp64", "k_tr_copy/fp64"};
     (void)names;
     const int sms = sm_count(dev);
+    const bool fused = c->tune.fused != 0;
+    if (fused) {
+        int rc = build_tiles(h, c);
+        if (rc != GRIST_OK) return rc;
+    }
+    const size_t tile_smem = (size_t)(c->tiles.Hmax + c->tiles.Emax) * 32 * sizeof(TC);
+    auto launch_tile = [&](int stage) -> int {
+        if (B.T.total == 0) return GRIST_OK;
+        const unsigned grid = (unsigned)B.T.total;
+        if (B.beta1) {
+            GRIST_CUDA_TRY(cudaFuncSetAttribute(k_tr_tile_stage<TQ, TC, true>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem));
+            GRIST_LAUNCH(h, sizeof(TC) == 4 ? "k_tr_tile_stage/mix" : "k_tr_tile_stage/fp64", st,
+                         k_tr_tile_stage<TQ, TC, true><<<grid, 256, tile_smem, st>>>(m, c->tiles, B, stage, status));
+        } else {
+            GRIST_CUDA_TRY(cudaFuncSetAttribute(k_tr_tile_stage<TQ, TC, false>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem));
+            GRIST_LAUNCH(h, sizeof(TC) == 4 ? "k_tr_tile_stage/mix" : "k_tr_tile_stage/fp64", st,
+                         k_tr_tile_stage<TQ, TC, false><<<grid, 256, tile_smem, st>>>(m, c->tiles, B, stage, status));
+        }
+        return GRIST_OK;
+    };
     for (int ph = P_DIV; ph <= P_COPY; ph++) {
         if (!B.fct && ph > P_UPD2) break;
         if (B.fct && ph == P_UPD2) continue;
+        if (fused && (ph == P_EDGE0 || ph == P_EDGE1 || (!B.fct && ph == P_EDGE2))) continue;
+        if (fused && (ph == P_UPD0 || ph == P_UPD1 || ph == P_UPD2)) {
+            const int rc = launch_tile(ph == P_UPD0 ? 0 : (ph == P_UPD1 ? 1 : 2));
+            if (rc != GRIST_OK) return rc;
+            continue;
+        }
         const Space &S = (ph == P_DIV) ? B.D : (ph == P_EDGE0 || ph == P_EDGE1 || ph == P_EDGE2) ? B.E : B.C;
         long long want = (long long)((S.total + block - 1) / block);
         const long long cap = (long long)sms * 2048 * 32 / block;  // enough blocks to fill every SM many times
@@ -659,6 +826,85 @@ int enqueue_step(grist_mesh_s *h, TracerCtx *c, const Batch &B, cudaStream_t st)
         }
     }
     return cudaGetLastError() == cudaSuccess ? GRIST_OK : GRIST_ECUDA;
+}
+
+// Build the tile tables of the mesh (once per handle) and upload them.
+int build_tiles(grist_mesh_s *h, TracerCtx *c) {
+    if (c->dtile) return GRIST_OK;
+    const HostTables &ht = host_tables(h);
+    const int nC = ht.nC;
+    const int nt = (nC + kTileCells - 1) / kTileCells;
+    std::vector<int> hoff(nt + 1, 0), eoff(nt + 1, 0), halo, tedge;
+    std::vector<uint16_t> eloc, cle((size_t)nt * kTileCells * 6, 0);
+    int Hmax = 0, Emax = 0;
+    std::vector<int> cells, edges;
+    for (int t = 0; t < nt; t++) {
+        const int c0 = t * kTileCells, c1 = std::min(nC, c0 + kTileCells);
+        edges.clear();
+        for (int i = c0; i < c1; i++)
+            for (int j = 0; j < 6; j++) edges.push_back(ht.eoc[(size_t)i * 6 + j]);
+        std::sort(edges.begin(), edges.end());
+        edges.erase(std::unique(edges.begin(), edges.end()), edges.end());
+        cells.clear();
+        for (int e : edges) {
+            cells.push_back(ht.coe[e].x);
+            cells.push_back(ht.coe[e].y);
+            for (int q = 0; q < 14; q++) cells.push_back(ht.d2i[(size_t)e * 14 + q]);
+        }
+        std::sort(cells.begin(), cells.end());
+        cells.erase(std::unique(cells.begin(), cells.end()), cells.end());
+        if (cells.size() > 65535 || edges.size() > 65535) return GRIST_EUNSUPPORTED;
+        auto loc = [&](int cell) {
+            return (uint16_t)(std::lower_bound(cells.begin(), cells.end(), cell) - cells.begin());
+        };
+        for (int e : edges) {
+            eloc.push_back(loc(ht.coe[e].x));
+            eloc.push_back(loc(ht.coe[e].y));
+            for (int q = 0; q < 14; q++) eloc.push_back(loc(ht.d2i[(size_t)e * 14 + q]));
+        }
+        for (int i = c0; i < c1; i++)
+            for (int j = 0; j < 6; j++)
+                cle[(size_t)i * 6 + j] = (uint16_t)(std::lower_bound(edges.begin(), edges.end(),
+                                                                     ht.eoc[(size_t)i * 6 + j]) - edges.begin());
+        halo.insert(halo.end(), cells.begin(), cells.end());
+        tedge.insert(tedge.end(), edges.begin(), edges.end());
+        hoff[t + 1] = (int)halo.size();
+        eoff[t + 1] = (int)tedge.size();
+        Hmax = std::max(Hmax, (int)cells.size());
+        Emax = std::max(Emax, (int)edges.size());
+    }
+    size_t o = 0;
+    const size_t o_hoff = o; o += al256(hoff.size() * 4);
+    const size_t o_halo = o; o += al256(halo.size() * 4);
+    const size_t o_eoff = o; o += al256(eoff.size() * 4);
+    const size_t o_tedge = o; o += al256(tedge.size() * 4);
+    const size_t o_eloc = o; o += al256(eloc.size() * 2);
+    const size_t o_cle = o; o += al256(cle.size() * 2);
+    std::vector<char> hb(o, 0);
+    std::memcpy(hb.data() + o_hoff, hoff.data(), hoff.size() * 4);
+    std::memcpy(hb.data() + o_halo, halo.data(), halo.size() * 4);
+    std::memcpy(hb.data() + o_eoff, eoff.data(), eoff.size() * 4);
+    std::memcpy(hb.data() + o_tedge, tedge.data(), tedge.size() * 4);
+    std::memcpy(hb.data() + o_eloc, eloc.data(), eloc.size() * 2);
+    std::memcpy(hb.data() + o_cle, cle.data(), cle.size() * 2);
+    char *d = nullptr;
+    if (cudaMalloc(&d, o) != cudaSuccess) return GRIST_ENOMEM;
+    if (cudaMemcpy(d, hb.data(), o, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(d);
+        return GRIST_ECUDA;
+    }
+    c->dtile = d;
+    TileMesh &T = c->tiles;
+    T.ntiles = nt;
+    T.Hmax = Hmax;
+    T.Emax = Emax;
+    T.hoff = (const int *)(d + o_hoff);
+    T.halo = (const int *)(d + o_halo);
+    T.eoff = (const int *)(d + o_eoff);
+    T.tedge = (const int *)(d + o_tedge);
+    T.eloc = (const uint16_t *)(d + o_eloc);
+    T.cle = (const uint16_t *)(d + o_cle);
+    return GRIST_OK;
 }
 
 TracerCtx *ctx_of(grist_mesh_s *h) {
@@ -753,6 +999,7 @@ int check_tuning(const grist_tracer_tuning *t) {
     if (t->tracers_per_thread < 1 || t->tracers_per_thread > 64) return GRIST_EINVAL;
     if (t->persistent != 0 && t->persistent != 1) return GRIST_EINVAL;
     if (t->use_graph != 0 && t->use_graph != 1) return GRIST_EINVAL;
+    if (t->fused != 0 && t->fused != 1) return GRIST_EINVAL;
     return GRIST_OK;
 }
 
@@ -853,12 +1100,14 @@ extern "C" int grist_tracer_autotune(grist_mesh h, const grist_tracer_batch *b, 
     double bestms = 1e300;
     const int blocks[] = {128, 256, 512};
     const int tpts[] = {1, 2, 4, 8};
-    for (int bl : blocks) {
-        for (int tp : tpts) {
-            if (tp > 1 && tp / 2 >= maxT) continue;
-            grist_tracer_tuning t{bl, tp, 0, 0};
-            double ms = 0;
-            if (time_cfg(t, &ms) == GRIST_OK && ms < bestms) { bestms = ms; bestt = t; }
+    for (int fu = 0; fu <= 1; fu++) {
+        for (int bl : blocks) {
+            for (int tp : tpts) {
+                if (tp > 1 && tp / 2 >= maxT) continue;
+                grist_tracer_tuning t{bl, tp, 0, 0, fu};
+                double ms = 0;
+                if (time_cfg(t, &ms) == GRIST_OK && ms < bestms) { bestms = ms; bestt = t; }
+            }
         }
     }
     for (int pers = 0; pers <= 1; pers++) {
@@ -867,6 +1116,7 @@ extern "C" int grist_tracer_autotune(grist_mesh h, const grist_tracer_batch *b, 
             grist_tracer_tuning t = bestt;
             t.persistent = pers;
             t.use_graph = gr;
+            if (pers) t.fused = 0;
             double ms = 0;
             if (time_cfg(t, &ms) == GRIST_OK && ms < bestms) { bestms = ms; bestt = t; }
         }

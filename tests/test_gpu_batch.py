@@ -54,8 +54,9 @@ def _run(G, mesh, members, dt, prec, steps=1, tuning=None, limiter=True):
 
 SHAPES = [(1, 30, 30), (4, 60, 60), (10, 37, 40), (3, 8, 8), (25, 12, 16)]
 TUNINGS = [None,
-           {"block": 128, "tracers_per_thread": 1},
-           {"block": 512, "tracers_per_thread": 8},
+           {"block": 128, "tracers_per_thread": 1, "fused": False},
+           {"block": 512, "tracers_per_thread": 8, "fused": False},
+           {"block": 256, "tracers_per_thread": 3, "fused": True},
            {"block": 256, "tracers_per_thread": 4, "persistent": True},
            {"block": 256, "tracers_per_thread": 2, "use_graph": True},
            {"block": 256, "tracers_per_thread": 4, "persistent": True, "use_graph": True}]
@@ -79,6 +80,23 @@ def test_uneven_batch_fp64_parity(G, mesh_cache, tuning):
     for g, r in zip(got, refs):
         assert O.max_rel_diff(g, r) <= FP64_TOL
     assert mesh.last_status() == 0
+    mesh.close()
+
+
+@pytest.mark.parametrize("fused", [True, False])
+def test_uneven_batch_no_limiter_fp64(G, mesh_cache, fused):
+    m = mesh_cache(4)
+    mesh = G.Mesh(m)
+    rng = np.random.default_rng(43)
+    members = _members(m, rng, [(2, 30, 32), (5, 45, 45)])
+    M = O.Mesh(m)
+    got = _run(G, mesh, members, 300.0, "fp64", steps=2, limiter=False,
+               tuning={"block": 256, "tracers_per_thread": 2, "fused": fused})
+    for g, mb in zip(got, members):
+        q = mb["q"]
+        for _ in range(2):
+            q = O.tracer_step(M, q, mb["dpi"], mb["F"], 300.0, fct=False)
+        assert O.max_rel_diff(g, q) <= FP64_TOL
     mesh.close()
 
 
