@@ -81,6 +81,38 @@ def algorithmic_bytes(name, nC, nE, nV, L, T, prec):
     return table.get(base)
 
 
+# FP64 work of the kernels of the mixed step that are bound by the FP64 pipe
+# (ncu: sm__pipe_fp64_cycles_active 80-90 % of peak, DRAM well below its
+# peak): FP64 flops = 2 DFMA + DADD + DMUL executed thread instructions, and
+# DRAM bytes (read + write), per unit of work, both counted by ncu on the
+# level-7 mesh (163,842 cells, 60 levels) of the same workload and step.
+# Units: cell-levels "c", edge-levels "e", vertex-levels "v", cell-interfaces
+# (L + 1 per column) "i".  Per-launch figures scale with the units processed.
+FP64_WORK_MIX = {
+    # kernel: (unit, FP64 flop per unit, DRAM bytes per unit)
+    "k_nh_solve": ("c", 101.6, None),
+    "k_momentum": ("e", 19.9, 36.6),
+    "k_nh_explicit": ("i", 28.2, 73.1),
+    "k_ke": ("c", 18.0, 18.3),
+    "k_mass_col": ("c", 12.4, 36.7),
+    "k_mass_edge": ("e", 0.55, 11.4),
+    "k_eos": ("c", 93.0, 21.2),
+}
+
+SM_COUNT = 152
+DFMA_PER_SM_CLK = 2     # ncu: smsp__sass_thread_inst_executed_op_dfma_pred_on.sum.peak_sustained = 304 / GPU
+
+
+def fp64_peak_tflops(sm_mhz):
+    """FP64 peak from the unit counts and clock: 152 SMs x 2 DFMA per clock
+    x 2 flop at the given SM clock."""
+    return SM_COUNT * DFMA_PER_SM_CLK * 2 * sm_mhz * 1e6 / 1e12
+
+
+def units_of(kind, nC, nE, nV, L):
+    return {"c": nC * L, "e": nE * L, "v": nV * L, "i": nC * (L + 1)}[kind]
+
+
 # ---------------------------------------------------------------------------
 # clocks during the timed region
 
@@ -223,10 +255,18 @@ def gpu_arm(args, wl):
     nC, nE, nV, L, T = mesh.nC, mesh.nE, mesh.nV, wl["L"], wl["T"]
     K, W = args.steps, args.warmup
 
+    tunings = {}
+
     def run_prec(prec, sample_clocks=False):
         s = make_state(torch, host, prec, device, nE, nC, L, T, wl["nh"])
-        for _ in range(W):
+        for w in range(W):
             step(mesh, s, P, wl, prec)
+            if w == 0 and T and not args.no_autotune:
+                # the tracer launch configuration from the library's autotuner,
+                # on this step's own tracer inputs (restored after timing)
+                tunings[prec] = mesh.autotune_tracer(
+                    [{"q": s["q"], "dpi": s["dpi_start"], "mass_flux": s["mass_flux_accum"], "n_levels": L}],
+                    wl["dt"], prec=prec, steps=2)[0]
         torch.cuda.synchronize()
         cs = ClockSampler(device) if sample_clocks else None
         if cs:
@@ -297,22 +337,42 @@ def gpu_arm(args, wl):
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    f64_peak = fp64_peak_tflops(sm_max)
+    fp64_table = FP64_WORK_MIX if args.prec != "fp64" else {}
     kernels = []
     for name, (launches, ms) in sorted(prof_mix.items(), key=lambda kv: -kv[1][1]):
         b = algorithmic_bytes(name, nC, nE, nV, L, T, args.prec)
         avg = ms / max(launches, 1)
-        kernels.append({"kernel": name, "launches": launches, "total_ms": round(ms, 3),
-                        "avg_ms": round(avg, 4), "share": None,
-                        "gbs": round(b / (avg * 1e-3) / 1e9, 1) if b else None})
+        row = {"kernel": name, "launches": launches, "total_ms": round(ms, 3),
+               "avg_ms": round(avg, 4), "share": None,
+               "gbs": round(b / (avg * 1e-3) / 1e9, 1) if b else None}
+        w = fp64_table.get(name.split("/")[0])
+        if w:
+            row["fp64_tflops"] = round(w[1] * units_of(w[0], nC, nE, nV, L) / (avg * 1e-3) / 1e12, 4)
+        kernels.append(row)
     tot = sum(k["total_ms"] for k in kernels) or 1.0
     for k in kernels:
         k["share"] = round(k["total_ms"] / tot, 4)
     dom = kernels[0] if kernels else None
     roofline = None
-    if dom and dom["gbs"] is not None:
-        roofline = {"bound": "hbm", "kernel": dom["kernel"], "achieved": dom["gbs"], "peak": hbm_peak,
-                    "unit": "GB/s", "frac": round(dom["gbs"] / hbm_peak, 4), "traffic": None,
-                    "peak_source": peak_src}
+    if dom:
+        hbm_ctx = ({"achieved": dom["gbs"], "peak": hbm_peak, "unit": "GB/s",
+                    "frac": round(dom["gbs"] / hbm_peak, 4), "peak_source": peak_src}
+                   if dom["gbs"] is not None else None)
+        w = fp64_table.get(dom["kernel"].split("/")[0])
+        if w:
+            units = units_of(w[0], nC, nE, nV, L)
+            roofline = {"bound": "alu", "kernel": dom["kernel"], "achieved": dom["fp64_tflops"],
+                        "peak": round(f64_peak, 4), "unit": "TFLOP/s",
+                        "frac": round(dom["fp64_tflops"] / f64_peak, 4),
+                        "traffic": (int(w[2] * units) if w[2] is not None else None),
+                        "work": "FP64 flop per launch %.4g (%.1f per unit, ncu-counted)" % (w[1] * units, w[1]),
+                        "peak_source": "derived: %d SMs x %d DFMA/clk x 2 flop x %.0f MHz" % (
+                            SM_COUNT, DFMA_PER_SM_CLK, sm_max),
+                        "hbm": hbm_ctx}
+        elif hbm_ctx:
+            roofline = dict({"bound": "hbm", "kernel": dom["kernel"], "traffic": None}, **hbm_ctx)
     launches_per_step = sum(k["launches"] for k in kernels) / max(K, 1)
 
     mesh.close()
@@ -332,6 +392,7 @@ def gpu_arm(args, wl):
                "config": {"workload": wl["desc"], "precision": args.prec, "n_cells": nC, "n_edges": nE,
                           "n_levels": L, "n_tracers": T, "dt_s": wl["dt"],
                           "l2_policy": "inputs larger than L2 (state >> 129 MB), no flush",
+                          "tracer_tuning": tunings or "library default",
                           "parallelism": "independent ensemble member per GPU" if world > 1 else "single GPU"},
                "fp64": ({"value": total_units / secs_64, "ms_per_step": secs_64 / K * 1e3,
                          "speedup_mix_over_fp64": secs_64 / secs_mix} if secs_64 else None),
@@ -465,6 +526,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="default tracer launch configuration")
     ap.add_argument("--mesh-level", type=int, default=None,
                     help="override the workload's mesh level (small cases for profiling)")
     ap.add_argument("--cpu-level", type=int, default=8)

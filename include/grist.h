@@ -352,6 +352,24 @@ int grist_weighted_sum_noalloc(const double *x, const double *w, int64_t n, doub
  * usable.  Asynchronous on `stream`.  No counterpart in the paper. */
 int grist_selftest_bounded_wait(grist_mesh mesh, int64_t spin_limit, void *stream);
 
+/* Diagnostic: check the library's integer-arithmetic conversions between
+ * binary32 and binary64 (the mixed-precision kernels use them in place of
+ * the hardware conversion instructions, which issue on the FP64 pipe)
+ * against the hardware conversions, on the current device:
+ *   binary32 -> binary64 over all 2^32 bit patterns;
+ *   binary64 -> binary32 over, for every binary32 pattern f, the value f,
+ *   the midpoint between f and the next binary32 away from zero and the
+ *   two binary64 neighbours of that midpoint (every rounding boundary,
+ *   ties included), plus n_random pseudo-random binary64 patterns
+ *   (splitmix64 of seed + i; half of them with exponents inside and around
+ *   the binary32 range).
+ * Bit-exact agreement is required, except that any NaN matches any NaN.
+ *   out_checked[2], out_mismatch[2]  host, out: conversions checked and
+ *                    mismatches for {binary32->binary64, binary64->binary32}.
+ * Synchronous (uses and synchronises the default stream); allocates and
+ * frees 32 bytes of device memory.  No counterpart in the paper. */
+int grist_selftest_conversions(uint64_t n_random, uint64_t seed, uint64_t *out_checked, uint64_t *out_mismatch);
+
 /* Flags raised by the steps since the previous call (read after the stream
  * has been synchronised; synchronises the device and clears the flags). */
 int grist_last_step_status(grist_mesh mesh, uint32_t *flags);

@@ -45,6 +45,17 @@ def _prec(p):
     return PREC[p] if isinstance(p, str) else int(p)
 
 
+def selftest_conversions(n_random=1 << 28, seed=2404_08849):
+    """grist_selftest_conversions: the library's integer binary32 <->
+    binary64 conversions against the hardware ones on the current device.
+    Returns {"f2d": (checked, mismatches), "d2f": (checked, mismatches)}."""
+    lib = _lib.load()
+    checked = (ctypes.c_uint64 * 2)()
+    bad = (ctypes.c_uint64 * 2)()
+    _lib.check("grist_selftest_conversions", lib.grist_selftest_conversions(int(n_random), int(seed), checked, bad))
+    return {"f2d": (int(checked[0]), int(bad[0])), "d2f": (int(checked[1]), int(bad[1]))}
+
+
 class Mesh:
     """Device copy of one icosahedral Voronoi mesh (``grist_mesh_create``)."""
 

@@ -108,6 +108,73 @@ __device__ __forceinline__ float fmin_(float a, float b) { return fminf(a, b); }
 __device__ __forceinline__ double fmax_(double a, double b) { return fmax(a, b); }
 __device__ __forceinline__ float fmax_(float a, float b) { return fmaxf(a, b); }
 
+// Correctly rounded reciprocal (the same value as 1.0 / x, without the
+// general division sequence).
+__device__ __forceinline__ double rcp(double x) { return __drcp_rn(x); }
+
+// Conversions between binary32 and binary64 in integer arithmetic.  On this
+// GPU the hardware conversion instructions issue on the FP64 pipe, the
+// scarce resource of the mixed-precision kernels, so the IEEE-754 fields are
+// moved with integer operations instead.  Results equal the hardware
+// conversions bit for bit (round to nearest even; zeros, subnormals,
+// infinities and NaN classes kept).
+//
+// binary32 -> binary64 is exact: rebias the exponent (127 -> 1023) and shift
+// the fraction left by 29; a subnormal input is normalised first.
+__device__ __forceinline__ double f2d(float f) {
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t s = u & 0x80000000u, a = u & 0x7fffffffu;
+    uint32_t hi = (a >> 3) + 0x38000000u, lo = a << 29;   // 0x38000000 = (1023 - 127) << 20
+    if (a >= 0x7f800000u) hi = (a >> 3) | 0x7ff00000u;      // infinity / NaN
+    if (a < 0x00800000u) {                                  // zero / subnormal
+        const int sh = __clz(a | 1u) - 8;                   // leading one to bit 23
+        const uint32_t mnt = (a << sh) & 0x7fffffu;
+        hi = a ? (((uint32_t)(897 - sh) << 20) | (mnt >> 3)) : 0u;
+        lo = a ? (mnt << 29) : 0u;
+    }
+    return __hiloint2double((int)(hi | s), (int)lo);
+}
+
+// binary64 -> binary32, round to nearest, ties to even: keep the top 23
+// fraction bits, round on the 29 dropped ones; exponents past the binary32
+// range give infinity (NaN stays NaN); results below 2^-126 are rounded to
+// the subnormal grid 2^-149.
+__device__ __forceinline__ float d2f(double x) {
+    const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+    const uint32_t s = hi & 0x80000000u, ah = hi & 0x7fffffffu;
+    const int e = (int)(ah >> 20);
+    uint32_t mag;
+    if (e >= 897 && e <= 1150) {
+        mag = ((uint32_t)(e - 896) << 23) | ((ah & 0xfffffu) << 3) | (lo >> 29);
+        const uint32_t rest = lo & 0x1fffffffu;
+        mag += (uint32_t)(rest > 0x10000000u) | ((uint32_t)(rest == 0x10000000u) & (mag & 1u));
+    } else if (e > 1150) {
+        mag = (e == 2047 && ((ah & 0xfffffu) | lo)) ? 0x7fc00000u : 0x7f800000u;
+    } else {
+        const int sh = 926 - e;                             // value = M 2^(e - 1075), M 53 bits
+        if (e == 0 || sh >= 54) {
+            mag = 0u;
+        } else {
+            const unsigned long long M = (1ull << 52) | ((unsigned long long)(ah & 0xfffffu) << 32) | lo;
+            const unsigned long long q = M >> sh, r = M & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+            mag = (uint32_t)q + (uint32_t)((r > half) | ((r == half) & (q & 1ull)));
+        }
+    }
+    return __uint_as_float(mag | s);
+}
+
+// cv<T>(x): x in type T, through the integer conversions above.
+template <typename T> struct Cvt;
+template <> struct Cvt<double> {
+    static __device__ __forceinline__ double from(double x) { return x; }
+    static __device__ __forceinline__ double from(float x) { return f2d(x); }
+};
+template <> struct Cvt<float> {
+    static __device__ __forceinline__ float from(double x) { return d2f(x); }
+    static __device__ __forceinline__ float from(float x) { return x; }
+};
+template <typename T, typename S> __device__ __forceinline__ T cv(S x) { return Cvt<T>::from(x); }
+
 inline unsigned grid_for(long long n, int block) {
     long long g = (n + block - 1) / block;
     return (unsigned)(g > 0 ? g : 1);
@@ -124,6 +191,10 @@ int mesh_device(grist_mesh_s *m);
 // needs more than the current size.  slot separates independent users.
 void *scratch(grist_mesh_s *m, int slot, size_t bytes);
 uint32_t *status_word(grist_mesh_s *m);
+// True while per-kernel profiling (grist_profile_enable) is on; a step then
+// launches its kernels directly rather than replaying a captured graph, so
+// every launch is timed.
+bool profiling(grist_mesh_s *m);
 
 // Host copies of the packed connectivity (internal numbering), kept for
 // building derived tables (tracer tiles) after creation.

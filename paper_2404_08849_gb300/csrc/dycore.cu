@@ -40,8 +40,6 @@ struct DyPar {
     const double *phis;   // [nC]  surface geopotential
 };
 
-__device__ __forceinline__ double rcp(double x) { return __drcp_rn(x); }
-
 // Compensated single-precision accumulation (Knuth's TwoSum): a value is
 // hi + lo with |lo| <= ulp(hi)/2, so a sum of FP32 terms carries about 48
 // significant bits - as accurate as FP64 accumulation of the same FP32
@@ -74,21 +72,37 @@ __device__ __forceinline__ double col_reduce(double part) {
 }
 
 // r^g for a ratio r close to 1 by the binomial series
-// (1 + x)^g = sum_n C(g, n) x^n, n = 0..9, Horner in FP64, with the binomial
-// coefficients C(g, n) = C(g, n-1) (g - n + 1)/n formed on the host; for
-// |x| <= 2^-6 and |g| < 2 the omitted terms are below 1e-17 relative.
-// Outside that range the library pow() is used.
+// (1 + x)^g = sum_n C(g, n) x^n, Horner in FP64, with the binomial
+// coefficients C(g, n) = C(g, n-1) (g - n + 1)/n formed on the host.  For
+// |g| < 2 the coefficients stay below 4 in magnitude up to n = 16, so after N
+// terms the omitted tail is below 4 |x|^N / (1 - |x|): the warp takes the
+// shortest series with 4 |x|^N <= 2^-58 for the largest |x| among its lanes
+// (N = 4, 5, 6, 8, 10 for |x| < 2^-15, 2^-12, 2^-10, 2^-8, 2^-6) - a
+// warp-uniform branch, so no FP64 issue slot is spent on terms no lane
+// needs.  A lane with |x| > 2^-6 uses the library pow().  mask: the lanes
+// executing the call.
 struct Binom {
     double c[10];
 };
 
-__device__ __forceinline__ double pow_near1(double r, double g, const Binom &B) {
-    const double x = r - 1.0;
-    if (fabs(x) > 0.015625) return pow(r, g);
-    double s = B.c[9];
+template <int N> __device__ __forceinline__ double horner(double x, const Binom &B) {
+    double s = B.c[N - 1];
 #pragma unroll
-    for (int n = 8; n >= 0; n--) s = fma(s, x, B.c[n]);
+    for (int n = N - 2; n >= 0; n--) s = fma(s, x, B.c[n]);
     return s;
+}
+
+__device__ __forceinline__ double pow_near1(double r, double g, const Binom &B, unsigned mask) {
+    const double x = r - 1.0;
+    // high word of |x|: exponent and leading fraction bits, monotone in |x|
+    const unsigned hx = (unsigned)__double2hiint(x) & 0x7fffffffu;
+    const unsigned hm = __reduce_max_sync(mask, hx);
+    if (hm < 0x3f000000u) return horner<4>(x, B);    // |x| < 2^-15
+    if (hm < 0x3f300000u) return horner<5>(x, B);    // 2^-12
+    if (hm < 0x3f500000u) return horner<6>(x, B);    // 2^-10
+    if (hm < 0x3f700000u) return horner<8>(x, B);    // 2^-8
+    if (hx > 0x3f900000u || (hx == 0x3f900000u && __double2loint(x) != 0)) return pow(r, g);
+    return horner<10>(x, B);
 }
 
 Binom binomial(double g) {
@@ -100,61 +114,74 @@ Binom binomial(double g) {
 
 // ---------------------------------------------------------------------------
 // Eq. 3: mass flux at edges F = dpi_e u, dpi_e = mean of the two cells'
-// layer mass = dB_k (ps1 + ps2 - 2 pi_top)/2, one warp per edge with the
-// lanes over levels.  The column factor is formed in FP64 once per edge and
-// the product in the mass-flux type.  The warp also forms the edge's FP64
-// column sum sum_k F_k (a fixed butterfly, so both cells of the edge later
-// use the same value and the global mass change cancels to round-off) and
-// the reciprocal 1/(ps1 + ps2 - 2 pi_top) for the momentum equation.  In the
-// final stage the flux is accumulated for the tracer solver (Sec. 2.3:
-// single computed, saved double).
+// layer mass = dB_k (ps1 + ps2 - 2 pi_top)/2.  One warp takes 32 edges: the
+// per-edge FP64 work (column factor, the reciprocal 1/(ps1 + ps2 - 2 pi_top)
+// for the momentum equation) runs one edge per lane - an FP64 instruction
+// costs the FP64 pipe a full warp slot however few lanes are active - then
+// the warp walks its edges with the lanes over levels, forming the product
+// in the mass-flux type and the edge's column sum sum_k F_k by a fixed
+// butterfly (both cells of the edge later use the same value, so the global
+// mass change cancels to round-off).  In the final stage the flux is
+// accumulated for the tracer solver (Sec. 2.3: single computed, saved
+// double).
 template <class P>
 __global__ void k_mass_edge(DevMesh m, DyPar d, const double *__restrict__ ps_s,
                             const typename P::TU *__restrict__ u_s, typename P::TM *__restrict__ F,
                             double *__restrict__ Facc, double *__restrict__ rsum_e, double *__restrict__ Fcol) {
     using TM = typename P::TM;
-    const int e = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int e0 = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32;
     const int lane = threadIdx.x & 31;
-    if (e >= m.nE) return;
-    TM hs = 0;
-    if (lane == 0) {
-        const int2 c = ldg(m.coe + e);
+    if (e0 >= m.nE) return;
+    const int ne = min(32, m.nE - e0);
+    TM hs_l = 0;
+    if (lane < ne) {
+        const int2 c = ldg(m.coe + e0 + lane);
         const double sum = (ldg(ps_s + c.x) - d.pi_top) + (ldg(ps_s + c.y) - d.pi_top);
-        hs = (TM)(0.5 * sum);
-        rsum_e[e] = 0.5 * rcp(sum);   // 1 / (2 dpi_e / dB)
+        hs_l = cv<TM>(0.5 * sum);
+        rsum_e[e0 + lane] = 0.5 * rcp(sum);   // 1 / (2 dpi_e / dB)
     }
-    hs = __shfl_sync(0xffffffffu, hs, 0);
-    if (sizeof(TM) == 8) {
-        double col = 0.0;
-        for (int k = lane; k < d.L; k += 32) {
-            const size_t x = (size_t)e * d.ld + k;
-            const TM f = (TM)ldg(d.dB + k) * hs * (TM)u_s[x];
-            F[x] = f;
-            col += (double)f;
-            if (Facc) Facc[x] += (double)f;
-        }
-        col = col_reduce(col);
-        if (lane == 0) Fcol[e] = col;
-    } else {
-        F2 col{0.f, 0.f};
-        for (int k = lane; k < d.L; k += 32) {
-            const size_t x = (size_t)e * d.ld + k;
-            const TM f = ldg(d.dBf + k) * hs * (TM)u_s[x];
-            F[x] = f;
-            col = f2_add(col, F2{(float)f, 0.f});
-            if (Facc) Facc[x] += (double)f;
-        }
+    double col64 = 0.0;
+    float col_hi = 0.f, col_lo = 0.f;
+    for (int j = 0; j < ne; j++) {
+        const int e = e0 + j;
+        const TM hs = __shfl_sync(0xffffffffu, hs_l, j);
+        if (sizeof(TM) == 8) {
+            double col = 0.0;
+            for (int k = lane; k < d.L; k += 32) {
+                const size_t x = (size_t)e * d.ld + k;
+                const TM f = (TM)ldg(d.dB + k) * hs * cv<TM>(u_s[x]);
+                F[x] = f;
+                col += (double)f;
+                if (Facc) Facc[x] += (double)f;
+            }
+            col = col_reduce(col);
+            if (lane == j) col64 = col;
+        } else {
+            F2 col{0.f, 0.f};
+            for (int k = lane; k < d.L; k += 32) {
+                const size_t x = (size_t)e * d.ld + k;
+                const TM f = ldg(d.dBf + k) * hs * cv<TM>(u_s[x]);
+                F[x] = f;
+                col = f2_add(col, F2{cv<float>(f), 0.f});
+                if (Facc) Facc[x] += cv<double>(f);
+            }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) col = f2_add(col, f2_shfl_xor(col, o));
-        if (lane == 0) Fcol[e] = (double)col.hi + (double)col.lo;
+            for (int o = 16; o > 0; o >>= 1) col = f2_add(col, f2_shfl_xor(col, o));
+            if (lane == j) {
+                col_hi = col.hi;
+                col_lo = col.lo;
+            }
+        }
     }
+    if (lane < ne) Fcol[e0 + lane] = sizeof(TM) == 8 ? col64 : f2d(col_hi) + f2d(col_lo);
 }
 
-// Eq. 3 column part, one warp per cell: layer divergence D_k (mass-flux
-// type), surface pressure tendency -sum_j s dv/A (column sum of edge j) in
-// FP64, vertical mass flux M_{k+1/2} = -B_{k+1/2} dps/dt - sum_{l<=k} D_l by
-// a warp scan, the stage update of ps, theta = (dpi theta)/dpi of the stage
-// input for Eq. 4, and the column reciprocal 1/(ps - pi_top).
+// Eq. 3 column part.  One warp takes 32 cells; the per-cell FP64 work (the
+// surface pressure tendency -sum_j s dv/A (column sum of edge j), its stage
+// update, 1/(ps - pi_top)) runs one cell per lane, then the warp walks its
+// cells with the lanes over levels: layer divergence D_k (mass-flux type),
+// vertical mass flux M_{k+1/2} = -B_{k+1/2} dps/dt - sum_{l<=k} D_l by a
+// warp scan, theta = (dpi theta)/dpi of the stage input for Eq. 4.
 template <class P>
 __global__ void k_mass_col(DevMesh m, DyPar d, const typename P::TM *__restrict__ F,
                            const double *__restrict__ Fcol, const double *__restrict__ ps_s,
@@ -164,66 +191,70 @@ __global__ void k_mass_col(DevMesh m, DyPar d, const typename P::TM *__restrict_
                            double *__restrict__ rdps_out, double *__restrict__ rth_out) {
     using TM = typename P::TM;
     using TA = typename P::TA;
-    const int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int i0 = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32;
     const int lane = threadIdx.x & 31;
-    if (i >= m.nC) return;
-    int eidx[GRIST_MAXE];
-    TM cw[GRIST_MAXE];
+    if (i0 >= m.nC) return;
+    const int nci = min(32, m.nC - i0);
+    double pst_l = 0.0, dps_l = 0.0, rdps_l = 0.0;
+    if (lane < nci) {
+        const int i = i0 + lane;
 #pragma unroll
-    for (int j = 0; j < GRIST_MAXE; j++) {
-        eidx[j] = ldg(m.eoc + i * 6 + j);
-        cw[j] = ldg(Coef<TM>::cdiv(m) + i * 6 + j);
-    }
-    // scalar column work on lane 0, broadcast
-    double pst = 0.0, dps = 0.0, rdps = 0.0;
-    if (lane == 0) {
-#pragma unroll
-        for (int j = 0; j < GRIST_MAXE; j++) pst -= ldg(m.cdiv + i * 6 + j) * ldg(Fcol + eidx[j]);
-        dps = ldg(ps_s + i) - d.pi_top;
-        rdps = rcp(dps);
-        ps_out[i] = ps_n[i] + dts * pst;
-        rdps_out[i] = rdps;
+        for (int j = 0; j < GRIST_MAXE; j++) pst_l -= ldg(m.cdiv + i * 6 + j) * ldg(Fcol + ldg(m.eoc + i * 6 + j));
+        dps_l = ldg(ps_s + i) - d.pi_top;
+        rdps_l = rcp(dps_l);
+        ps_out[i] = ps_n[i] + dts * pst_l;
+        rdps_out[i] = rdps_l;
         Mv[(size_t)i * d.ldi] = 0.0;
         Mv[(size_t)i * d.ldi + d.L] = 0.0;
     }
-    pst = __shfl_sync(0xffffffffu, pst, 0);
-    dps = __shfl_sync(0xffffffffu, dps, 0);
-    rdps = __shfl_sync(0xffffffffu, rdps, 0);
-    double run = 0.0;
     const int nch = (d.L + 31) >> 5;
-    for (int ch = 0; ch < nch; ch++) {
-        const int k = ch * 32 + lane;
-        TM s = 0;
-        if (k < d.L) {
+    for (int c = 0; c < nci; c++) {
+        const int i = i0 + c;
+        const double pst = __shfl_sync(0xffffffffu, pst_l, c);
+        const double dps = __shfl_sync(0xffffffffu, dps_l, c);
+        const double rdps = __shfl_sync(0xffffffffu, rdps_l, c);
+        int eidx[GRIST_MAXE];
+        TM cw[GRIST_MAXE];
 #pragma unroll
-            for (int j = 0; j < GRIST_MAXE; j++) s += cw[j] * ldg(F + (size_t)eidx[j] * d.ld + k);
-            const size_t x = (size_t)i * d.ld + k;
-            theta[x] = (TA)(th_s[x] * ldg(d.rdB + k) * rdps);
-            if (dpi_out) dpi_out[x] = ldg(d.dB + k) * dps;
-            if (rth_out) rth_out[x] = rcp(th_s[x]);
+        for (int j = 0; j < GRIST_MAXE; j++) {
+            eidx[j] = ldg(m.eoc + i * 6 + j);
+            cw[j] = ldg(Coef<TM>::cdiv(m) + i * 6 + j);
         }
-        // inclusive prefix of D over the chunk, carried across chunks: FP64
-        // terms in FP64, FP32 terms in compensated FP32
-        if (sizeof(TM) == 8) {
-            double v = (double)s;
+        double run = 0.0;
+        for (int ch = 0; ch < nch; ch++) {
+            const int k = ch * 32 + lane;
+            TM s = 0;
+            if (k < d.L) {
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const double t = __shfl_up_sync(0xffffffffu, v, o);
-                if (lane >= o) v += t;
+                for (int j = 0; j < GRIST_MAXE; j++) s += cw[j] * ldg(F + (size_t)eidx[j] * d.ld + k);
+                const size_t x = (size_t)i * d.ld + k;
+                theta[x] = cv<TA>(th_s[x] * ldg(d.rdB + k) * rdps);
+                if (dpi_out) dpi_out[x] = ldg(d.dB + k) * dps;
+                if (rth_out) rth_out[x] = rcp(th_s[x]);
             }
-            if (k < d.L - 1) Mv[(size_t)i * d.ldi + k + 1] = -ldg(d.B + k + 1) * pst - (run + v);
-            run += __shfl_sync(0xffffffffu, v, 31);
-        } else {
-            F2 v{(float)s, 0.f};
+            // inclusive prefix of D over the chunk, carried across chunks:
+            // FP64 terms in FP64, FP32 terms in compensated FP32
+            if (sizeof(TM) == 8) {
+                double v = (double)s;
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const F2 t = f2_shfl_up(v, o);
-                if (lane >= o) v = f2_add(v, t);
+                for (int o = 1; o < 32; o <<= 1) {
+                    const double t = __shfl_up_sync(0xffffffffu, v, o);
+                    if (lane >= o) v += t;
+                }
+                if (k < d.L - 1) Mv[(size_t)i * d.ldi + k + 1] = -ldg(d.B + k + 1) * pst - (run + v);
+                run += __shfl_sync(0xffffffffu, v, 31);
+            } else {
+                F2 v{cv<float>(s), 0.f};
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const F2 t = f2_shfl_up(v, o);
+                    if (lane >= o) v = f2_add(v, t);
+                }
+                if (k < d.L - 1)
+                    Mv[(size_t)i * d.ldi + k + 1] = -ldg(d.B + k + 1) * pst - (run + (f2d(v.hi) + f2d(v.lo)));
+                const F2 last{__shfl_sync(0xffffffffu, v.hi, 31), __shfl_sync(0xffffffffu, v.lo, 31)};
+                run += f2d(last.hi) + f2d(last.lo);
             }
-            if (k < d.L - 1)
-                Mv[(size_t)i * d.ldi + k + 1] = -ldg(d.B + k + 1) * pst - (run + ((double)v.hi + (double)v.lo));
-            const F2 last{__shfl_sync(0xffffffffu, v.hi, 31), __shfl_sync(0xffffffffu, v.lo, 31)};
-            run += (double)last.hi + (double)last.lo;
         }
     }
 }
@@ -240,7 +271,7 @@ __global__ void k_theta_flux(DevMesh m, DyPar d, LevelDiv Dv, const typename P::
     split_index(n, Dv, e, k);
     const int2 c = ldg(m.coe + e);
     const size_t x = (size_t)e * d.ld + k;
-    const TA f = (TA)F[x];
+    const TA f = cv<TA>(F[x]);
     const int side = f >= (TA)0 ? 0 : 1;
     const int32_t *st = m.d2i + (size_t)e * 14 + side * GRIST_D2P;
     const TA *cf = Coef<TA>::d2c(m) + (size_t)e * 14 + side * GRIST_D2P;
@@ -269,10 +300,10 @@ __global__ void k_theta_update(DevMesh m, DyPar d, LevelDiv Dv, const typename P
     const size_t x = (size_t)i * d.ld + k;
     const TA tk = th[x];
     TA top = 0, bot = 0;
-    if (k > 0) top = (TA)Mv[(size_t)i * d.ldi + k] * ((TA)0.5 * (th[x - 1] + tk));
-    if (k < d.L - 1) bot = (TA)Mv[(size_t)i * d.ldi + k + 1] * ((TA)0.5 * (tk + th[x + 1]));
+    if (k > 0) top = cv<TA>(Mv[(size_t)i * d.ldi + k]) * ((TA)0.5 * (th[x - 1] + tk));
+    if (k < d.L - 1) bot = cv<TA>(Mv[(size_t)i * d.ldi + k + 1]) * ((TA)0.5 * (tk + th[x + 1]));
     const TA tend = -div - (bot - top);
-    th_out[x] = th_n[x] + dts * (double)tend;
+    th_out[x] = th_n[x] + dts * cv<double>(tend);
 }
 
 // Eq. 8 (hydrostatic diagnostics), one warp per column: mid-layer pressure,
@@ -339,8 +370,8 @@ __global__ void k_vort(DevMesh m, DyPar d, LevelDiv Dv, const typename P::TU *__
     TA z = 0;
 #pragma unroll
     for (int j = 0; j < 3; j++)
-        z += ldg(Coef<TA>::ccurl(m) + v * 3 + j) * (TA)ldg(u + (size_t)ldg(m.eov + v * 3 + j) * d.ld + k);
-    qv[(size_t)v * d.ld + k] = (TA)(((double)z + ldg(m.fv + v)) * (ldg(d.rdB + k) * ldg(rdpv + v)));
+        z += ldg(Coef<TA>::ccurl(m) + v * 3 + j) * cv<TA>(ldg(u + (size_t)ldg(m.eov + v * 3 + j) * d.ld + k));
+    qv[(size_t)v * d.ld + k] = cv<TA>((cv<double>(z) + ldg(m.fv + v)) * (ldg(d.rdB + k) * ldg(rdpv + v)));
 }
 
 // Cell kinetic energy, stored doubled: 2K = sum (dc dv / 2A) u^2 (FP64:
@@ -354,7 +385,7 @@ __global__ void k_ke(DevMesh m, DyPar d, LevelDiv Dv, const typename P::TU *__re
     double s = 0.0;
 #pragma unroll
     for (int j = 0; j < GRIST_MAXE; j++) {
-        double ue = (double)ldg(u + (size_t)ldg(m.eoc + i * 6 + j) * d.ld + k);
+        const double ue = cv<double>(ldg(u + (size_t)ldg(m.eoc + i * 6 + j) * d.ld + k));
         s += ldg(m.kec2 + i * 6 + j) * ue * ue;
     }
     K[(size_t)i * d.ld + k] = s;
@@ -402,17 +433,17 @@ __global__ void k_momentum(DevMesh m, DyPar d, LevelDiv Dv, const typename P::TU
     for (int j = 0; j < GRIST_MAXEOE; j++) {
         const int e2 = ldg(m.eoe + e * 10 + j);
         const size_t y = (size_t)e2 * d.ld + k;
-        pv += ldg(Coef<TA>::wpv(m) + e * 10 + j) * (TA)ldg(F + y) * ((TA)0.5 * (qee + ldg(qe + y)));
+        pv += ldg(Coef<TA>::wpv(m) + e * 10 + j) * cv<TA>(ldg(F + y)) * ((TA)0.5 * (qee + ldg(qe + y)));
     }
     const size_t a1 = (size_t)c.x * d.ld + k, a2 = (size_t)c.y * d.ld + k;
-    const double uk = (double)ldg(u_s + x);
+    const double uk = cv<double>(ldg(u_s + x));
     double va = 0.0;
     if (k < d.L - 1)
         va = (ldg(Mv + (size_t)c.x * d.ldi + k + 1) + ldg(Mv + (size_t)c.y * d.ldi + k + 1)) *
-             ((double)ldg(u_s + x + 1) - uk);
+             (cv<double>(ldg(u_s + x + 1)) - uk);
     if (k > 0)
-        va = fma(ldg(Mv + (size_t)c.x * d.ldi + k) + ldg(Mv + (size_t)c.y * d.ldi + k), uk - (double)ldg(u_s + x - 1),
-                 va);
+        va = fma(ldg(Mv + (size_t)c.x * d.ldi + k) + ldg(Mv + (size_t)c.y * d.ldi + k),
+                 uk - cv<double>(ldg(u_s + x - 1)), va);
     // [M sums](du) / (2 dpi_e) with dpi_e = dB (sum)/2, M_e = (M1 + M2)/2;
     // rsum_e holds 1/(2 sum)
     va *= ldg(d.rdB + k) * ldg(rsum_e + e);
@@ -422,9 +453,9 @@ __global__ void k_momentum(DevMesh m, DyPar d, LevelDiv Dv, const typename P::TU
     const double grad = fma(ldg(al + a1) + ldg(al + a2), ldg(p + a2) - ldg(p + a1),
                             fma(de, ldg(phl + a2) - ldg(phl + a1), ldg(K + a2) - ldg(K + a1)));
     const double slow = fma(ldg(m.hrdc + e), grad, -va);
-    const TA tend = pv + (TA)slow;
-    const TU v = (TU)((TA)u_n[x] + (TA)dts * tend);
-    if (!isfinite((double)v)) atomicOr(status, GRIST_FLAG_NONFINITE);
+    const TA tend = pv + cv<TA>(slow);
+    const TU v = cv<TU>(cv<TA>(u_n[x]) + cv<TA>(dts) * tend);
+    if (!isfinite(v)) atomicOr(status, GRIST_FLAG_NONFINITE);
     u_out[x] = v;
 }
 
@@ -477,20 +508,20 @@ __global__ void k_nh_explicit(DevMesh m, DyPar d, LevelDiv Dv, const typename P:
         const int nb = ldg(m.coc + i * 6 + s);
         TA ui;
         const size_t ue = (size_t)e * d.ld;
-        if (j == 0) ui = (TA)ldg(u_s + ue);
-        else ui = (TA)0.5 * ((TA)ldg(u_s + ue + j - 1) + (TA)ldg(u_s + ue + j));
+        if (j == 0) ui = cv<TA>(ldg(u_s + ue));
+        else ui = (TA)0.5 * (cv<TA>(ldg(u_s + ue + j - 1)) + cv<TA>(ldg(u_s + ue + j)));
         const TA cu = ldg(Coef<TA>::cdiv(m) + i * 6 + s) * ui * (TA)0.5;
         const size_t y = (size_t)nb * d.ldi + j;
-        hw += cu * (TA)(ldg(w_s + y) - wi);
-        hp += cu * (TA)(ldg(phi_s + y) - pi);
+        hw += cu * cv<TA>(ldg(w_s + y) - wi);
+        hp += cu * cv<TA>(ldg(phi_s + y) - pi);
     }
     TA vw = 0, vp = 0;
     double fw = 0.0;
     if (j > 0) {
         const double rd2 = 0.5 * ldg(d.rdBi + j) * ldg(rdps_s + i);   // 1/(dpi_{j-1} + dpi_j)
-        const TA r = (TA)(Mv[(size_t)i * d.ldi + j] * rd2);
-        vw = r * (TA)(w_s[xi + 1] - w_s[xi - 1]);
-        vp = r * (TA)(phi_s[xi + 1] - phi_s[xi - 1]);
+        const TA r = cv<TA>(Mv[(size_t)i * d.ldi + j] * rd2);
+        vw = r * cv<TA>(w_s[xi + 1] - w_s[xi - 1]);
+        vp = r * cv<TA>(phi_s[xi + 1] - phi_s[xi - 1]);
         if (FIRST) {
             // first stage: the stage input is t^n, so rdps_s is 1/(ps^n - pi_top)
             fw = d.g * fma(p_n[(size_t)i * d.ld + j] - p_n[(size_t)i * d.ld + j - 1], 2.0 * rd2, -1.0);
@@ -499,8 +530,8 @@ __global__ void k_nh_explicit(DevMesh m, DyPar d, LevelDiv Dv, const typename P:
             fw = fw_n[xi];
         }
     }
-    wst[xi] = w_n[xi] + dts * ((double)(-hw - vw) + (1.0 - d.beta) * fw);
-    phst[xi] = phi_n[xi] + dts * ((double)(-hp - vp) + (1.0 - d.beta) * d.g * w_n[xi]);
+    wst[xi] = w_n[xi] + dts * (cv<double>(-hw - vw) + (1.0 - d.beta) * fw);
+    phst[xi] = phi_n[xi] + dts * (cv<double>(-hp - vp) + (1.0 - d.beta) * d.g * w_n[xi]);
 }
 
 // Staging of a [32 columns][8 levels] tile between global memory (rows of
@@ -564,6 +595,8 @@ __global__ void __launch_bounds__(32) k_nh_solve(DevMesh m, DyPar d, const doubl
     const double bg = d.beta * dts * d.g;
     const double gbg = d.gamma * bg;
     const double rdps = act ? rcp(ps[i] - d.pi_top) : 1.0;
+    const double bgr = bg * rdps;
+    const unsigned amask = __ballot_sync(0xffffffffu, act);
     double cp[kNHMax], dd[kNHMax], pst[kNHMax], rdf[kNHMax];
     double ftop = act ? phst[(size_t)i * d.ldi] : 0.0, rtop = act ? phi_r[(size_t)i * d.ldi] : 0.0;
     const double phi_top0 = ftop;
@@ -587,12 +620,12 @@ __global__ void __launch_bounds__(32) k_nh_solve(DevMesh m, DyPar d, const doubl
                 const double rdfj = rcp(ftop - fbot);
                 const double pstj = sA[4 * kStage + o] *
                                     pow_near1(sA[2 * kStage + o] * sA[3 * kStage + o] * ((rtop - rbot) * rdfj),
-                                              d.gamma, bg_pos);
+                                              d.gamma, bg_pos, amask);
                 pst[j] = pstj;
                 rdf[j] = rdfj;
                 const double C = gbg * pstj * rdfj;
                 if (j >= 1) {
-                    const double aj = bg * ldg(d.rdBi + j) * rdps;
+                    const double aj = bgr * ldg(d.rdBi + j);
                     const double a = (j == 1) ? 0.0 : -aj * C_prev;
                     const double c = (j == L - 1) ? 0.0 : -aj * C;
                     const double b = fma(aj, C_prev + C, 1.0);
@@ -650,7 +683,7 @@ __global__ void __launch_bounds__(32) k_nh_solve(DevMesh m, DyPar d, const doubl
                 const double w_top = sA[1 * kStage + o];
                 const double w_bot = (kk + 1 < nk) ? sA[1 * kStage + o + kRow] : sA[6 * kStage + lane];
                 const double phi_bot = (k + 1 < L) ? fma(bg, w_bot, sA[o]) : ldg(d.phis + i);
-                const double pk = pst[k] * pow_near1(fma(bg * (w_top - w_bot), rdf[k], 1.0), -d.gamma, bg_neg);
+                const double pk = pst[k] * pow_near1(fma(bg * (w_top - w_bot), rdf[k], 1.0), -d.gamma, bg_neg, amask);
                 double dcur = 1.0;
                 if (k > 0) {
                     dcur = (pk - pprev) * (ldg(d.rdBi + k) * rdps);
@@ -758,7 +791,8 @@ int dycore_step(grist_mesh_s *h, grist_dycore_state *S, const grist_dycore_param
     const unsigned gC = grid_for((long long)m.nC * L, kBlock), gE = grid_for((long long)m.nE * L, kBlock),
                    gV = grid_for((long long)m.nV * L, kBlock), gW = grid_for((long long)m.nC * 32, kBlock),
                    gI = grid_for((long long)m.nC * (L + 1), kBlock), gSolve = grid_for(m.nC, kSolveCols),
-                   gVx = grid_for(m.nV, kBlock), gWE = grid_for((long long)m.nE * 32, kBlock);
+                   gVx = grid_for(m.nV, kBlock), gE32 = grid_for((long long)m.nE + 31, kBlock),
+                   gC32 = grid_for((long long)m.nC + 31, kBlock);
     const double dts[3] = {dt / 3.0, dt / 2.0, dt};
 
     GRIST_CUDA_TRY(cudaMemcpyAsync(psN, S->ps, m.nC * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -786,9 +820,9 @@ int dycore_step(grist_mesh_s *h, grist_dycore_state *S, const grist_dycore_param
     double *phi_outs[3] = {phA, phB, S->phi};
     for (int s3 = 0; s3 < 3; s3++) {
         const double h3 = dts[s3];
-        GRIST_LAUNCH(h, PN("k_mass_edge"), st, k_mass_edge<P><<<gWE, kBlock, 0, st>>>(
+        GRIST_LAUNCH(h, PN("k_mass_edge"), st, k_mass_edge<P><<<gE32, kBlock, 0, st>>>(
             m, d, ps_in, u_in, F, s3 == 2 ? S->mass_flux_accum : nullptr, rsum, fcol));
-        GRIST_LAUNCH(h, PN("k_mass_col"), st, k_mass_col<P><<<gW, kBlock, 0, st>>>(
+        GRIST_LAUNCH(h, PN("k_mass_col"), st, k_mass_col<P><<<gC32, kBlock, 0, st>>>(
             m, d, F, fcol, ps_in, psN, ps_outs[s3], th_in, theta, Mv, h3, s3 == 0 ? S->dpi_start : nullptr, rdps,
             (NH && s3 == 0) ? rthn : nullptr));
         GRIST_LAUNCH(h, PN("k_theta_flux"), st, k_theta_flux<P><<<gE, kBlock, 0, st>>>(m, d, DL, F, theta, Fth));

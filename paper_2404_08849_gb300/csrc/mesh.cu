@@ -38,6 +38,7 @@ namespace grist {
 const DevMesh &dev_mesh(grist_mesh_s *m) { return m->d; }
 int mesh_device(grist_mesh_s *m) { return m->device; }
 uint32_t *status_word(grist_mesh_s *m) { return m->status; }
+bool profiling(grist_mesh_s *m) { return m->prof_on; }
 TracerCtx *&tracer_ctx(grist_mesh_s *m) { return m->tctx; }
 const HostTables &host_tables(grist_mesh_s *m) { return m->ht; }
 

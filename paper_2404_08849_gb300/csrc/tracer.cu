@@ -11,6 +11,10 @@
 // iterations.  The phases run either as one launch each or inside one
 // persistent cooperative kernel separated by bounded grid barriers.
 //
+// These kernels are bound by instruction issue and latency, not by the FP64
+// pipe, so they keep the hardware binary32/binary64 conversions (one issue
+// slot each) rather than the integer ones the FP64-bound dycore kernels use.
+//
 // Data layout: q [T][nC][ld], dpi [nC][ld], mass flux [nE][ld], edge
 // fluxes [T][nE][ld]; consecutive threads take consecutive levels of one
 // entity (coalesced rows), neighbour rows are gathered through L1/L2.
@@ -104,6 +108,7 @@ struct Batch {
     Space T;        // blocks of the fused stage kernel: segment start = first block of (member, group)
     int tpt;
     double dt;
+    double dt3;     // dt / 3, the first RK stage (formed on the host)
     int fct;
     int beta1;
     double beta;
@@ -155,7 +160,7 @@ __device__ __forceinline__ void item_edge(const DevMesh &m, const MemberDev &mb,
                                           int e, int k, bool beta1, TC beta) {
     const int ld = mb.ld;
     const int2 c = ldg(m.coe + e);
-    const TC f = (TC)ldg(mb.F + (size_t)e * ld + k);
+    const TC f = static_cast<TC>(ldg(mb.F + (size_t)e * ld + k));
     const TC dc2 = ldg(Coef<TC>::dc2(m) + e);
     const int32_t *st = m.d2i + (size_t)e * 14;
     const TC *cf = Coef<TC>::d2c(m) + (size_t)e * 14;
@@ -173,8 +178,8 @@ __device__ __forceinline__ void item_edge(const DevMesh &m, const MemberDev &mb,
             const TQ *qt = q + (size_t)t * mb.qs;
             TC d = 0;
 #pragma unroll
-            for (int j = 0; j < GRIST_D2P; j++) d += w[j] * (TC)lds<PERS>(qt + (size_t)idx[j] * ld + k);
-            const TC q1 = (TC)lds<PERS>(qt + (size_t)c.x * ld + k), q2 = (TC)lds<PERS>(qt + (size_t)c.y * ld + k);
+            for (int j = 0; j < GRIST_D2P; j++) d += w[j] * static_cast<TC>(lds<PERS>(qt + (size_t)idx[j] * ld + k));
+            const TC q1 = static_cast<TC>(lds<PERS>(qt + (size_t)c.x * ld + k)), q2 = static_cast<TC>(lds<PERS>(qt + (size_t)c.y * ld + k));
             FH[(size_t)t * mb.fs + (size_t)e * ld + k] = f * ((TC)0.5 * (q1 + q2) - (TC)2 * dc2 * d);
         }
     } else {
@@ -184,10 +189,10 @@ __device__ __forceinline__ void item_edge(const DevMesh &m, const MemberDev &mb,
             TC d1 = 0, d2 = 0;
 #pragma unroll
             for (int j = 0; j < GRIST_D2P; j++) {
-                d1 += ldg(cf + j) * (TC)lds<PERS>(qt + (size_t)ldg(st + j) * ld + k);
-                d2 += ldg(cf + GRIST_D2P + j) * (TC)lds<PERS>(qt + (size_t)ldg(st + GRIST_D2P + j) * ld + k);
+                d1 += ldg(cf + j) * static_cast<TC>(lds<PERS>(qt + (size_t)ldg(st + j) * ld + k));
+                d2 += ldg(cf + GRIST_D2P + j) * static_cast<TC>(lds<PERS>(qt + (size_t)ldg(st + GRIST_D2P + j) * ld + k));
             }
-            const TC q1 = (TC)lds<PERS>(qt + (size_t)c.x * ld + k), q2 = (TC)lds<PERS>(qt + (size_t)c.y * ld + k);
+            const TC q1 = static_cast<TC>(lds<PERS>(qt + (size_t)c.x * ld + k)), q2 = static_cast<TC>(lds<PERS>(qt + (size_t)c.y * ld + k));
             const TC qe = (TC)0.5 * (q1 + q2) - dc2 * (d1 + d2) + sgn * beta * dc2 * (d2 - d1);
             FH[(size_t)t * mb.fs + (size_t)e * ld + k] = f * qe;
         }
@@ -204,8 +209,8 @@ __device__ __forceinline__ bool item_update(const DevMesh &m, const MemberDev &m
     const int ld = mb.ld;
     const size_t x = (size_t)i * ld + k;
     const double dp = mb.dpi[x];
-    const double rinv = 1.0 / (dp - dts * lds<PERS>(mb.divF + x));
-    const TC r1 = (TC)(dp * rinv), r2 = (TC)(dts * rinv);
+    const double rinv = rcp(dp - dts * lds<PERS>(mb.divF + x));
+    const TC r1 = static_cast<TC>(dp * rinv), r2 = static_cast<TC>(dts * rinv);
     int eidx[GRIST_MAXE];
     TC cw[GRIST_MAXE];
 #pragma unroll
@@ -221,9 +226,9 @@ __device__ __forceinline__ bool item_update(const DevMesh &m, const MemberDev &m
         TC div = 0;
 #pragma unroll
         for (int j = 0; j < GRIST_MAXE; j++) div += cw[j] * lds<PERS>(ft + (size_t)eidx[j] * ld + k);
-        const TC v = r1 * (TC)qn[(size_t)t * mb.qs + x] - r2 * div;
+        const TC v = r1 * static_cast<TC>(qn[(size_t)t * mb.qs + x]) - r2 * div;
         bad |= !isfinite(v);
-        qout[(size_t)t * mb.qs + x] = (TQ)v;
+        qout[(size_t)t * mb.qs + x] = static_cast<TQ>(v);
     }
     return bad;
 }
@@ -235,7 +240,7 @@ template <bool PERS, typename TQ, typename TC>
 __device__ __forceinline__ TC upwind_flux(TC f, TC cw, int i, int nb, const TQ *qt, int ld, int k) {
     const bool i_is_c1 = cw > (TC)0;
     const int up = ((f >= (TC)0) == i_is_c1) ? i : nb;
-    return f * (TC)lds<PERS>(qt + (size_t)up * ld + k);
+    return f * static_cast<TC>(lds<PERS>(qt + (size_t)up * ld + k));
 }
 
 // FCT 1: low-order solution q^td = (dpi^n q^n - dt div F^L) / dpi^(3).
@@ -245,8 +250,8 @@ __device__ __forceinline__ void item_lowres(const DevMesh &m, const MemberDev &m
     const int ld = mb.ld;
     const size_t x = (size_t)i * ld + k;
     const double dp = mb.dpi[x];
-    const double rinv = 1.0 / (dp - dt * lds<PERS>(mb.divF + x));
-    const TC r1 = (TC)(dp * rinv), r2 = (TC)(dt * rinv);
+    const double rinv = rcp(dp - dt * lds<PERS>(mb.divF + x));
+    const TC r1 = static_cast<TC>(dp * rinv), r2 = static_cast<TC>(dt * rinv);
     int nb[GRIST_MAXE];
     TC cw[GRIST_MAXE], fe[GRIST_MAXE];
 #pragma unroll
@@ -254,7 +259,7 @@ __device__ __forceinline__ void item_lowres(const DevMesh &m, const MemberDev &m
         const int e = ldg(m.eoc + i * 6 + j);
         nb[j] = ldg(m.coc + i * 6 + j);
         cw[j] = ldg(Coef<TC>::cdiv(m) + i * 6 + j);
-        fe[j] = (TC)ldg(mb.F + (size_t)e * ld + k);
+        fe[j] = static_cast<TC>(ldg(mb.F + (size_t)e * ld + k));
     }
     const TQ *qn = (const TQ *)mb.q;
     TQ *qtd = (TQ *)mb.qA;
@@ -263,7 +268,7 @@ __device__ __forceinline__ void item_lowres(const DevMesh &m, const MemberDev &m
         TC div = 0;
 #pragma unroll
         for (int j = 0; j < GRIST_MAXE; j++) div += cw[j] * upwind_flux<PERS, TQ, TC>(fe[j], cw[j], i, nb[j], qt, ld, k);
-        qtd[(size_t)t * mb.qs + x] = (TQ)(r1 * (TC)qt[x] - r2 * div);
+        qtd[(size_t)t * mb.qs + x] = static_cast<TQ>(r1 * static_cast<TC>(qt[x]) - r2 * div);
     }
 }
 
@@ -275,8 +280,8 @@ __device__ __forceinline__ void item_ratios(const DevMesh &m, const MemberDev &m
                                             double dt) {
     const int ld = mb.ld;
     const size_t x = (size_t)i * ld + k;
-    const TC dp3 = (TC)(mb.dpi[x] - dt * lds<PERS>(mb.divF + x));
-    const TC dtc = (TC)dt;
+    const TC dp3 = static_cast<TC>(mb.dpi[x] - dt * lds<PERS>(mb.divF + x));
+    const TC dtc = static_cast<TC>(dt);
     int nb[GRIST_MAXE], eidx[GRIST_MAXE];
     TC cw[GRIST_MAXE], fe[GRIST_MAXE];
 #pragma unroll
@@ -284,7 +289,7 @@ __device__ __forceinline__ void item_ratios(const DevMesh &m, const MemberDev &m
         eidx[j] = ldg(m.eoc + i * 6 + j);
         nb[j] = ldg(m.coc + i * 6 + j);
         cw[j] = ldg(Coef<TC>::cdiv(m) + i * 6 + j);
-        fe[j] = (TC)ldg(mb.F + (size_t)eidx[j] * ld + k);
+        fe[j] = static_cast<TC>(ldg(mb.F + (size_t)eidx[j] * ld + k));
     }
     const TQ *qn = (const TQ *)mb.q, *qtd = (const TQ *)mb.qA;
     const TC *FH = (const TC *)mb.FH;
@@ -293,16 +298,19 @@ __device__ __forceinline__ void item_ratios(const DevMesh &m, const MemberDev &m
         const TQ *qt = qn + (size_t)t * mb.qs;
         const TQ *qd = qtd + (size_t)t * mb.qs;
         const TC *ft = FH + (size_t)t * mb.fs;
-        const TC qtd_i = (TC)lds<PERS>(qd + x);
-        TC qmax = fmax_((TC)qt[x], qtd_i), qmin = fmin_((TC)qt[x], qtd_i);
+        const TC qtd_i = static_cast<TC>(lds<PERS>(qd + x));
+        const TC qn_i = static_cast<TC>(qt[x]);
+        TC qmax = fmax_(qn_i, qtd_i), qmin = fmin_(qn_i, qtd_i);
         TC pp = 0, pm = 0;
 #pragma unroll
         for (int j = 0; j < GRIST_MAXE; j++) {
             const size_t y = (size_t)nb[j] * ld + k;
-            const TC a = (TC)qt[y], b = (TC)lds<PERS>(qd + y);
+            const TC a = static_cast<TC>(qt[y]), b = static_cast<TC>(lds<PERS>(qd + y));
             qmax = fmax_(qmax, fmax_(a, b));
             qmin = fmin_(qmin, fmin_(a, b));
-            const TC ae = lds<PERS>(ft + (size_t)eidx[j] * ld + k) - upwind_flux<PERS, TQ, TC>(fe[j], cw[j], i, nb[j], qt, ld, k);
+            // low-order flux from the upwind cell's q^n (already in registers)
+            const TC fl = fe[j] * (((fe[j] >= (TC)0) == (cw[j] > (TC)0)) ? qn_i : a);
+            const TC ae = lds<PERS>(ft + (size_t)eidx[j] * ld + k) - fl;
             const TC out = cw[j] * ae;  // outward antidiffusive flux / A_i (sign and dv folded in)
             pp += fmax_((TC)0, -out);
             pm += fmax_((TC)0, out);
@@ -324,8 +332,8 @@ __device__ __forceinline__ bool item_final(const DevMesh &m, const MemberDev &mb
     const int ld = mb.ld;
     const size_t x = (size_t)i * ld + k;
     const double dp = mb.dpi[x];
-    const double rinv = 1.0 / (dp - dt * lds<PERS>(mb.divF + x));
-    const TC r1 = (TC)(dp * rinv), r2 = (TC)(dt * rinv);
+    const double rinv = rcp(dp - dt * lds<PERS>(mb.divF + x));
+    const TC r1 = static_cast<TC>(dp * rinv), r2 = static_cast<TC>(dt * rinv);
     int nb[GRIST_MAXE], eidx[GRIST_MAXE];
     TC cw[GRIST_MAXE], fe[GRIST_MAXE];
 #pragma unroll
@@ -333,7 +341,7 @@ __device__ __forceinline__ bool item_final(const DevMesh &m, const MemberDev &mb
         eidx[j] = ldg(m.eoc + i * 6 + j);
         nb[j] = ldg(m.coc + i * 6 + j);
         cw[j] = ldg(Coef<TC>::cdiv(m) + i * 6 + j);
-        fe[j] = (TC)ldg(mb.F + (size_t)eidx[j] * ld + k);
+        fe[j] = static_cast<TC>(ldg(mb.F + (size_t)eidx[j] * ld + k));
     }
     const TQ *qn = (const TQ *)mb.q;
     const TC *FH = (const TC *)mb.FH;
@@ -358,9 +366,9 @@ __device__ __forceinline__ bool item_final(const DevMesh &m, const MemberDev &mb
             const TC c = ae >= (TC)0 ? fmin_(rm1, rp2) : fmin_(rp1, rm2);
             div += cw[j] * (fl + c * ae);
         }
-        const TC v = r1 * (TC)qt[x] - r2 * div;
+        const TC v = r1 * static_cast<TC>(qt[x]) - r2 * div;
         bad |= !isfinite(v);
-        qout[(size_t)t * mb.qs + x] = (TQ)v;
+        qout[(size_t)t * mb.qs + x] = static_cast<TQ>(v);
     }
     return bad;
 }
@@ -384,7 +392,8 @@ __device__ void run_phase(const DevMesh &m, const Batch &B, uint32_t *status) {
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     int seg = -1;
     bool bad = false;
-    const double dts = PH <= P_UPD0 ? B.dt / 3.0 : (PH <= P_UPD1 ? B.dt / 2.0 : B.dt);
+    const double dts = PH <= P_UPD0 ? B.dt3 : (PH <= P_UPD1 ? 0.5 * B.dt : B.dt);
+    const TC beta = static_cast<TC>(B.beta);
     for (unsigned long long n = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; n < S.total; n += stride) {
         seg = find_seg(S, n, seg);
         const int2 mg = S.mg[seg];
@@ -394,9 +403,9 @@ __device__ void run_phase(const DevMesh &m, const Batch &B, uint32_t *status) {
         const int t0 = mg.y * B.tpt;
         const int t1 = min(mb.T, t0 + B.tpt);
         if (PH == P_DIV) item_div(m, mb, ent, k);
-        if (PH == P_EDGE0) item_edge<PERS, TQ, TC>(m, mb, (const TQ *)mb.q, t0, t1, ent, k, B.beta1, (TC)B.beta);
-        if (PH == P_EDGE1) item_edge<PERS, TQ, TC>(m, mb, (const TQ *)mb.qA, t0, t1, ent, k, B.beta1, (TC)B.beta);
-        if (PH == P_EDGE2) item_edge<PERS, TQ, TC>(m, mb, (const TQ *)mb.qB, t0, t1, ent, k, B.beta1, (TC)B.beta);
+        if (PH == P_EDGE0) item_edge<PERS, TQ, TC>(m, mb, (const TQ *)mb.q, t0, t1, ent, k, B.beta1, beta);
+        if (PH == P_EDGE1) item_edge<PERS, TQ, TC>(m, mb, (const TQ *)mb.qA, t0, t1, ent, k, B.beta1, beta);
+        if (PH == P_EDGE2) item_edge<PERS, TQ, TC>(m, mb, (const TQ *)mb.qB, t0, t1, ent, k, B.beta1, beta);
         if (PH == P_UPD0) bad |= item_update<PERS, TQ, TC>(m, mb, (TQ *)mb.qA, t0, t1, ent, k, dts);
         if (PH == P_UPD1) bad |= item_update<PERS, TQ, TC>(m, mb, (TQ *)mb.qB, t0, t1, ent, k, dts);
         if (PH == P_UPD2) bad |= item_update<PERS, TQ, TC>(m, mb, (TQ *)mb.q, t0, t1, ent, k, dts);
@@ -444,8 +453,8 @@ __global__ void __launch_bounds__(256) k_tr_tile_stage(DevMesh m, TileMesh tm, B
     const TQ *qin = stage == 0 ? (const TQ *)mb.q : (stage == 1 ? (const TQ *)mb.qA : (const TQ *)mb.qB);
     TQ *qout = stage == 0 ? (TQ *)mb.qA : (stage == 1 ? (TQ *)mb.qB : (TQ *)mb.q);
     const TQ *qn = (const TQ *)mb.q;
-    const double dts = stage == 0 ? B.dt / 3.0 : (stage == 1 ? B.dt / 2.0 : B.dt);
-    const TC beta = (TC)B.beta;
+    const double dts = stage == 0 ? B.dt3 : (stage == 1 ? 0.5 * B.dt : B.dt);
+    const TC beta = static_cast<TC>(B.beta);
     // stage ratios of this warp's cells (same for every tracer)
     constexpr int kCpw = kTileCells / 4;   // cells per warp for blocks of >= 4 warps
     TC r1v[kCpw], r2v[kCpw];
@@ -456,9 +465,9 @@ __global__ void __launch_bounds__(256) k_tr_tile_stage(DevMesh m, TileMesh tm, B
         if (ci < nc && kin) {
             const size_t x = (size_t)(c0 + ci) * ld + k;
             const double dp = mb.dpi[x];
-            const double rinv = 1.0 / (dp - dts * mb.divF[x]);
-            r1v[idx] = (TC)(dp * rinv);
-            r2v[idx] = (TC)(dts * rinv);
+            const double rinv = rcp(dp - dts * mb.divF[x]);
+            r1v[idx] = static_cast<TC>(dp * rinv);
+            r2v[idx] = static_cast<TC>(dts * rinv);
         }
     }
     const int t0 = mg.y * B.tpt, t1 = min(mb.T, t0 + B.tpt);
@@ -466,13 +475,13 @@ __global__ void __launch_bounds__(256) k_tr_tile_stage(DevMesh m, TileMesh tm, B
     for (int t = t0; t < t1; t++) {
         const TQ *qt = qin + (size_t)t * mb.qs;
         for (int hh = warp; hh < H; hh += nw)
-            qs[hh * 32 + lane] = kin ? (TC)ldg(qt + (size_t)ldg(tm.halo + h0 + hh) * ld + k) : (TC)0;
+            qs[hh * 32 + lane] = kin ? static_cast<TC>(ldg(qt + (size_t)ldg(tm.halo + h0 + hh) * ld + k)) : (TC)0;
         __syncthreads();
         for (int j = warp; j < E; j += nw) {
             if (kin) {
                 const int e = ldg(tm.tedge + e0 + j);
                 const uint16_t *loc = tm.eloc + (size_t)(e0 + j) * 16;
-                const TC f = (TC)ldg(mb.F + (size_t)e * ld + k);
+                const TC f = static_cast<TC>(ldg(mb.F + (size_t)e * ld + k));
                 const TC dc2 = ldg(Coef<TC>::dc2(m) + e);
                 const TC *cf = Coef<TC>::d2c(m) + (size_t)e * 14;
                 const TC q1 = qs[loc[0] * 32 + lane], q2 = qs[loc[1] * 32 + lane];
@@ -508,9 +517,9 @@ __global__ void __launch_bounds__(256) k_tr_tile_stage(DevMesh m, TileMesh tm, B
 #pragma unroll
                 for (int j = 0; j < GRIST_MAXE; j++) div += ldg(Coef<TC>::cdiv(m) + cell * 6 + j) * fs[le[j] * 32 + lane];
                 const size_t x = (size_t)cell * ld + k;
-                const TC v = r1v[idx] * (TC)qn[(size_t)t * mb.qs + x] - r2v[idx] * div;
+                const TC v = r1v[idx] * static_cast<TC>(qn[(size_t)t * mb.qs + x]) - r2v[idx] * div;
                 bad |= !isfinite(v);
-                qout[(size_t)t * mb.qs + x] = (TQ)v;
+                qout[(size_t)t * mb.qs + x] = static_cast<TQ>(v);
             }
         }
         __syncthreads();
@@ -724,6 +733,7 @@ int upload_plan(grist_mesh_s *h, TracerCtx *c, HostPlan &P, const grist_tracer_b
     B.T = Space{(const unsigned long long *)(c->dtab + o_sT), (const int2 *)(c->dtab + o_mT), (int)P.mT.size(), P.sT.back()};
     B.tpt = c->tune.tracers_per_thread;
     B.dt = dt;
+    B.dt3 = dt / 3.0;
     B.fct = b->limiter ? 1 : 0;
     B.beta1 = b->beta_upwind == 1.0 ? 1 : 0;
     B.beta = b->beta_upwind;
@@ -923,7 +933,7 @@ int tracer_step_t(grist_mesh_s *h, const grist_tracer_batch *b, double dt, cudaS
     Batch B;
     rc = upload_plan<TQ, TC>(h, c, P, b, dt, B, st);
     if (rc != GRIST_OK) return rc;
-    if (!c->tune.use_graph) return enqueue_step<TQ, TC>(h, c, B, st);
+    if (!c->tune.use_graph || profiling(h)) return enqueue_step<TQ, TC>(h, c, B, st);
     // graph path: signature = batch contents + tuning + dt + stream
     std::vector<unsigned long long> sig;
     sig.push_back((unsigned long long)b->prec);
