@@ -534,21 +534,32 @@ __global__ void k_nh_explicit(DevMesh m, DyPar d, LevelDiv Dv, const typename P:
     phst[xi] = phi_n[xi] + dts * (cv<double>(-hp - vp) + (1.0 - d.beta) * d.g * w_n[xi]);
 }
 
-// Staging of a [32 columns][8 levels] tile between global memory (rows of
-// stride S, one row per column) and shared memory sm[level * 33 + column]:
-// each step moves 8 consecutive levels (64 bytes) of four columns, so the
-// global side is coalesced; the 33-wide rows keep the shared-memory side
-// free of bank conflicts.
+// Staging of a [32 columns][kSolveKC levels] tile between global memory
+// (rows of stride S, one row per column) and shared memory
+// sm[level * 33 + column]: each step moves kSolveKC consecutive levels
+// (32 bytes, one sector) of 32 / kSolveKC columns, so every global sector
+// is used whole; the 33-wide rows keep the shared-memory side free of bank
+// conflicts.  Four-level chunks keep a block's shared memory at 6.6 KB so
+// that 24 one-warp blocks fit on an SM.
+#ifndef GRIST_SOLVE_KC
+#define GRIST_SOLVE_KC 4          // levels per staged chunk (1, 2, 4 or 8)
+#endif
+#ifndef GRIST_SOLVE_MIN_BLOCKS
+#define GRIST_SOLVE_MIN_BLOCKS 24 // resident one-warp blocks per SM the registers must allow
+#endif
 constexpr int kSolveCols = 32;
-constexpr int kSolveKC = 8;
+constexpr int kSolveKC = GRIST_SOLVE_KC;
+constexpr int kSolveColsPerStep = 32 / kSolveKC;
 constexpr int kRow = 33;
 constexpr int kStage = kSolveKC * kRow;
+constexpr int kSolveMinBlocks = GRIST_SOLVE_MIN_BLOCKS;
+static_assert(kSolveKC == 1 || kSolveKC == 2 || kSolveKC == 4 || kSolveKC == 8, "chunk of 1, 2, 4 or 8 levels");
 
 __device__ __forceinline__ void stage_in(const double *X, size_t S, int col0, int ncol, int k0, int nk, double *sm) {
-    const int lane = threadIdx.x & 31, kk = lane & 7;
+    const int lane = threadIdx.x & 31, kk = lane % kSolveKC;
 #pragma unroll
-    for (int it = 0; it < kSolveCols / 4; it++) {
-        const int col = it * 4 + (lane >> 3);
+    for (int it = 0; it < kSolveKC; it++) {
+        const int col = it * kSolveColsPerStep + lane / kSolveKC;
         double v = 0.0;
         if (col < ncol && kk < nk) v = X[(size_t)(col0 + col) * S + k0 + kk];
         sm[kk * kRow + col] = v;
@@ -556,17 +567,17 @@ __device__ __forceinline__ void stage_in(const double *X, size_t S, int col0, in
 }
 
 __device__ __forceinline__ void stage_out(double *X, size_t S, int col0, int ncol, int k0, int nk, const double *sm) {
-    const int lane = threadIdx.x & 31, kk = lane & 7;
+    const int lane = threadIdx.x & 31, kk = lane % kSolveKC;
 #pragma unroll
-    for (int it = 0; it < kSolveCols / 4; it++) {
-        const int col = it * 4 + (lane >> 3);
+    for (int it = 0; it < kSolveKC; it++) {
+        const int col = it * kSolveColsPerStep + lane / kSolveKC;
         if (col < ncol && kk < nk) X[(size_t)(col0 + col) * S + k0 + kk] = sm[kk * kRow + col];
     }
 }
 
 // Implicit part of Eqs. 6-7 and Eq. 9, one thread per column (a block is
 // one warp of 32 consecutive columns), FP64.  Column data moves through
-// shared memory in 8-level chunks (coalesced global access).
+// shared memory in kSolveKC-level chunks (whole-sector global access).
 // Equation of state relative to the t^n state (1/th_r, phi_r, p_r):
 //   p** = p_r ((th dphi_r) / (th_r dphi**))^gamma     (pow_near1)
 // linearised about phi**: p_k = p**_k - C_k (w_k - w_{k+1}),
@@ -578,7 +589,7 @@ __device__ __forceinline__ void stage_out(double *X, size_t S, int col0, int nco
 // (interface value 1 at top and bottom) for the momentum equation.  phi_out
 // may be phi_r and p may be p_r (the last stage writes the state in place):
 // each block reads all reference values of its columns before writing them.
-__global__ void __launch_bounds__(32) k_nh_solve(DevMesh m, DyPar d, const double *__restrict__ wst,
+__global__ void __launch_bounds__(32, kSolveMinBlocks) k_nh_solve(DevMesh m, DyPar d, const double *__restrict__ wst,
                                                  const double *__restrict__ phst, const double *__restrict__ th,
                                                  const double *__restrict__ rth_r, const double *phi_r,
                                                  const double *p_r, const double *__restrict__ ps, double dts,
