@@ -174,7 +174,7 @@ int grist_tracer_step(grist_mesh mesh, const grist_tracer_batch *batch, double d
 
 /* Launch configuration of the tracer step (the batching design of this
  * library; no counterpart in the paper).
- *   block               threads per block (64..1024, multiple of 32)
+ *   block               threads per block (64..512, multiple of 32)
  *   tracers_per_thread  tracers one thread carries through a phase (>= 1)
  *   persistent          0 = one launch per phase; 1 = one cooperative
  *                       persistent launch per step with grid barriers

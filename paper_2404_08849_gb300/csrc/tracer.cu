@@ -100,6 +100,9 @@ void tracer_ctx_free(TracerCtx *c) {
 namespace {
 
 constexpr long long kBarrierSpinLimit = 20000000;  // x ~64 ns sleep: about a second
+// Largest block of the work-list kernels (their register use, at most 128
+// per thread, lets every block up to this size launch).
+constexpr int kTracerMaxBlock = 512;
 
 struct Batch {
     const MemberDev *mem;
@@ -1005,7 +1008,7 @@ int dispatch(grist_mesh_s *h, const grist_tracer_batch *b, double dt, cudaStream
 
 int check_tuning(const grist_tracer_tuning *t) {
     if (!t) return GRIST_EINVAL;
-    if (t->block < 64 || t->block > 1024 || t->block % 32) return GRIST_EINVAL;
+    if (t->block < 64 || t->block > kTracerMaxBlock || t->block % 32) return GRIST_EINVAL;
     if (t->tracers_per_thread < 1 || t->tracers_per_thread > 64) return GRIST_EINVAL;
     if (t->persistent != 0 && t->persistent != 1) return GRIST_EINVAL;
     if (t->use_graph != 0 && t->use_graph != 1) return GRIST_EINVAL;

@@ -164,3 +164,15 @@ def test_bounded_wait_times_out_and_context_survives(G, mesh_cache):
     assert O.max_rel_diff(got, ref) <= FP64_TOL
     assert mesh.last_status() == 0
     mesh.close()
+
+
+def test_tuning_rejects_unlaunchable_block(G, mesh_cache):
+    """Blocks above 512 threads are refused when set, not at launch."""
+    m = mesh_cache(3)
+    mesh = G.Mesh(m)
+    for bad in (1024, 544, 48, 100):
+        with pytest.raises(G.GristError):
+            mesh.set_tracer_tuning(block=bad, tracers_per_thread=4)
+    mesh.set_tracer_tuning(block=512, tracers_per_thread=8)
+    assert mesh.tracer_tuning()["block"] == 512
+    mesh.close()
