@@ -370,6 +370,19 @@ int grist_selftest_bounded_wait(grist_mesh mesh, int64_t spin_limit, void *strea
  * frees 32 bytes of device memory.  No counterpart in the paper. */
 int grist_selftest_conversions(uint64_t n_random, uint64_t seed, uint64_t *out_checked, uint64_t *out_mismatch);
 
+/* Diagnostic: check the library's FMA-refined approximate reciprocal (used
+ * in the FP64 column solve in place of the correctly rounded one) against
+ * the IEEE quotient 1.0 / x on n pseudo-random binary64 values (splitmix64
+ * of seed + i; any sign and fraction, |x| in [2^-1020, 2^1021)), on the
+ * current device.
+ *   out_checked     host, out: values checked.
+ *   out_over_1ulp   host, out: results more than one ulp from 1.0 / x.
+ *   out_max_ulp     host, out: largest distance seen, in ulps.
+ * Synchronous (default stream); allocates and frees 24 bytes of device
+ * memory.  No counterpart in the paper. */
+int grist_selftest_reciprocal(uint64_t n, uint64_t seed, uint64_t *out_checked, uint64_t *out_over_1ulp,
+                              uint64_t *out_max_ulp);
+
 /* Flags raised by the steps since the previous call (read after the stream
  * has been synchronised; synchronises the device and clears the flags). */
 int grist_last_step_status(grist_mesh mesh, uint32_t *flags);

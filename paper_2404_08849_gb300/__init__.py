@@ -56,6 +56,16 @@ def selftest_conversions(n_random=1 << 28, seed=2404_08849):
     return {"f2d": (int(checked[0]), int(bad[0])), "d2f": (int(checked[1]), int(bad[1]))}
 
 
+def selftest_reciprocal(n=1 << 28, seed=2404_08849):
+    """grist_selftest_reciprocal: the FMA-refined reciprocal against 1.0 / x.
+    Returns (checked, results more than one ulp off, largest ulp distance)."""
+    lib = _lib.load()
+    c, b, w = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    _lib.check("grist_selftest_reciprocal", lib.grist_selftest_reciprocal(int(n), int(seed), ctypes.byref(c),
+                                                                          ctypes.byref(b), ctypes.byref(w)))
+    return int(c.value), int(b.value), int(w.value)
+
+
 class Mesh:
     """Device copy of one icosahedral Voronoi mesh (``grist_mesh_create``)."""
 

@@ -74,6 +74,8 @@ EXPORTS = {
     "grist_weighted_sum_noalloc": ([_V, _V, ctypes.c_int64, _V, _V], ctypes.c_int),
     "grist_selftest_conversions": ([ctypes.c_uint64, ctypes.c_uint64, _P(ctypes.c_uint64), _P(ctypes.c_uint64)],
                                    ctypes.c_int),
+    "grist_selftest_reciprocal": ([ctypes.c_uint64, ctypes.c_uint64, _P(ctypes.c_uint64), _P(ctypes.c_uint64),
+                                   _P(ctypes.c_uint64)], ctypes.c_int),
 }
 
 _lib = None

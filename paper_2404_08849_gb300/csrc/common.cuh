@@ -112,6 +112,20 @@ __device__ __forceinline__ float fmax_(float a, float b) { return fmaxf(a, b); }
 // general division sequence).
 __device__ __forceinline__ double rcp(double x) { return __drcp_rn(x); }
 
+// Reciprocal within one ulp from three FMAs: the approximate reciprocal of
+// PTX (rcp.approx.ftz.f64, about 20 correct bits) refined by one cubically
+// convergent Newton-Raphson step, y (1 + e + e^2) with e = 1 - x y, so the
+// seed's relative error e shrinks to e^3 plus the rounding of the last FMA.
+// For normal x with |x| in [2^-1020, 2^1020] (checked against 1.0 / x by
+// grist_selftest_reciprocal); used where an FP64 instruction count matters
+// more than correct rounding.
+__device__ __forceinline__ double rcp_nr(double x) {
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    const double e = fma(-x, y, 1.0);
+    return fma(fma(e, e, e), y, y);
+}
+
 // Conversions between binary32 and binary64 in integer arithmetic.  On this
 // GPU the hardware conversion instructions issue on the FP64 pipe, the
 // scarce resource of the mixed-precision kernels, so the IEEE-754 fields are

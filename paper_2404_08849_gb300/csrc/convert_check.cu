@@ -1,5 +1,7 @@
-// convert_check.cu - self-test of the integer binary32 <-> binary64
-// conversions (f2d, d2f in common.cuh) against the hardware conversions.
+// convert_check.cu - self-tests of the arithmetic helpers in common.cuh:
+// the integer binary32 <-> binary64 conversions (f2d, d2f) against the
+// hardware conversions, and the Newton-Raphson reciprocal (rcp_nr) against
+// the IEEE quotient 1.0 / x.
 // Each kernel compares both results in-register and counts disagreements,
 // so the 2^32-pattern sweeps need no input or output buffers.
 #include "common.cuh"
@@ -77,10 +79,56 @@ __global__ void k_check_d2f(unsigned long long n_random, unsigned long long seed
     atomicAdd(out + 3, bad);
 }
 
+// out[0] checked, out[1] results more than one ulp from 1.0 / x, out[2]
+// the largest distance in ulps (as a count of binary64 steps)
+__global__ void k_check_rcp(unsigned long long n, unsigned long long seed, unsigned long long *out) {
+    unsigned long long cnt = 0, bad = 0, worst = 0;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        unsigned long long b = splitmix64(seed + i);
+        // exponent in [3, 2043] (|x| in [2^-1020, 2^1021)), any sign and fraction
+        const unsigned long long ex = 3ull + (splitmix64(b ^ 0x5bd1e995ull) % 2041ull);
+        b = (b & 0x800fffffffffffffull) | (ex << 52);
+        const double x = __longlong_as_double((long long)b);
+        const long long a = __double_as_longlong(rcp_nr(x)), r = __double_as_longlong(1.0 / x);
+        const unsigned long long d = (unsigned long long)(a > r ? a - r : r - a);
+        bad += d > 1ull;
+        worst = d > worst ? d : worst;
+        cnt++;
+    }
+    atomicAdd(out + 0, cnt);
+    atomicAdd(out + 1, bad);
+    atomicMax(out + 2, worst);
+}
+
 }  // namespace
 }  // namespace grist
 
 using namespace grist;
+
+extern "C" int grist_selftest_reciprocal(uint64_t n, uint64_t seed, uint64_t *out_checked, uint64_t *out_over_1ulp,
+                                         uint64_t *out_max_ulp) {
+    if (!out_checked || !out_over_1ulp || !out_max_ulp) return GRIST_EINVAL;
+    unsigned long long *d = nullptr;
+    if (cudaMalloc(&d, 3 * sizeof(unsigned long long)) != cudaSuccess) return GRIST_ENOMEM;
+    unsigned long long h[3] = {0, 0, 0};
+    int rc = GRIST_OK;
+    if (cudaMemset(d, 0, sizeof(h)) != cudaSuccess) rc = GRIST_ECUDA;
+    if (rc == GRIST_OK) {
+        int dev = 0, nsm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        k_check_rcp<<<(unsigned)(nsm > 0 ? nsm * 8 : 1024), 256>>>((unsigned long long)n, (unsigned long long)seed, d);
+        if (cudaGetLastError() != cudaSuccess) rc = GRIST_ECUDA;
+    }
+    if (rc == GRIST_OK && cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) rc = GRIST_ECUDA;
+    cudaFree(d);
+    if (rc != GRIST_OK) return rc;
+    *out_checked = h[0];
+    *out_over_1ulp = h[1];
+    *out_max_ulp = h[2];
+    return GRIST_OK;
+}
 
 extern "C" int grist_selftest_conversions(uint64_t n_random, uint64_t seed, uint64_t *out_checked,
                                           uint64_t *out_mismatch) {

@@ -92,8 +92,8 @@ template <int N> __device__ __forceinline__ double horner(double x, const Binom 
     return s;
 }
 
-__device__ __forceinline__ double pow_near1(double r, double g, const Binom &B, unsigned mask) {
-    const double x = r - 1.0;
+// (1 + x)^g for a small x given directly.
+__device__ __forceinline__ double pow1p_near0(double x, double g, const Binom &B, unsigned mask) {
     // high word of |x|: exponent and leading fraction bits, monotone in |x|
     const unsigned hx = (unsigned)__double2hiint(x) & 0x7fffffffu;
     const unsigned hm = __reduce_max_sync(mask, hx);
@@ -101,8 +101,12 @@ __device__ __forceinline__ double pow_near1(double r, double g, const Binom &B, 
     if (hm < 0x3f300000u) return horner<5>(x, B);    // 2^-12
     if (hm < 0x3f500000u) return horner<6>(x, B);    // 2^-10
     if (hm < 0x3f700000u) return horner<8>(x, B);    // 2^-8
-    if (hx > 0x3f900000u || (hx == 0x3f900000u && __double2loint(x) != 0)) return pow(r, g);
+    if (hx > 0x3f900000u || (hx == 0x3f900000u && __double2loint(x) != 0)) return pow(1.0 + x, g);
     return horner<10>(x, B);
+}
+
+__device__ __forceinline__ double pow_near1(double r, double g, const Binom &B, unsigned mask) {
+    return pow1p_near0(r - 1.0, g, B, mask);
 }
 
 Binom binomial(double g) {
@@ -628,7 +632,7 @@ __global__ void __launch_bounds__(32, kSolveMinBlocks) k_nh_solve(DevMesh m, DyP
                 const int j = k0 + kk;
                 const int o = kk * kRow + lane;
                 const double fbot = sA[0 * kStage + o], rbot = sA[1 * kStage + o];
-                const double rdfj = rcp(ftop - fbot);
+                const double rdfj = rcp_nr(ftop - fbot);
                 const double pstj = sA[4 * kStage + o] *
                                     pow_near1(sA[2 * kStage + o] * sA[3 * kStage + o] * ((rtop - rbot) * rdfj),
                                               d.gamma, bg_pos, amask);
@@ -643,11 +647,11 @@ __global__ void __launch_bounds__(32, kSolveMinBlocks) k_nh_solve(DevMesh m, DyP
                     const double rhs = sA[5 * kStage + o] + fma(aj, pstj - pst_prev, -bg);
                     const int r = j - 1;
                     if (r == 0) {
-                        const double rb = rcp(b);
+                        const double rb = rcp_nr(b);
                         cp[0] = c * rb;
                         dd[0] = rhs * rb;
                     } else {
-                        const double rden = rcp(fma(-a, cp[r - 1], b));
+                        const double rden = rcp_nr(fma(-a, cp[r - 1], b));
                         cp[r] = c * rden;
                         dd[r] = fma(-a, dd[r - 1], rhs) * rden;
                     }
@@ -694,7 +698,7 @@ __global__ void __launch_bounds__(32, kSolveMinBlocks) k_nh_solve(DevMesh m, DyP
                 const double w_top = sA[1 * kStage + o];
                 const double w_bot = (kk + 1 < nk) ? sA[1 * kStage + o + kRow] : sA[6 * kStage + lane];
                 const double phi_bot = (k + 1 < L) ? fma(bg, w_bot, sA[o]) : ldg(d.phis + i);
-                const double pk = pst[k] * pow_near1(fma(bg * (w_top - w_bot), rdf[k], 1.0), -d.gamma, bg_neg, amask);
+                const double pk = pst[k] * pow1p_near0(bg * (w_top - w_bot) * rdf[k], -d.gamma, bg_neg, amask);
                 double dcur = 1.0;
                 if (k > 0) {
                     dcur = (pk - pprev) * (ldg(d.rdBi + k) * rdps);

@@ -23,3 +23,17 @@ def test_integer_conversions_equal_hardware():
     n_nonfinite = 2 * (1 << 23)
     assert checked == 4 * ((1 << 32) - n_nonfinite) + n_nonfinite + (1 << 28)
     assert bad == 0
+
+
+def test_fma_reciprocal_within_one_ulp():
+    """The column solve's reciprocal (approximate seed + one cubic
+    Newton-Raphson step) stays within one ulp of the IEEE quotient 1.0 / x
+    over 2^28 pseudo-random normal doubles of every sign and magnitude."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    import paper_2404_08849_gb300 as G
+    G.load()
+    checked, over, worst = G.selftest_reciprocal(n=1 << 28, seed=240408849)
+    assert checked == 1 << 28
+    assert over == 0 and worst <= 1
