@@ -230,10 +230,13 @@ typedef struct {
  *   dpi_theta   [nC][ld] double, mass-weighted potential temperature
  *   w, phi      [nC][ld_int] double, NH vertical velocity and geopotential
  *               at interfaces (ignored by the hydrostatic step)
- *   mass_flux_accum [nE][ld] double or NULL: the final-stage mass flux of
- *               the step is added to it (time-mean flux for the tracer,
- *               Sec. 2.3 "accumulated and averaged")
- *   accum_weight device double or NULL: incremented by 1 per step.
+ *   mass_flux_accum [nE][ld] double or NULL: accum_scale times the
+ *               final-stage mass flux of the step is added to it (time-mean
+ *               flux for the tracer, Sec. 2.1 / Sec. 2.3 "accumulated and
+ *               averaged"): n steps with accum_scale = 1/n leave the mean
+ *               flux over the n steps, the flux that carries the tracers
+ *               over one tracer step of n dycore time steps.
+ *   accum_weight device double or NULL: accum_scale is added per step.
  *   dpi_start   [nC][ld] double or NULL: receives the layer mass dpi at
  *               the start of the step (the tracer solver's dpi^n).
  *   p_nh        [nC][ld] double or NULL (NH only): the non-hydrostatic
@@ -242,7 +245,9 @@ typedef struct {
  *               evaluating the equation of state; on return it holds the
  *               pressure of the new state and p_nh_valid is set to 1.  Set
  *               p_nh_valid to 0 whenever dpi_theta or phi change outside
- *               the step. */
+ *               the step.
+ *   accum_scale weight of this step's flux in mass_flux_accum and
+ *               accum_weight; 0 is read as 1. */
 typedef struct {
     void *u;
     double *ps;
@@ -254,6 +259,7 @@ typedef struct {
     double *dpi_start;
     double *p_nh;
     int32_t p_nh_valid;
+    double accum_scale;
 } grist_dycore_state;
 
 /* Hydrostatic step: WS-RK3, Mesinger forward-backward inside each stage

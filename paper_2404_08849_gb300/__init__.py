@@ -221,6 +221,7 @@ class Mesh:
         s.dpi_start = _ptr(state.get("dpi_start"))
         s.p_nh = _ptr(state.get("p_nh"))
         s.p_nh_valid = 1 if state.get("p_nh_valid") else 0
+        s.accum_scale = float(state.get("accum_scale", 1.0))
         _lib.check(fn, getattr(lib, fn)(self.handle, ctypes.byref(s), ctypes.byref(params.c), _prec(prec),
                                         float(dt), _stream_handle(stream)))
         if state.get("p_nh") is not None:

@@ -51,7 +51,7 @@ class DycoreParams(ctypes.Structure):
 
 class DycoreState(ctypes.Structure):
     _fields_ = [("u", _V), ("ps", _V), ("dpi_theta", _V), ("w", _V), ("phi", _V), ("mass_flux_accum", _V),
-                ("accum_weight", _V), ("dpi_start", _V), ("p_nh", _V), ("p_nh_valid", _I)]
+                ("accum_weight", _V), ("dpi_start", _V), ("p_nh", _V), ("p_nh_valid", _I), ("accum_scale", _D)]
 
 
 EXPORTS = {

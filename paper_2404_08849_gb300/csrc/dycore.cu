@@ -125,13 +125,15 @@ Binom binomial(double g) {
 // the warp walks its edges with the lanes over levels, forming the product
 // in the mass-flux type and the edge's column sum sum_k F_k by a fixed
 // butterfly (both cells of the edge later use the same value, so the global
-// mass change cancels to round-off).  In the final stage the flux is
-// accumulated for the tracer solver (Sec. 2.3: single computed, saved
-// double).
+// mass change cancels to round-off).  In the final stage fscale times the
+// flux is accumulated for the tracer solver (Sec. 2.3: single computed,
+// saved double).
 template <class P>
 __global__ void k_mass_edge(DevMesh m, DyPar d, const double *__restrict__ ps_s,
                             const typename P::TU *__restrict__ u_s, typename P::TM *__restrict__ F,
-                            double *__restrict__ Facc, double *__restrict__ rsum_e, double *__restrict__ Fcol) {
+                            double *__restrict__ Facc, double fscale, double *__restrict__ rsum_e,
+                            double *__restrict__ Fcol) {
+    const bool scaled = fscale != 1.0;
     using TM = typename P::TM;
     const int e0 = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32;
     const int lane = threadIdx.x & 31;
@@ -156,7 +158,7 @@ __global__ void k_mass_edge(DevMesh m, DyPar d, const double *__restrict__ ps_s,
                 const TM f = (TM)ldg(d.dB + k) * hs * cv<TM>(u_s[x]);
                 F[x] = f;
                 col += (double)f;
-                if (Facc) Facc[x] += (double)f;
+                if (Facc) Facc[x] += scaled ? fscale * (double)f : (double)f;
             }
             col = col_reduce(col);
             if (lane == j) col64 = col;
@@ -167,7 +169,7 @@ __global__ void k_mass_edge(DevMesh m, DyPar d, const double *__restrict__ ps_s,
                 const TM f = ldg(d.dBf + k) * hs * cv<TM>(u_s[x]);
                 F[x] = f;
                 col = f2_add(col, F2{cv<float>(f), 0.f});
-                if (Facc) Facc[x] += cv<double>(f);
+                if (Facc) Facc[x] += scaled ? fscale * cv<double>(f) : cv<double>(f);
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) col = f2_add(col, f2_shfl_xor(col, o));
@@ -809,6 +811,7 @@ int dycore_step(grist_mesh_s *h, grist_dycore_state *S, const grist_dycore_param
                    gVx = grid_for(m.nV, kBlock), gE32 = grid_for((long long)m.nE + 31, kBlock),
                    gC32 = grid_for((long long)m.nC + 31, kBlock);
     const double dts[3] = {dt / 3.0, dt / 2.0, dt};
+    const double ascale = S->accum_scale != 0.0 ? S->accum_scale : 1.0;
 
     GRIST_CUDA_TRY(cudaMemcpyAsync(psN, S->ps, m.nC * sizeof(double), cudaMemcpyDeviceToDevice, st));
     // t^n pressure: carried in the state when valid, else from the EOS
@@ -836,7 +839,7 @@ int dycore_step(grist_mesh_s *h, grist_dycore_state *S, const grist_dycore_param
     for (int s3 = 0; s3 < 3; s3++) {
         const double h3 = dts[s3];
         GRIST_LAUNCH(h, PN("k_mass_edge"), st, k_mass_edge<P><<<gE32, kBlock, 0, st>>>(
-            m, d, ps_in, u_in, F, s3 == 2 ? S->mass_flux_accum : nullptr, rsum, fcol));
+            m, d, ps_in, u_in, F, s3 == 2 ? S->mass_flux_accum : nullptr, ascale, rsum, fcol));
         GRIST_LAUNCH(h, PN("k_mass_col"), st, k_mass_col<P><<<gC32, kBlock, 0, st>>>(
             m, d, F, fcol, ps_in, psN, ps_outs[s3], th_in, theta, Mv, h3, s3 == 0 ? S->dpi_start : nullptr, rdps,
             (NH && s3 == 0) ? rthn : nullptr));
@@ -869,7 +872,7 @@ int dycore_step(grist_mesh_s *h, grist_dycore_state *S, const grist_dycore_param
         w_in = w_outs[s3];
         phi_in = phi_outs[s3];
     }
-    if (S->accum_weight) GRIST_LAUNCH(h, PN("k_add_scalar"), st, k_add_scalar<<<1, 32, 0, st>>>(S->accum_weight, 1.0));
+    if (S->accum_weight) GRIST_LAUNCH(h, PN("k_add_scalar"), st, k_add_scalar<<<1, 32, 0, st>>>(S->accum_weight, ascale));
     if (cudaGetLastError() != cudaSuccess) return GRIST_ECUDA;
     if (NH && S->p_nh) S->p_nh_valid = 1;
     return GRIST_OK;
@@ -891,6 +894,7 @@ int check(grist_mesh h, grist_dycore_state *S, const grist_dycore_params *prm, g
     if (!(prm->pi_top >= 0) || !(prm->p0 > 0) || !(prm->rd > 0) || !(prm->cp > prm->rd) || !(prm->g > 0))
         return GRIST_EINVAL;
     if (nh && !(prm->offcentre_beta > 0 && prm->offcentre_beta <= 1)) return GRIST_EINVAL;
+    if (!std::isfinite(S->accum_scale) || S->accum_scale < 0) return GRIST_EINVAL;
     return GRIST_OK;
 }
 
