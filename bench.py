@@ -82,7 +82,7 @@ def algorithmic_bytes(name, nC, nE, nV, L, T, prec):
 
 
 # FP64 work of the kernels of the mixed step that are bound by the FP64 pipe
-# (ncu: sm__pipe_fp64_cycles_active 80-90 % of peak, DRAM well below its
+# (ncu: sm__pipe_fp64_cycles_active 64-92 % of peak, DRAM well below its
 # peak): FP64 flops = 2 DFMA + DADD + DMUL executed thread instructions, and
 # DRAM bytes (read + write), per unit of work, both counted by ncu on the
 # level-7 mesh (163,842 cells, 60 levels) of the same workload and step.
@@ -90,13 +90,15 @@ def algorithmic_bytes(name, nC, nE, nV, L, T, prec):
 # (L + 1 per column) "i".  Per-launch figures scale with the units processed.
 FP64_WORK_MIX = {
     # kernel: (unit, FP64 flop per unit, DRAM bytes per unit)
-    "k_nh_solve": ("c", 101.6, None),
-    "k_momentum": ("e", 19.9, 36.6),
-    "k_nh_explicit": ("i", 28.2, 73.1),
-    "k_ke": ("c", 18.0, 18.3),
-    "k_mass_col": ("c", 12.4, 36.7),
-    "k_mass_edge": ("e", 0.55, 11.4),
-    "k_eos": ("c", 93.0, 21.2),
+    "k_nh_solve": ("c", 66.73, 282.8),
+    "k_momentum": ("e", 19.88, 36.6),
+    "k_nh_explicit": ("i", 28.20, 73.1),
+    "k_ke": ("c", 18.00, 18.3),
+    "k_mass_col": ("c", 12.41, 41.0),
+    "k_vort": ("v", 3.00, 9.2),
+    "k_eos": ("c", 93.0, 21.1),
+    "k_tr_div": ("c", 12.00, 31.6),
+    "k_tr_lowres": ("c", 14.00, 72.1),
 }
 
 SM_COUNT = 152
@@ -367,6 +369,9 @@ def gpu_arm(args, wl):
                         "peak": round(f64_peak, 4), "unit": "TFLOP/s",
                         "frac": round(dom["fp64_tflops"] / f64_peak, 4),
                         "traffic": (int(w[2] * units) if w[2] is not None else None),
+                        "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per unit on the "
+                                          "level-7 case, times this launch's units",
+                        "algorithmic_bytes": algorithmic_bytes(dom["kernel"], nC, nE, nV, L, T, args.prec),
                         "work": "FP64 flop per launch %.4g (%.1f per unit, ncu-counted)" % (w[1] * units, w[1]),
                         "peak_source": "derived: %d SMs x %d DFMA/clk x 2 flop x %.0f MHz" % (
                             SM_COUNT, DFMA_PER_SM_CLK, sm_max),
@@ -374,6 +379,34 @@ def gpu_arm(args, wl):
         elif hbm_ctx:
             roofline = dict({"bound": "hbm", "kernel": dom["kernel"], "traffic": None}, **hbm_ctx)
     launches_per_step = sum(k["launches"] for k in kernels) / max(K, 1)
+
+    # time splitting: n dycore steps accumulate the mean mass flux
+    # (accum_scale = 1/n), then one tracer step of n dycore time steps
+    split = None
+    if T and args.split > 1:
+        n = args.split
+        s = make_state(torch, host, args.prec, device, nE, nC, L, T, wl["nh"])
+        s["accum_scale"] = 1.0 / n
+        dpi0 = s.pop("dpi_start")
+
+        def window():
+            s["mass_flux_accum"].zero_()
+            for i in range(n):
+                s["dpi_start"] = dpi0 if i == 0 else None
+                if wl["nh"]:
+                    mesh.dycore_step_nh(s, P, wl["dt"], prec=args.prec)
+                else:
+                    mesh.dycore_step_hydro(s, P, wl["dt"], prec=args.prec)
+            mesh.tracer_step([{"q": s["q"], "dpi": dpi0, "mass_flux": s["mass_flux_accum"], "n_levels": L}],
+                             n * wl["dt"], prec=args.prec, limiter=True)
+        for _ in range(max(1, W // n)):
+            window()
+        secs_w = allmax(timed(torch, window, K, dist))
+        split = {"dycore_steps_per_tracer_step": n, "tracer_dt_s": n * wl["dt"],
+                 "value": world * nC * L * n * K / secs_w, "unit": UNIT + " (dycore steps)",
+                 "ms_per_window": secs_w / K * 1e3, "status_flags": mesh.last_status()}
+        del s, dpi0
+        torch.cuda.empty_cache()
 
     mesh.close()
     del mesh
@@ -397,7 +430,7 @@ def gpu_arm(args, wl):
                "fp64": ({"value": total_units / secs_64, "ms_per_step": secs_64 / K * 1e3,
                          "speedup_mix_over_fp64": secs_64 / secs_mix} if secs_64 else None),
                "roofline": roofline, "kernels": kernels[:12], "gpu_launches": int(round(launches_per_step * K)),
-               "batched_ensemble": batched,
+               "batched_ensemble": batched, "split_coupling": split,
                "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
                "status_flags": {"mix": st_mix, "fp64": st_64},
                "dry_mass_end": {"mix": dry_mix, "fp64": dry_64}}
@@ -527,6 +560,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="default tracer launch configuration")
+    ap.add_argument("--split", type=int, default=3,
+                    help="dycore steps per tracer step of the time-splitting measurement (1 = skip it)")
     ap.add_argument("--mesh-level", type=int, default=None,
                     help="override the workload's mesh level (small cases for profiling)")
     ap.add_argument("--cpu-level", type=int, default=8)
