@@ -116,6 +116,27 @@ def units_of(kind, nC, nE, nV, L):
 
 
 # ---------------------------------------------------------------------------
+# multi-rank aggregation (one process per GPU; each rank times its own K steps)
+
+def reduce_max(x, dist, device):
+    """The largest x over all ranks (every rank passes its own; None and a
+    single-process run pass through).  device: where the collective's
+    tensor lives (the rank's GPU for NCCL, "cpu" for gloo)."""
+    if dist is None or x is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, secs_max):
+    """Whole-job throughput: the units every rank processed, over the
+    slowest rank's time (weak scaling: each rank has the same work)."""
+    return world * units_per_rank / secs_max
+
+
+# ---------------------------------------------------------------------------
 # clocks during the timed region
 
 class ClockSampler:
@@ -309,27 +330,17 @@ def gpu_arm(args, wl):
                 v.copy_(s[k], non_blocking=True)
         for _ in range(W):
             e2e_step()
-        secs_e2e = timed(torch, e2e_step, K, dist)
-        e2e = {"value": nC * L * K / secs_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(h2d)}
+        secs_e2e = reduce_max(timed(torch, e2e_step, K, dist), dist, device)
+        e2e = {"value": whole_job_rate(nC * L * K, world, secs_e2e), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(h2d)}
         del s, pinned
 
     # max over ranks
-    def allmax(x):
-        if dist is None or x is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-    secs_mix = allmax(secs_mix)
-    secs_64 = allmax(secs_64)
-    if e2e is not None and dist is not None:
-        e2e["value"] = world * nC * L * K / allmax(nC * L * K / e2e["value"])
-    elif e2e is not None:
-        pass
+    secs_mix = reduce_max(secs_mix, dist, device)
+    secs_64 = reduce_max(secs_64, dist, device)
 
     total_units = world * nC * L * K
-    value = total_units / secs_mix
+    value = whole_job_rate(nC * L * K, world, secs_mix)
 
     # roofline of the dominant kernel of the mixed step
     peaks = {}
@@ -401,9 +412,9 @@ def gpu_arm(args, wl):
                              n * wl["dt"], prec=args.prec, limiter=True)
         for _ in range(max(1, W // n)):
             window()
-        secs_w = allmax(timed(torch, window, K, dist))
+        secs_w = reduce_max(timed(torch, window, K, dist), dist, device)
         split = {"dycore_steps_per_tracer_step": n, "tracer_dt_s": n * wl["dt"],
-                 "value": world * nC * L * n * K / secs_w, "unit": UNIT + " (dycore steps)",
+                 "value": whole_job_rate(nC * L * n * K, world, secs_w), "unit": UNIT + " (dycore steps)",
                  "ms_per_window": secs_w / K * 1e3, "status_flags": mesh.last_status()}
         del s, dpi0
         torch.cuda.empty_cache()
@@ -470,13 +481,10 @@ def batched_ensemble(G, torch, device, args, dist):
             for d in dev[:2]]
     status = mesh.last_status()
     world = int(os.environ.get("WORLD_SIZE", "1"))
-    if dist is not None:
-        t = torch.tensor([secs], dtype=torch.float64, device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        secs = float(t.item())
+    secs = reduce_max(secs, dist, device)
     out = {"workload": "16-member uneven tracer ensemble, L7 mesh 163842 cells, T in {1,4,10,25}, "
                        "L in {30,60}, FP32 tracers + FCT, dt %.1f s" % dt,
-           "value": world * units * args.steps / secs, "unit": "tracer-cell-level-steps/s",
+           "value": whole_job_rate(units * args.steps, world, secs), "unit": "tracer-cell-level-steps/s",
            "ms_per_step": secs / args.steps * 1e3, "tuning": tuning, "autotune_ms_per_step": tune_ms,
            "members": [[mb["n_tracers"], mb["n_levels"]] for mb in members], "status_flags": status}
     mesh.close()
