@@ -222,7 +222,27 @@ typedef struct {
     double offcentre_beta;         /* implicit weight of the NH vertical terms (0.5..1) */
     const double *b_interface;     /* host, [L+1] */
     const double *phi_surface;     /* device, [nC] surface geopotential */
+    uint32_t emulate_fp32_rows;    /* GRIST_ROW_* bits; 0 = none (see below) */
 } grist_dycore_params;
+
+/* Rows of the precision map (Sec. 2.3) for the iterative precision search
+ * of Sec. 2.2 (Eqs. 1-2).  With a bit set, every FP64 value of that row is
+ * rounded to binary32 where it is produced (storage-rounding emulation:
+ * the arithmetic between roundings stays in the policy's type), so the
+ * accuracy cost of a single-precision row can be measured on the FP64
+ * path without a kernel per combination.  Values already single in the
+ * chosen policy are unaffected.  0 leaves every result unchanged. */
+#define GRIST_ROW_MASS_FLUX 0x001u  /* dpi V at edges and its layer divergence (Eq. 3) */
+#define GRIST_ROW_WIND 0x002u       /* u_n after each stage update (Eq. 5) */
+#define GRIST_ROW_PV_FLUX 0x004u    /* vertex and edge PV, tangential PV flux (Eq. 5) */
+#define GRIST_ROW_KE_GRAD 0x008u    /* cell kinetic energy (Eq. 5) */
+#define GRIST_ROW_VADV_U 0x010u     /* vertical advection of momentum (Eq. 5) */
+#define GRIST_ROW_PGF 0x020u        /* pressure gradient and gravity terms, inputs and sum (Eq. 5) */
+#define GRIST_ROW_THETA 0x040u      /* theta and its edge flux (Eq. 4) */
+#define GRIST_ROW_DPI_PV 0x080u     /* vertex layer mass dividing the PV (Sec. 2.3 "green") */
+#define GRIST_ROW_EOS 0x100u        /* p, alpha, layer phi, dp/dpi (Eqs. 8-9) */
+#define GRIST_ROW_NH_ADV 0x200u     /* advection of w and phi (Eqs. 6-7) */
+#define GRIST_ROW_ALL 0x3ffu
 
 /* Prognostic state (device, in/out, caller-owned).
  *   u           [nE][ld] edge-normal wind: double (FP64) or float (mixed)
@@ -275,6 +295,16 @@ int grist_dycore_step_hydro(grist_mesh mesh, grist_dycore_state *state, const gr
  * geopotential.  Asynchronous on `stream`. */
 int grist_dycore_step_nh(grist_mesh mesh, grist_dycore_state *state, const grist_dycore_params *params,
                          grist_precision prec, double dt, void *stream);
+
+/* Diagnostic: relative vorticity at the vertices, zeta_v = (1/A_v) sum over
+ * the vertex's edges of t(e,v) dc_e u_e, on every level (the velocity
+ * diagnostic of Eq. 1).
+ *   u       device, in, [nE][ld] double (u_prec GRIST_FP64) or float
+ *           (GRIST_MIX / GRIST_MIX_DBL_MASS).
+ *   vor     device, out, [nV][ld] double.
+ * Asynchronous on `stream`. */
+int grist_diag_vorticity(grist_mesh mesh, const void *u, grist_precision u_prec, int32_t n_levels, int32_t ld,
+                         double *vor, void *stream);
 
 /* ---------------------------------------------------------------------- */
 /* Global sums (Sec. 2.3: global mass conserved to round-off)              */

@@ -16,12 +16,12 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import (GRIST_FLAG_NONFINITE, GRIST_FLAG_TIMEOUT, GRIST_FP64, GRIST_MIX, GRIST_MIX_DBL_MASS,
-                   GRIST_SUM_AREA_WEIGHTED, GRIST_SUM_DRY_MASS, GRIST_SUM_TRACER_MASS, GristError)
+from ._lib import (GRIST_FLAG_NONFINITE, GRIST_FLAG_TIMEOUT, GRIST_FP64, GRIST_MIX, GRIST_MIX_DBL_MASS, GRIST_ROW_ALL,
+                   GRIST_ROWS, GRIST_SUM_AREA_WEIGHTED, GRIST_SUM_DRY_MASS, GRIST_SUM_TRACER_MASS, GristError)
 
 __all__ = ["Mesh", "DycoreParams", "GRIST_FP64", "GRIST_MIX", "GRIST_MIX_DBL_MASS", "GristError",
            "GRIST_SUM_DRY_MASS", "GRIST_SUM_TRACER_MASS", "GRIST_SUM_AREA_WEIGHTED", "load",
-           "GRIST_FLAG_NONFINITE", "GRIST_FLAG_TIMEOUT"]
+           "GRIST_FLAG_NONFINITE", "GRIST_FLAG_TIMEOUT", "GRIST_ROWS", "GRIST_ROW_ALL"]
 
 PREC = {"fp64": GRIST_FP64, "mix": GRIST_MIX, "mix_dbl_mass": GRIST_MIX_DBL_MASS}
 
@@ -233,6 +233,18 @@ class Mesh:
     def dycore_step_nh(self, state, params, dt, prec="fp64", stream=None):
         self._dycore("grist_dycore_step_nh", state, params, prec, dt, stream)
 
+    def vorticity(self, u, n_levels, out=None, stream=None):
+        """Relative vorticity at the vertices, [nV][ld] float64 on the device
+        (grist_diag_vorticity); u is [nE][ld] float64 or float32."""
+        import torch
+        ld = int(u.shape[-1])
+        if out is None:
+            out = torch.empty((self.nV, ld), dtype=torch.float64, device=u.device)
+        prec = GRIST_FP64 if u.dtype == torch.float64 else GRIST_MIX
+        _lib.check("grist_diag_vorticity", _lib.load().grist_diag_vorticity(
+            self.handle, _ptr(u), prec, int(n_levels), ld, _ptr(out), _stream_handle(stream)))
+        return out
+
     def global_sum(self, kind, field, dpi=None, n_levels=1, offset=0.0, stream=None):
         """Compensated deterministic sum; returns (sum, compensation)."""
         import torch
@@ -276,7 +288,7 @@ class DycoreParams:
     device tensor [nC] (internal numbering)."""
 
     def __init__(self, n_levels, b_interface, pi_top, phi_surface, ld=None, ld_int=None, p0=1.0e5, rd=287.04,
-                 cp=1004.64, g=9.80616, beta=0.55):
+                 cp=1004.64, g=9.80616, beta=0.55, emulate_fp32_rows=0):
         self.b = np.ascontiguousarray(b_interface, dtype=np.float64)
         self.phi_surface = phi_surface
         c = _lib.DycoreParams()
@@ -286,4 +298,5 @@ class DycoreParams:
         c.pi_top, c.p0, c.rd, c.cp, c.g, c.offcentre_beta = pi_top, p0, rd, cp, g, beta
         c.b_interface = self.b.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         c.phi_surface = _ptr(phi_surface)
+        c.emulate_fp32_rows = int(emulate_fp32_rows)
         self.c = c

@@ -15,6 +15,10 @@ _V = ctypes.c_void_p
 GRIST_FP64, GRIST_MIX, GRIST_MIX_DBL_MASS = 0, 1, 2
 GRIST_SUM_DRY_MASS, GRIST_SUM_TRACER_MASS, GRIST_SUM_AREA_WEIGHTED = 0, 1, 2
 GRIST_FLAG_NONFINITE, GRIST_FLAG_TIMEOUT = 0x1, 0x2
+# precision-map rows (grist_dycore_params.emulate_fp32_rows), in the header's order
+GRIST_ROWS = {"mass_flux": 0x001, "wind": 0x002, "pv_flux": 0x004, "ke_grad": 0x008, "vadv_u": 0x010,
+              "pgf": 0x020, "theta": 0x040, "dpi_pv": 0x080, "eos": 0x100, "nh_adv": 0x200}
+GRIST_ROW_ALL = 0x3ff
 
 STATUS = {0: "GRIST_OK", -1: "GRIST_EINVAL", -2: "GRIST_ECUDA", -3: "GRIST_ENOMEM",
           -4: "GRIST_ENUMERIC", -5: "GRIST_ETIMEOUT", -6: "GRIST_EUNSUPPORTED"}
@@ -46,7 +50,8 @@ class TracerTuning(ctypes.Structure):
 
 class DycoreParams(ctypes.Structure):
     _fields_ = [("n_levels", _I), ("ld", _I), ("ld_int", _I), ("pi_top", _D), ("p0", _D), ("rd", _D),
-                ("cp", _D), ("g", _D), ("offcentre_beta", _D), ("b_interface", _P(_D)), ("phi_surface", _V)]
+                ("cp", _D), ("g", _D), ("offcentre_beta", _D), ("b_interface", _P(_D)), ("phi_surface", _V),
+                ("emulate_fp32_rows", ctypes.c_uint32)]
 
 
 class DycoreState(ctypes.Structure):
@@ -74,6 +79,7 @@ EXPORTS = {
     "grist_weighted_sum_noalloc": ([_V, _V, ctypes.c_int64, _V, _V], ctypes.c_int),
     "grist_selftest_conversions": ([ctypes.c_uint64, ctypes.c_uint64, _P(ctypes.c_uint64), _P(ctypes.c_uint64)],
                                    ctypes.c_int),
+    "grist_diag_vorticity": ([_V, _V, ctypes.c_int, _I, _I, _V, _V], ctypes.c_int),
     "grist_selftest_reciprocal": ([ctypes.c_uint64, ctypes.c_uint64, _P(ctypes.c_uint64), _P(ctypes.c_uint64),
                                    _P(ctypes.c_uint64)], ctypes.c_int),
 }

@@ -38,7 +38,17 @@ struct DyPar {
     const double *rdBi;   // [L+1] 2/(dB[j-1] + dB[j]) at interior interfaces j
     const float *dBf;     // [L]   dB rounded to single precision
     const double *phis;   // [nC]  surface geopotential
+    uint32_t emu;         // GRIST_ROW_* rows rounded to binary32 (precision search)
 };
+
+// Storage-rounding emulation of a single-precision row (precision search,
+// Sec. 2.2 Eqs. 1-2): a double value of a row whose bit is set is rounded
+// to binary32 where it is produced; single values are already rounded.
+// The branch is uniform across the launch.
+__device__ __forceinline__ double emu(double x, uint32_t mask, uint32_t bit) {
+    return (mask & bit) ? (double)(float)x : x;
+}
+__device__ __forceinline__ float emu(float x, uint32_t, uint32_t) { return x; }
 
 // Compensated single-precision accumulation (Knuth's TwoSum): a value is
 // hi + lo with |lo| <= ulp(hi)/2, so a sum of FP32 terms carries about 48
@@ -155,7 +165,7 @@ __global__ void k_mass_edge(DevMesh m, DyPar d, const double *__restrict__ ps_s,
             double col = 0.0;
             for (int k = lane; k < d.L; k += 32) {
                 const size_t x = (size_t)e * d.ld + k;
-                const TM f = (TM)ldg(d.dB + k) * hs * cv<TM>(u_s[x]);
+                const TM f = emu((TM)ldg(d.dB + k) * hs * cv<TM>(u_s[x]), d.emu, GRIST_ROW_MASS_FLUX);
                 F[x] = f;
                 col += (double)f;
                 if (Facc) Facc[x] += scaled ? fscale * (double)f : (double)f;
@@ -233,8 +243,9 @@ __global__ void k_mass_col(DevMesh m, DyPar d, const typename P::TM *__restrict_
             if (k < d.L) {
 #pragma unroll
                 for (int j = 0; j < GRIST_MAXE; j++) s += cw[j] * ldg(F + (size_t)eidx[j] * d.ld + k);
+                s = emu(s, d.emu, GRIST_ROW_MASS_FLUX);
                 const size_t x = (size_t)i * d.ld + k;
-                theta[x] = cv<TA>(th_s[x] * ldg(d.rdB + k) * rdps);
+                theta[x] = emu(cv<TA>(th_s[x] * ldg(d.rdB + k) * rdps), d.emu, GRIST_ROW_THETA);
                 if (dpi_out) dpi_out[x] = ldg(d.dB + k) * dps;
                 if (rth_out) rth_out[x] = rcp(th_s[x]);
             }
@@ -286,7 +297,7 @@ __global__ void k_theta_flux(DevMesh m, DyPar d, LevelDiv Dv, const typename P::
     for (int j = 0; j < GRIST_D2P; j++) s += ldg(cf + j) * ldg(th + (size_t)ldg(st + j) * d.ld + k);
     const TA te = (TA)0.5 * (ldg(th + (size_t)c.x * d.ld + k) + ldg(th + (size_t)c.y * d.ld + k)) -
                   (TA)2 * ldg(Coef<TA>::dc2(m) + e) * s;
-    Fth[x] = f * te;
+    Fth[x] = emu(f * te, d.emu, GRIST_ROW_THETA);
 }
 
 // Eq. 4 update: dpi theta^(s) = dpi theta^n + dt_s (-div F_theta - delta(M theta)).
@@ -343,9 +354,9 @@ __global__ void k_hydro_diag(DevMesh m, DyPar d, const double *__restrict__ ps, 
         }
         if (k < d.L) {
             const size_t x = (size_t)i * d.ld + k;
-            p[x] = pk;
-            al[x] = a;
-            phl[x] = carry + (v - contrib) + 0.5 * contrib;
+            p[x] = emu(pk, d.emu, GRIST_ROW_EOS);
+            al[x] = emu(a, d.emu, GRIST_ROW_EOS);
+            phl[x] = emu(carry + (v - contrib) + 0.5 * contrib, d.emu, GRIST_ROW_EOS);
         }
         carry += __shfl_sync(0xffffffffu, v, 0);
     }
@@ -359,7 +370,7 @@ __global__ void k_vertex_mass(DevMesh m, DyPar d, const double *__restrict__ ps_
     double s = 0.0;
 #pragma unroll
     for (int j = 0; j < 3; j++) s += ldg(m.ckite + v * 3 + j) * (ldg(ps_s + ldg(m.cov + v * 3 + j)) - d.pi_top);
-    rdpv[v] = rcp(s);
+    rdpv[v] = emu(rcp(s), d.emu, GRIST_ROW_DPI_PV);
 }
 
 // Vertex PV, Sec. 2.3: zeta_p = (zeta + f) / dpi_v, the relative vorticity
@@ -377,7 +388,8 @@ __global__ void k_vort(DevMesh m, DyPar d, LevelDiv Dv, const typename P::TU *__
 #pragma unroll
     for (int j = 0; j < 3; j++)
         z += ldg(Coef<TA>::ccurl(m) + v * 3 + j) * cv<TA>(ldg(u + (size_t)ldg(m.eov + v * 3 + j) * d.ld + k));
-    qv[(size_t)v * d.ld + k] = cv<TA>((cv<double>(z) + ldg(m.fv + v)) * (ldg(d.rdB + k) * ldg(rdpv + v)));
+    qv[(size_t)v * d.ld + k] =
+        emu(cv<TA>((cv<double>(z) + ldg(m.fv + v)) * (ldg(d.rdB + k) * ldg(rdpv + v))), d.emu, GRIST_ROW_PV_FLUX);
 }
 
 // Cell kinetic energy, stored doubled: 2K = sum (dc dv / 2A) u^2 (FP64:
@@ -394,7 +406,7 @@ __global__ void k_ke(DevMesh m, DyPar d, LevelDiv Dv, const typename P::TU *__re
         const double ue = cv<double>(ldg(u + (size_t)ldg(m.eoc + i * 6 + j) * d.ld + k));
         s += ldg(m.kec2 + i * 6 + j) * ue * ue;
     }
-    K[(size_t)i * d.ld + k] = s;
+    K[(size_t)i * d.ld + k] = emu(s, d.emu, GRIST_ROW_KE_GRAD);
 }
 
 template <class P>
@@ -406,7 +418,8 @@ __global__ void k_pv_edge(DevMesh m, DyPar d, LevelDiv Dv, const typename P::TA 
     int e, k;
     split_index(n, Dv, e, k);
     const int2 v = ldg(m.voe + e);
-    qe[(size_t)e * d.ld + k] = (TA)0.5 * (ldg(qv + (size_t)v.x * d.ld + k) + ldg(qv + (size_t)v.y * d.ld + k));
+    qe[(size_t)e * d.ld + k] =
+        emu((TA)0.5 * (ldg(qv + (size_t)v.x * d.ld + k) + ldg(qv + (size_t)v.y * d.ld + k)), d.emu, GRIST_ROW_PV_FLUX);
 }
 
 // Eq. 5 momentum tendency and stage update:
@@ -453,14 +466,28 @@ __global__ void k_momentum(DevMesh m, DyPar d, LevelDiv Dv, const typename P::TU
     // [M sums](du) / (2 dpi_e) with dpi_e = dB (sum)/2, M_e = (M1 + M2)/2;
     // rsum_e holds 1/(2 sum)
     va *= ldg(d.rdB + k) * ldg(rsum_e + e);
-    const double de = NH ? ldg(dpp + a1) + ldg(dpp + a2) : 2.0;
+    va = emu(va, d.emu, GRIST_ROW_VADV_U);
     // dK/dn + alpha_e dp/dn + (dp/dpi)_e dphi/dn with the two means folded
     // into -1/(2 dc) (hrdc) and K stored doubled
-    const double grad = fma(ldg(al + a1) + ldg(al + a2), ldg(p + a2) - ldg(p + a1),
-                            fma(de, ldg(phl + a2) - ldg(phl + a1), ldg(K + a2) - ldg(K + a1)));
+    double grad;
+    if (!(d.emu & GRIST_ROW_PGF)) {
+        const double de = NH ? ldg(dpp + a1) + ldg(dpp + a2) : 2.0;
+        grad = fma(ldg(al + a1) + ldg(al + a2), ldg(p + a2) - ldg(p + a1),
+                   fma(de, ldg(phl + a2) - ldg(phl + a1), ldg(K + a2) - ldg(K + a1)));
+    } else {
+        // pressure gradient and gravity from binary32 inputs, summed and
+        // rounded to binary32 (precision search)
+        const uint32_t r = GRIST_ROW_PGF;
+        const double de = NH ? emu(ldg(dpp + a1), d.emu, r) + emu(ldg(dpp + a2), d.emu, r) : 2.0;
+        const double pgf = emu(fma(emu(ldg(al + a1), d.emu, r) + emu(ldg(al + a2), d.emu, r),
+                                   emu(ldg(p + a2), d.emu, r) - emu(ldg(p + a1), d.emu, r),
+                                   de * (emu(ldg(phl + a2), d.emu, r) - emu(ldg(phl + a1), d.emu, r))),
+                               d.emu, r);
+        grad = pgf + (ldg(K + a2) - ldg(K + a1));
+    }
     const double slow = fma(ldg(m.hrdc + e), grad, -va);
-    const TA tend = pv + cv<TA>(slow);
-    const TU v = cv<TU>(cv<TA>(u_n[x]) + cv<TA>(dts) * tend);
+    const TA tend = emu(pv, d.emu, GRIST_ROW_PV_FLUX) + cv<TA>(slow);
+    const TU v = emu(cv<TU>(cv<TA>(u_n[x]) + cv<TA>(dts) * tend), d.emu, GRIST_ROW_WIND);
     if (!isfinite(v)) atomicOr(status, GRIST_FLAG_NONFINITE);
     u_out[x] = v;
 }
@@ -477,7 +504,8 @@ __global__ void k_eos(DevMesh m, DyPar d, LevelDiv Dv, const double *__restrict_
     int i, k;
     split_index(n, Dv, i, k);
     const double dphi = phi[(size_t)i * d.ldi + k] - phi[(size_t)i * d.ldi + k + 1];
-    p[(size_t)i * d.ld + k] = d.p0 * exp(d.gamma * log(d.rd * th[(size_t)i * d.ld + k] / (d.p0 * dphi)));
+    p[(size_t)i * d.ld + k] =
+        emu(d.p0 * exp(d.gamma * log(d.rd * th[(size_t)i * d.ld + k] / (d.p0 * dphi))), d.emu, GRIST_ROW_EOS);
 }
 
 // Explicit parts of Eqs. 6-7 at every interface: horizontal advection
@@ -536,8 +564,8 @@ __global__ void k_nh_explicit(DevMesh m, DyPar d, LevelDiv Dv, const typename P:
             fw = fw_n[xi];
         }
     }
-    wst[xi] = w_n[xi] + dts * (cv<double>(-hw - vw) + (1.0 - d.beta) * fw);
-    phst[xi] = phi_n[xi] + dts * (cv<double>(-hp - vp) + (1.0 - d.beta) * d.g * w_n[xi]);
+    wst[xi] = w_n[xi] + dts * (cv<double>(emu(-hw - vw, d.emu, GRIST_ROW_NH_ADV)) + (1.0 - d.beta) * fw);
+    phst[xi] = phi_n[xi] + dts * (cv<double>(emu(-hp - vp, d.emu, GRIST_ROW_NH_ADV)) + (1.0 - d.beta) * d.g * w_n[xi]);
 }
 
 // Staging of a [32 columns][kSolveKC levels] tile between global memory
@@ -705,12 +733,12 @@ __global__ void __launch_bounds__(32, kSolveMinBlocks) k_nh_solve(DevMesh m, DyP
                 if (k > 0) {
                     dcur = (pk - pprev) * (ldg(d.rdBi + k) * rdps);
                     const double dv = 0.5 * (dtop + dcur);
-                    if (kk > 0) sA[5 * kStage + o - kRow] = dv;   // layer k-1 of this chunk
-                    else dpp[(size_t)i * d.ld + k - 1] = dv;        // layer k-1 of the previous chunk
+                    if (kk > 0) sA[5 * kStage + o - kRow] = emu(dv, d.emu, GRIST_ROW_EOS);   // layer k-1 of this chunk
+                    else dpp[(size_t)i * d.ld + k - 1] = emu(dv, d.emu, GRIST_ROW_EOS);        // of the previous chunk
                 }
-                sA[2 * kStage + o] = pk;
-                sA[3 * kStage + o] = (phi_top - phi_bot) * (ldg(d.rdB + k) * rdps);
-                sA[4 * kStage + o] = 0.5 * (phi_top + phi_bot);
+                sA[2 * kStage + o] = emu(pk, d.emu, GRIST_ROW_EOS);
+                sA[3 * kStage + o] = emu((phi_top - phi_bot) * (ldg(d.rdB + k) * rdps), d.emu, GRIST_ROW_EOS);
+                sA[4 * kStage + o] = emu(0.5 * (phi_top + phi_bot), d.emu, GRIST_ROW_EOS);
                 sA[1 * kStage + o] = phi_bot;   // w_top of this row is no longer needed
                 dtop = dcur;
                 pprev = pk;
@@ -724,7 +752,21 @@ __global__ void __launch_bounds__(32, kSolveMinBlocks) k_nh_solve(DevMesh m, DyP
         stage_out(phl, d.ld, col0, ncol, k0, nk, sA + 4 * kStage);
         stage_out(dpp, d.ld, col0, ncol, k0, nk - 1, sA + 5 * kStage);
     }
-    if (act) dpp[(size_t)i * d.ld + L - 1] = 0.5 * (dtop + 1.0);
+    if (act) dpp[(size_t)i * d.ld + L - 1] = emu(0.5 * (dtop + 1.0), d.emu, GRIST_ROW_EOS);
+}
+
+// Relative vorticity at the vertices (diagnostic): zeta_v = sum_j ccurl u,
+// ccurl = t(e,v) dc_e / A_v, in FP64.
+template <typename TU>
+__global__ void k_diag_vort(DevMesh m, int L, int ld, LevelDiv Dv, const TU *__restrict__ u, double *__restrict__ vor) {
+    uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= (uint32_t)m.nV * (uint32_t)L) return;
+    int v, k;
+    split_index(n, Dv, v, k);
+    double z = 0.0;
+#pragma unroll
+    for (int j = 0; j < 3; j++) z += ldg(m.ccurl + v * 3 + j) * (double)ldg(u + (size_t)ldg(m.eov + v * 3 + j) * ld + k);
+    vor[(size_t)v * ld + k] = z;
 }
 
 __global__ void k_add_scalar(double *x, double v) {
@@ -785,6 +827,7 @@ int dycore_step(grist_mesh_s *h, grist_dycore_state *S, const grist_dycore_param
     d.beta = prm->offcentre_beta; d.kappa = prm->rd / prm->cp; d.gamma = prm->cp / (prm->cp - prm->rd);
     d.B = dvg; d.dB = dvg + L + 1; d.rdB = dvg + 2 * L + 1; d.rdBi = dvg + 3 * L + 1; d.phis = prm->phi_surface;
     d.dBf = reinterpret_cast<const float *>(dvg + 4 * L + 2);
+    d.emu = prm->emulate_fp32_rows;
 
     TU *uA = (TU *)(s + o_uA), *uB = (TU *)(s + o_uB);
     double *psA = (double *)(s + o_psA), *psB = (double *)(s + o_psB), *psN = (double *)(s + o_psN);
@@ -895,6 +938,7 @@ int check(grist_mesh h, grist_dycore_state *S, const grist_dycore_params *prm, g
         return GRIST_EINVAL;
     if (nh && !(prm->offcentre_beta > 0 && prm->offcentre_beta <= 1)) return GRIST_EINVAL;
     if (!std::isfinite(S->accum_scale) || S->accum_scale < 0) return GRIST_EINVAL;
+    if (prm->emulate_fp32_rows & ~GRIST_ROW_ALL) return GRIST_EINVAL;
     return GRIST_OK;
 }
 
@@ -927,4 +971,20 @@ extern "C" int grist_dycore_step_nh(grist_mesh h, grist_dycore_state *S, const g
         case GRIST_MIX: return dycore_step<PolMIX, true>(h, S, prm, dt, st);
         default: return dycore_step<PolMIXDBL, true>(h, S, prm, dt, st);
     }
+}
+
+extern "C" int grist_diag_vorticity(grist_mesh h, const void *u, grist_precision prec, int32_t n_levels, int32_t ld,
+                                    double *vor, void *stream) {
+    if (!h || !u || !vor || n_levels < 1 || n_levels > GRIST_MAXL || ld < n_levels) return GRIST_EINVAL;
+    if (prec != GRIST_FP64 && prec != GRIST_MIX && prec != GRIST_MIX_DBL_MASS) return GRIST_EINVAL;
+    if (cudaSetDevice(mesh_device(h)) != cudaSuccess) return GRIST_ECUDA;
+    const DevMesh &m = dev_mesh(h);
+    cudaStream_t st = (cudaStream_t)stream;
+    const LevelDiv Dv = make_div((uint32_t)n_levels);
+    const unsigned grid = grid_for((long long)m.nV * n_levels, kBlock);
+    if (prec == GRIST_FP64)
+        k_diag_vort<double><<<grid, kBlock, 0, st>>>(m, n_levels, ld, Dv, (const double *)u, vor);
+    else
+        k_diag_vort<float><<<grid, kBlock, 0, st>>>(m, n_levels, ld, Dv, (const float *)u, vor);
+    return cudaGetLastError() == cudaSuccess ? GRIST_OK : GRIST_ECUDA;
 }
