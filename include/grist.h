@@ -230,8 +230,9 @@ typedef struct {
  * rounded to binary32 where it is produced (storage-rounding emulation:
  * the arithmetic between roundings stays in the policy's type), so the
  * accuracy cost of a single-precision row can be measured on the FP64
- * path without a kernel per combination.  Values already single in the
- * chosen policy are unaffected.  0 leaves every result unchanged. */
+ * path without a kernel per combination.  A nonzero mask needs GRIST_FP64
+ * (else GRIST_EUNSUPPORTED) and runs a separately compiled emulating
+ * variant of the FP64 kernels; 0 runs the production kernels unchanged. */
 #define GRIST_ROW_MASS_FLUX 0x001u  /* dpi V at edges and its layer divergence (Eq. 3) */
 #define GRIST_ROW_WIND 0x002u       /* u_n after each stage update (Eq. 5) */
 #define GRIST_ROW_PV_FLUX 0x004u    /* vertex and edge PV, tangential PV flux (Eq. 5) */

@@ -81,9 +81,13 @@ template <typename T> __device__ __forceinline__ T ldg(const T *p) { return __ld
 //   TU : storage of the edge wind u_n
 //   TA : advective compute / storage (theta flux, PV flux, tracer fluxes)
 //   TM : mass flux dpi*V and its divergence
-struct PolFP64 { using TU = double; using TA = double; using TM = double; };
-struct PolMIX { using TU = float; using TA = float; using TM = float; };
-struct PolMIXDBL { using TU = float; using TA = float; using TM = double; };
+//   EMU: the kernels carry the binary32 row emulation of the precision search
+//        (grist_dycore_params.emulate_fp32_rows); the production policies
+//        compile without it.
+struct PolFP64 { using TU = double; using TA = double; using TM = double; static constexpr bool EMU = false; };
+struct PolMIX { using TU = float; using TA = float; using TM = float; static constexpr bool EMU = false; };
+struct PolMIXDBL { using TU = float; using TA = float; using TM = double; static constexpr bool EMU = false; };
+struct PolFP64EMU { using TU = double; using TA = double; using TM = double; static constexpr bool EMU = true; };
 
 template <typename T> struct Coef;
 template <> struct Coef<double> {

@@ -42,13 +42,14 @@ struct DyPar {
 };
 
 // Storage-rounding emulation of a single-precision row (precision search,
-// Sec. 2.2 Eqs. 1-2): a double value of a row whose bit is set is rounded
-// to binary32 where it is produced; single values are already rounded.
-// The branch is uniform across the launch.
-__device__ __forceinline__ double emu(double x, uint32_t mask, uint32_t bit) {
-    return (mask & bit) ? (double)(float)x : x;
+// Sec. 2.2 Eqs. 1-2): in the emulating FP64 policy (E) a double value of a
+// row whose bit is set is rounded to binary32 where it is produced; the
+// production policies compile to the plain value.
+template <bool E> __device__ __forceinline__ double emu(double x, uint32_t mask, uint32_t bit) {
+    if (E) return (mask & bit) ? (double)(float)x : x;
+    return x;
 }
-__device__ __forceinline__ float emu(float x, uint32_t, uint32_t) { return x; }
+template <bool E> __device__ __forceinline__ float emu(float x, uint32_t, uint32_t) { return x; }
 
 // Compensated single-precision accumulation (Knuth's TwoSum): a value is
 // hi + lo with |lo| <= ulp(hi)/2, so a sum of FP32 terms carries about 48
@@ -165,7 +166,7 @@ __global__ void k_mass_edge(DevMesh m, DyPar d, const double *__restrict__ ps_s,
             double col = 0.0;
             for (int k = lane; k < d.L; k += 32) {
                 const size_t x = (size_t)e * d.ld + k;
-                const TM f = emu((TM)ldg(d.dB + k) * hs * cv<TM>(u_s[x]), d.emu, GRIST_ROW_MASS_FLUX);
+                const TM f = emu<P::EMU>((TM)ldg(d.dB + k) * hs * cv<TM>(u_s[x]), d.emu, GRIST_ROW_MASS_FLUX);
                 F[x] = f;
                 col += (double)f;
                 if (Facc) Facc[x] += scaled ? fscale * (double)f : (double)f;
@@ -243,9 +244,9 @@ __global__ void k_mass_col(DevMesh m, DyPar d, const typename P::TM *__restrict_
             if (k < d.L) {
 #pragma unroll
                 for (int j = 0; j < GRIST_MAXE; j++) s += cw[j] * ldg(F + (size_t)eidx[j] * d.ld + k);
-                s = emu(s, d.emu, GRIST_ROW_MASS_FLUX);
+                s = emu<P::EMU>(s, d.emu, GRIST_ROW_MASS_FLUX);
                 const size_t x = (size_t)i * d.ld + k;
-                theta[x] = emu(cv<TA>(th_s[x] * ldg(d.rdB + k) * rdps), d.emu, GRIST_ROW_THETA);
+                theta[x] = emu<P::EMU>(cv<TA>(th_s[x] * ldg(d.rdB + k) * rdps), d.emu, GRIST_ROW_THETA);
                 if (dpi_out) dpi_out[x] = ldg(d.dB + k) * dps;
                 if (rth_out) rth_out[x] = rcp(th_s[x]);
             }
@@ -297,7 +298,7 @@ __global__ void k_theta_flux(DevMesh m, DyPar d, LevelDiv Dv, const typename P::
     for (int j = 0; j < GRIST_D2P; j++) s += ldg(cf + j) * ldg(th + (size_t)ldg(st + j) * d.ld + k);
     const TA te = (TA)0.5 * (ldg(th + (size_t)c.x * d.ld + k) + ldg(th + (size_t)c.y * d.ld + k)) -
                   (TA)2 * ldg(Coef<TA>::dc2(m) + e) * s;
-    Fth[x] = emu(f * te, d.emu, GRIST_ROW_THETA);
+    Fth[x] = emu<P::EMU>(f * te, d.emu, GRIST_ROW_THETA);
 }
 
 // Eq. 4 update: dpi theta^(s) = dpi theta^n + dt_s (-div F_theta - delta(M theta)).
@@ -326,6 +327,7 @@ __global__ void k_theta_update(DevMesh m, DyPar d, LevelDiv Dv, const typename P
 // Eq. 8 (hydrostatic diagnostics), one warp per column: mid-layer pressure,
 // alpha = Rd theta (p/p0)^kappa / p, geopotential integrated upward from
 // phi_s by a suffix scan, layer geopotential = mean of its interfaces.
+template <bool EMU>
 __global__ void k_hydro_diag(DevMesh m, DyPar d, const double *__restrict__ ps, const double *__restrict__ th,
                              double *__restrict__ p, double *__restrict__ al, double *__restrict__ phl) {
     const int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -354,9 +356,9 @@ __global__ void k_hydro_diag(DevMesh m, DyPar d, const double *__restrict__ ps, 
         }
         if (k < d.L) {
             const size_t x = (size_t)i * d.ld + k;
-            p[x] = emu(pk, d.emu, GRIST_ROW_EOS);
-            al[x] = emu(a, d.emu, GRIST_ROW_EOS);
-            phl[x] = emu(carry + (v - contrib) + 0.5 * contrib, d.emu, GRIST_ROW_EOS);
+            p[x] = emu<EMU>(pk, d.emu, GRIST_ROW_EOS);
+            al[x] = emu<EMU>(a, d.emu, GRIST_ROW_EOS);
+            phl[x] = emu<EMU>(carry + (v - contrib) + 0.5 * contrib, d.emu, GRIST_ROW_EOS);
         }
         carry += __shfl_sync(0xffffffffu, v, 0);
     }
@@ -364,13 +366,14 @@ __global__ void k_hydro_diag(DevMesh m, DyPar d, const double *__restrict__ ps, 
 
 // Column reciprocal of the kite-remapped vertex layer mass:
 // 1 / sum_i kite(i,v)/A_v (ps_i - pi_top); the layer value is dB_k times it.
+template <bool EMU>
 __global__ void k_vertex_mass(DevMesh m, DyPar d, const double *__restrict__ ps_s, double *__restrict__ rdpv) {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= m.nV) return;
     double s = 0.0;
 #pragma unroll
     for (int j = 0; j < 3; j++) s += ldg(m.ckite + v * 3 + j) * (ldg(ps_s + ldg(m.cov + v * 3 + j)) - d.pi_top);
-    rdpv[v] = emu(rcp(s), d.emu, GRIST_ROW_DPI_PV);
+    rdpv[v] = emu<EMU>(rcp(s), d.emu, GRIST_ROW_DPI_PV);
 }
 
 // Vertex PV, Sec. 2.3: zeta_p = (zeta + f) / dpi_v, the relative vorticity
@@ -389,7 +392,7 @@ __global__ void k_vort(DevMesh m, DyPar d, LevelDiv Dv, const typename P::TU *__
     for (int j = 0; j < 3; j++)
         z += ldg(Coef<TA>::ccurl(m) + v * 3 + j) * cv<TA>(ldg(u + (size_t)ldg(m.eov + v * 3 + j) * d.ld + k));
     qv[(size_t)v * d.ld + k] =
-        emu(cv<TA>((cv<double>(z) + ldg(m.fv + v)) * (ldg(d.rdB + k) * ldg(rdpv + v))), d.emu, GRIST_ROW_PV_FLUX);
+        emu<P::EMU>(cv<TA>((cv<double>(z) + ldg(m.fv + v)) * (ldg(d.rdB + k) * ldg(rdpv + v))), d.emu, GRIST_ROW_PV_FLUX);
 }
 
 // Cell kinetic energy, stored doubled: 2K = sum (dc dv / 2A) u^2 (FP64:
@@ -406,7 +409,7 @@ __global__ void k_ke(DevMesh m, DyPar d, LevelDiv Dv, const typename P::TU *__re
         const double ue = cv<double>(ldg(u + (size_t)ldg(m.eoc + i * 6 + j) * d.ld + k));
         s += ldg(m.kec2 + i * 6 + j) * ue * ue;
     }
-    K[(size_t)i * d.ld + k] = emu(s, d.emu, GRIST_ROW_KE_GRAD);
+    K[(size_t)i * d.ld + k] = emu<P::EMU>(s, d.emu, GRIST_ROW_KE_GRAD);
 }
 
 template <class P>
@@ -419,7 +422,7 @@ __global__ void k_pv_edge(DevMesh m, DyPar d, LevelDiv Dv, const typename P::TA 
     split_index(n, Dv, e, k);
     const int2 v = ldg(m.voe + e);
     qe[(size_t)e * d.ld + k] =
-        emu((TA)0.5 * (ldg(qv + (size_t)v.x * d.ld + k) + ldg(qv + (size_t)v.y * d.ld + k)), d.emu, GRIST_ROW_PV_FLUX);
+        emu<P::EMU>((TA)0.5 * (ldg(qv + (size_t)v.x * d.ld + k) + ldg(qv + (size_t)v.y * d.ld + k)), d.emu, GRIST_ROW_PV_FLUX);
 }
 
 // Eq. 5 momentum tendency and stage update:
@@ -466,11 +469,11 @@ __global__ void k_momentum(DevMesh m, DyPar d, LevelDiv Dv, const typename P::TU
     // [M sums](du) / (2 dpi_e) with dpi_e = dB (sum)/2, M_e = (M1 + M2)/2;
     // rsum_e holds 1/(2 sum)
     va *= ldg(d.rdB + k) * ldg(rsum_e + e);
-    va = emu(va, d.emu, GRIST_ROW_VADV_U);
+    va = emu<P::EMU>(va, d.emu, GRIST_ROW_VADV_U);
     // dK/dn + alpha_e dp/dn + (dp/dpi)_e dphi/dn with the two means folded
     // into -1/(2 dc) (hrdc) and K stored doubled
     double grad;
-    if (!(d.emu & GRIST_ROW_PGF)) {
+    if (!P::EMU || !(d.emu & GRIST_ROW_PGF)) {
         const double de = NH ? ldg(dpp + a1) + ldg(dpp + a2) : 2.0;
         grad = fma(ldg(al + a1) + ldg(al + a2), ldg(p + a2) - ldg(p + a1),
                    fma(de, ldg(phl + a2) - ldg(phl + a1), ldg(K + a2) - ldg(K + a1)));
@@ -478,16 +481,16 @@ __global__ void k_momentum(DevMesh m, DyPar d, LevelDiv Dv, const typename P::TU
         // pressure gradient and gravity from binary32 inputs, summed and
         // rounded to binary32 (precision search)
         const uint32_t r = GRIST_ROW_PGF;
-        const double de = NH ? emu(ldg(dpp + a1), d.emu, r) + emu(ldg(dpp + a2), d.emu, r) : 2.0;
-        const double pgf = emu(fma(emu(ldg(al + a1), d.emu, r) + emu(ldg(al + a2), d.emu, r),
-                                   emu(ldg(p + a2), d.emu, r) - emu(ldg(p + a1), d.emu, r),
-                                   de * (emu(ldg(phl + a2), d.emu, r) - emu(ldg(phl + a1), d.emu, r))),
+        const double de = NH ? emu<P::EMU>(ldg(dpp + a1), d.emu, r) + emu<P::EMU>(ldg(dpp + a2), d.emu, r) : 2.0;
+        const double pgf = emu<P::EMU>(fma(emu<P::EMU>(ldg(al + a1), d.emu, r) + emu<P::EMU>(ldg(al + a2), d.emu, r),
+                                   emu<P::EMU>(ldg(p + a2), d.emu, r) - emu<P::EMU>(ldg(p + a1), d.emu, r),
+                                   de * (emu<P::EMU>(ldg(phl + a2), d.emu, r) - emu<P::EMU>(ldg(phl + a1), d.emu, r))),
                                d.emu, r);
         grad = pgf + (ldg(K + a2) - ldg(K + a1));
     }
     const double slow = fma(ldg(m.hrdc + e), grad, -va);
-    const TA tend = emu(pv, d.emu, GRIST_ROW_PV_FLUX) + cv<TA>(slow);
-    const TU v = emu(cv<TU>(cv<TA>(u_n[x]) + cv<TA>(dts) * tend), d.emu, GRIST_ROW_WIND);
+    const TA tend = emu<P::EMU>(pv, d.emu, GRIST_ROW_PV_FLUX) + cv<TA>(slow);
+    const TU v = emu<P::EMU>(cv<TU>(cv<TA>(u_n[x]) + cv<TA>(dts) * tend), d.emu, GRIST_ROW_WIND);
     if (!isfinite(v)) atomicOr(status, GRIST_FLAG_NONFINITE);
     u_out[x] = v;
 }
@@ -497,6 +500,7 @@ __global__ void k_momentum(DevMesh m, DyPar d, LevelDiv Dv, const typename P::TU
 
 // Eq. 9 at time level n: p = p0 (Rd dpi_theta / (p0 dphi))^gamma, as
 // p0 exp(gamma log(.)).
+template <bool EMU>
 __global__ void k_eos(DevMesh m, DyPar d, LevelDiv Dv, const double *__restrict__ th, const double *__restrict__ phi,
                       double *__restrict__ p) {
     uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
@@ -505,7 +509,7 @@ __global__ void k_eos(DevMesh m, DyPar d, LevelDiv Dv, const double *__restrict_
     split_index(n, Dv, i, k);
     const double dphi = phi[(size_t)i * d.ldi + k] - phi[(size_t)i * d.ldi + k + 1];
     p[(size_t)i * d.ld + k] =
-        emu(d.p0 * exp(d.gamma * log(d.rd * th[(size_t)i * d.ld + k] / (d.p0 * dphi))), d.emu, GRIST_ROW_EOS);
+        emu<EMU>(d.p0 * exp(d.gamma * log(d.rd * th[(size_t)i * d.ld + k] / (d.p0 * dphi))), d.emu, GRIST_ROW_EOS);
 }
 
 // Explicit parts of Eqs. 6-7 at every interface: horizontal advection
@@ -564,8 +568,8 @@ __global__ void k_nh_explicit(DevMesh m, DyPar d, LevelDiv Dv, const typename P:
             fw = fw_n[xi];
         }
     }
-    wst[xi] = w_n[xi] + dts * (cv<double>(emu(-hw - vw, d.emu, GRIST_ROW_NH_ADV)) + (1.0 - d.beta) * fw);
-    phst[xi] = phi_n[xi] + dts * (cv<double>(emu(-hp - vp, d.emu, GRIST_ROW_NH_ADV)) + (1.0 - d.beta) * d.g * w_n[xi]);
+    wst[xi] = w_n[xi] + dts * (cv<double>(emu<P::EMU>(-hw - vw, d.emu, GRIST_ROW_NH_ADV)) + (1.0 - d.beta) * fw);
+    phst[xi] = phi_n[xi] + dts * (cv<double>(emu<P::EMU>(-hp - vp, d.emu, GRIST_ROW_NH_ADV)) + (1.0 - d.beta) * d.g * w_n[xi]);
 }
 
 // Staging of a [32 columns][kSolveKC levels] tile between global memory
@@ -623,6 +627,7 @@ __device__ __forceinline__ void stage_out(double *X, size_t S, int col0, int nco
 // (interface value 1 at top and bottom) for the momentum equation.  phi_out
 // may be phi_r and p may be p_r (the last stage writes the state in place):
 // each block reads all reference values of its columns before writing them.
+template <bool EMU>
 __global__ void __launch_bounds__(32, kSolveMinBlocks) k_nh_solve(DevMesh m, DyPar d, const double *__restrict__ wst,
                                                  const double *__restrict__ phst, const double *__restrict__ th,
                                                  const double *__restrict__ rth_r, const double *phi_r,
@@ -733,12 +738,12 @@ __global__ void __launch_bounds__(32, kSolveMinBlocks) k_nh_solve(DevMesh m, DyP
                 if (k > 0) {
                     dcur = (pk - pprev) * (ldg(d.rdBi + k) * rdps);
                     const double dv = 0.5 * (dtop + dcur);
-                    if (kk > 0) sA[5 * kStage + o - kRow] = emu(dv, d.emu, GRIST_ROW_EOS);   // layer k-1 of this chunk
-                    else dpp[(size_t)i * d.ld + k - 1] = emu(dv, d.emu, GRIST_ROW_EOS);        // of the previous chunk
+                    if (kk > 0) sA[5 * kStage + o - kRow] = emu<EMU>(dv, d.emu, GRIST_ROW_EOS);   // layer k-1 of this chunk
+                    else dpp[(size_t)i * d.ld + k - 1] = emu<EMU>(dv, d.emu, GRIST_ROW_EOS);        // of the previous chunk
                 }
-                sA[2 * kStage + o] = emu(pk, d.emu, GRIST_ROW_EOS);
-                sA[3 * kStage + o] = emu((phi_top - phi_bot) * (ldg(d.rdB + k) * rdps), d.emu, GRIST_ROW_EOS);
-                sA[4 * kStage + o] = emu(0.5 * (phi_top + phi_bot), d.emu, GRIST_ROW_EOS);
+                sA[2 * kStage + o] = emu<EMU>(pk, d.emu, GRIST_ROW_EOS);
+                sA[3 * kStage + o] = emu<EMU>((phi_top - phi_bot) * (ldg(d.rdB + k) * rdps), d.emu, GRIST_ROW_EOS);
+                sA[4 * kStage + o] = emu<EMU>(0.5 * (phi_top + phi_bot), d.emu, GRIST_ROW_EOS);
                 sA[1 * kStage + o] = phi_bot;   // w_top of this row is no longer needed
                 dtop = dcur;
                 pprev = pk;
@@ -752,7 +757,7 @@ __global__ void __launch_bounds__(32, kSolveMinBlocks) k_nh_solve(DevMesh m, DyP
         stage_out(phl, d.ld, col0, ncol, k0, nk, sA + 4 * kStage);
         stage_out(dpp, d.ld, col0, ncol, k0, nk - 1, sA + 5 * kStage);
     }
-    if (act) dpp[(size_t)i * d.ld + L - 1] = emu(0.5 * (dtop + 1.0), d.emu, GRIST_ROW_EOS);
+    if (act) dpp[(size_t)i * d.ld + L - 1] = emu<EMU>(0.5 * (dtop + 1.0), d.emu, GRIST_ROW_EOS);
 }
 
 // Relative vorticity at the vertices (diagnostic): zeta_v = sum_j ccurl u,
@@ -864,7 +869,7 @@ int dycore_step(grist_mesh_s *h, grist_dycore_state *S, const grist_dycore_param
             p_n = S->p_nh;
         } else {
             double *dst = S->p_nh ? S->p_nh : pn;
-            GRIST_LAUNCH(h, PN("k_eos"), st, k_eos<<<gC, kBlock, 0, st>>>(m, d, DL, S->dpi_theta, S->phi, dst));
+            GRIST_LAUNCH(h, PN("k_eos"), st, k_eos<P::EMU><<<gC, kBlock, 0, st>>>(m, d, DL, S->dpi_theta, S->phi, dst));
             p_n = dst;
         }
     }
@@ -896,14 +901,14 @@ int dycore_step(grist_mesh_s *h, grist_dycore_state *S, const grist_dycore_param
             else
                 GRIST_LAUNCH(h, PN("k_nh_explicit"), st, k_nh_explicit<P, false><<<gI, kBlock, 0, st>>>(
                     m, d, DI, u_in, rdps, Mv, w_in, phi_in, S->w, S->phi, p_n, fwn, wst, phst, h3));
-            GRIST_LAUNCH(h, PN("k_nh_solve"), st, k_nh_solve<<<gSolve, kSolveCols, 0, st>>>(
+            GRIST_LAUNCH(h, PN("k_nh_solve"), st, k_nh_solve<P::EMU><<<gSolve, kSolveCols, 0, st>>>(
                 m, d, wst, phst, th_outs[s3], rthn, S->phi, p_n, ps_outs[s3], h3, w_outs[s3],
                 phi_outs[s3], p_outs[s3], alp, phl, dpp, bpos, bneg));
         } else {
-            GRIST_LAUNCH(h, PN("k_hydro_diag"), st, k_hydro_diag<<<gW, kBlock, 0, st>>>(
+            GRIST_LAUNCH(h, PN("k_hydro_diag"), st, k_hydro_diag<P::EMU><<<gW, kBlock, 0, st>>>(
                 m, d, ps_outs[s3], th_outs[s3], p, alp, phl));
         }
-        GRIST_LAUNCH(h, PN("k_vertex_mass"), st, k_vertex_mass<<<gVx, kBlock, 0, st>>>(m, d, ps_in, rdpv));
+        GRIST_LAUNCH(h, PN("k_vertex_mass"), st, k_vertex_mass<P::EMU><<<gVx, kBlock, 0, st>>>(m, d, ps_in, rdpv));
         GRIST_LAUNCH(h, PN("k_vort"), st, k_vort<P><<<gV, kBlock, 0, st>>>(m, d, DL, u_in, rdpv, qv));
         GRIST_LAUNCH(h, PN("k_ke"), st, k_ke<P><<<gC, kBlock, 0, st>>>(m, d, DL, u_in, K));
         GRIST_LAUNCH(h, PN("k_pv_edge"), st, k_pv_edge<P><<<gE, kBlock, 0, st>>>(m, d, DL, qv, qe));
@@ -953,6 +958,10 @@ extern "C" int grist_dycore_step_hydro(grist_mesh h, grist_dycore_state *S, cons
     if (rc != GRIST_OK) return rc;
     if (cudaSetDevice(mesh_device(h)) != cudaSuccess) return GRIST_ECUDA;
     cudaStream_t st = (cudaStream_t)stream;
+    if (prm->emulate_fp32_rows) {
+        if (prec != GRIST_FP64) return GRIST_EUNSUPPORTED;
+        return dycore_step<PolFP64EMU, false>(h, S, prm, dt, st);
+    }
     switch (prec) {
         case GRIST_FP64: return dycore_step<PolFP64, false>(h, S, prm, dt, st);
         case GRIST_MIX: return dycore_step<PolMIX, false>(h, S, prm, dt, st);
@@ -966,6 +975,10 @@ extern "C" int grist_dycore_step_nh(grist_mesh h, grist_dycore_state *S, const g
     if (rc != GRIST_OK) return rc;
     if (cudaSetDevice(mesh_device(h)) != cudaSuccess) return GRIST_ECUDA;
     cudaStream_t st = (cudaStream_t)stream;
+    if (prm->emulate_fp32_rows) {
+        if (prec != GRIST_FP64) return GRIST_EUNSUPPORTED;
+        return dycore_step<PolFP64EMU, true>(h, S, prm, dt, st);
+    }
     switch (prec) {
         case GRIST_FP64: return dycore_step<PolFP64, true>(h, S, prm, dt, st);
         case GRIST_MIX: return dycore_step<PolMIX, true>(h, S, prm, dt, st);

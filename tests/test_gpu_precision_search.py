@@ -71,6 +71,8 @@ def test_row_emulation(G, hdc):
         assert errs[name] <= e_mix
     with pytest.raises(G.GristError):
         exp.run(G.GRIST_ROW_ALL + 1)
+    with pytest.raises(G.GristError):        # emulation runs on the FP64 path only
+        exp.run(G.GRIST_ROWS["eos"], prec="mix")
 
 
 def test_iterative_search_accepts_rows_within_alpha(G, hdc):
