@@ -60,8 +60,16 @@ typedef enum {
  *                       the implicit column solve, surface pressure, layer
  *                       mass and all global sums in double (Sec. 2.3).
  *   GRIST_MIX_DBL_MASS  as GRIST_MIX but the mass flux dpi*V and its
- *                       divergence in double (Sec. 2.3, Sec. 4.4). */
-typedef enum { GRIST_FP64 = 0, GRIST_MIX = 1, GRIST_MIX_DBL_MASS = 2 } grist_precision;
+ *                       divergence in double (Sec. 2.3, Sec. 4.4).
+ *   GRIST_MIX_DF        as GRIST_MIX but the pressure-gradient, gravity
+ *                       and kinetic-energy-gradient terms of Eq. 5, which
+ *                       GRIST_MIX computes in double, in single-precision
+ *                       arithmetic whose differences of nearly equal double
+ *                       fields (p, layer phi, K) come from double-float
+ *                       splits (about 48 bits); no counterpart in the
+ *                       paper (an FP32-dominant variant of its double rows).
+ *                       Tracers: as GRIST_MIX. */
+typedef enum { GRIST_FP64 = 0, GRIST_MIX = 1, GRIST_MIX_DBL_MASS = 2, GRIST_MIX_DF = 3 } grist_precision;
 
 /* ---------------------------------------------------------------------- */
 /* Mesh (Sec. 2.1: hexagonal Arakawa-C grid; Table 1 grid sizes)           */
@@ -419,6 +427,15 @@ int grist_selftest_conversions(uint64_t n_random, uint64_t seed, uint64_t *out_c
  * memory.  No counterpart in the paper. */
 int grist_selftest_reciprocal(uint64_t n, uint64_t seed, uint64_t *out_checked, uint64_t *out_over_1ulp,
                               uint64_t *out_max_ulp);
+
+/* Diagnostic: check the double-float split used by GRIST_MIX_DF (x ~ h + l,
+ * h = x rounded to binary32, l = the residual rounded to binary32) on n
+ * pseudo-random binary64 values (splitmix64 of seed + i; |x| in
+ * [2^-74, 2^127), any sign and fraction): counts splits whose h differs from
+ * the hardware rounding of x or whose |x - (h + l)| exceeds 2^-47 |x|.
+ * Synchronous (default stream); allocates and frees 16 bytes of device
+ * memory.  No counterpart in the paper. */
+int grist_selftest_split(uint64_t n, uint64_t seed, uint64_t *out_checked, uint64_t *out_bad);
 
 /* Flags raised by the steps since the previous call (read after the stream
  * has been synchronised; synchronises the device and clears the flags). */

@@ -16,14 +16,15 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import (GRIST_FLAG_NONFINITE, GRIST_FLAG_TIMEOUT, GRIST_FP64, GRIST_MIX, GRIST_MIX_DBL_MASS, GRIST_ROW_ALL,
+from ._lib import (GRIST_FLAG_NONFINITE, GRIST_FLAG_TIMEOUT, GRIST_FP64, GRIST_MIX, GRIST_MIX_DBL_MASS, GRIST_MIX_DF,
+                   GRIST_ROW_ALL,
                    GRIST_ROWS, GRIST_SUM_AREA_WEIGHTED, GRIST_SUM_DRY_MASS, GRIST_SUM_TRACER_MASS, GristError)
 
-__all__ = ["Mesh", "DycoreParams", "GRIST_FP64", "GRIST_MIX", "GRIST_MIX_DBL_MASS", "GristError",
+__all__ = ["Mesh", "DycoreParams", "GRIST_FP64", "GRIST_MIX", "GRIST_MIX_DBL_MASS", "GRIST_MIX_DF", "GristError",
            "GRIST_SUM_DRY_MASS", "GRIST_SUM_TRACER_MASS", "GRIST_SUM_AREA_WEIGHTED", "load",
            "GRIST_FLAG_NONFINITE", "GRIST_FLAG_TIMEOUT", "GRIST_ROWS", "GRIST_ROW_ALL"]
 
-PREC = {"fp64": GRIST_FP64, "mix": GRIST_MIX, "mix_dbl_mass": GRIST_MIX_DBL_MASS}
+PREC = {"fp64": GRIST_FP64, "mix": GRIST_MIX, "mix_dbl_mass": GRIST_MIX_DBL_MASS, "mix_df": GRIST_MIX_DF}
 
 
 def load():
@@ -54,6 +55,15 @@ def selftest_conversions(n_random=1 << 28, seed=2404_08849):
     bad = (ctypes.c_uint64 * 2)()
     _lib.check("grist_selftest_conversions", lib.grist_selftest_conversions(int(n_random), int(seed), checked, bad))
     return {"f2d": (int(checked[0]), int(bad[0])), "d2f": (int(checked[1]), int(bad[1]))}
+
+
+def selftest_split(n=1 << 28, seed=2404_08849):
+    """grist_selftest_split: the double-float split against RN32 and its
+    2^-47 error bound.  Returns (checked, failures)."""
+    lib = _lib.load()
+    c, b = ctypes.c_uint64(), ctypes.c_uint64()
+    _lib.check("grist_selftest_split", lib.grist_selftest_split(int(n), int(seed), ctypes.byref(c), ctypes.byref(b)))
+    return int(c.value), int(b.value)
 
 
 def selftest_reciprocal(n=1 << 28, seed=2404_08849):

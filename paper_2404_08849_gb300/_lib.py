@@ -12,7 +12,7 @@ _D = ctypes.c_double
 _I = ctypes.c_int32
 _V = ctypes.c_void_p
 
-GRIST_FP64, GRIST_MIX, GRIST_MIX_DBL_MASS = 0, 1, 2
+GRIST_FP64, GRIST_MIX, GRIST_MIX_DBL_MASS, GRIST_MIX_DF = 0, 1, 2, 3
 GRIST_SUM_DRY_MASS, GRIST_SUM_TRACER_MASS, GRIST_SUM_AREA_WEIGHTED = 0, 1, 2
 GRIST_FLAG_NONFINITE, GRIST_FLAG_TIMEOUT = 0x1, 0x2
 # precision-map rows (grist_dycore_params.emulate_fp32_rows), in the header's order
@@ -79,6 +79,8 @@ EXPORTS = {
     "grist_weighted_sum_noalloc": ([_V, _V, ctypes.c_int64, _V, _V], ctypes.c_int),
     "grist_selftest_conversions": ([ctypes.c_uint64, ctypes.c_uint64, _P(ctypes.c_uint64), _P(ctypes.c_uint64)],
                                    ctypes.c_int),
+    "grist_selftest_split": ([ctypes.c_uint64, ctypes.c_uint64, _P(ctypes.c_uint64), _P(ctypes.c_uint64)],
+                             ctypes.c_int),
     "grist_diag_vorticity": ([_V, _V, ctypes.c_int, _I, _I, _V, _V], ctypes.c_int),
     "grist_selftest_reciprocal": ([ctypes.c_uint64, ctypes.c_uint64, _P(ctypes.c_uint64), _P(ctypes.c_uint64),
                                    _P(ctypes.c_uint64)], ctypes.c_int),

@@ -84,10 +84,30 @@ template <typename T> __device__ __forceinline__ T ldg(const T *p) { return __ld
 //   EMU: the kernels carry the binary32 row emulation of the precision search
 //        (grist_dycore_params.emulate_fp32_rows); the production policies
 //        compile without it.
-struct PolFP64 { using TU = double; using TA = double; using TM = double; static constexpr bool EMU = false; };
-struct PolMIX { using TU = float; using TA = float; using TM = float; static constexpr bool EMU = false; };
-struct PolMIXDBL { using TU = float; using TA = float; using TM = double; static constexpr bool EMU = false; };
-struct PolFP64EMU { using TU = double; using TA = double; using TM = double; static constexpr bool EMU = true; };
+//   DF : the pressure-gradient, gravity and kinetic-energy-gradient terms of
+//        the momentum equation in binary32 arithmetic, their differences of
+//        nearly equal FP64 fields taken from double-float splits
+//        (GRIST_MIX_DF).
+struct PolFP64 {
+    using TU = double; using TA = double; using TM = double;
+    static constexpr bool EMU = false, DF = false;
+};
+struct PolMIX {
+    using TU = float; using TA = float; using TM = float;
+    static constexpr bool EMU = false, DF = false;
+};
+struct PolMIXDBL {
+    using TU = float; using TA = float; using TM = double;
+    static constexpr bool EMU = false, DF = false;
+};
+struct PolFP64EMU {
+    using TU = double; using TA = double; using TM = double;
+    static constexpr bool EMU = true, DF = false;
+};
+struct PolMIXDF {
+    using TU = float; using TA = float; using TM = float;
+    static constexpr bool EMU = false, DF = true;
+};
 
 template <typename T> struct Coef;
 template <> struct Coef<double> {
@@ -180,6 +200,47 @@ __device__ __forceinline__ float d2f(double x) {
     }
     return __uint_as_float(mag | s);
 }
+
+// Double-float split in integer arithmetic: x ~ h + l with h = RN32(x) and
+// l = the residual x - h (exact in binary64, at most 29 significant bits)
+// rounded to binary32, so h + l carries about 48 bits of x.  The residual
+// is the difference of the two significands aligned at x's exponent.  For
+// |x| < 2^-74 (where the residual's scale leaves the binary32 range) and
+// for non-finite x, l = 0.  No FP64 instruction is issued.
+__device__ __forceinline__ void split_df(double x, float &h, float &l) {
+    h = d2f(x);
+    l = 0.f;
+    const uint32_t hx = (uint32_t)__double2hiint(x), lx = (uint32_t)__double2loint(x);
+    const int ex = (int)((hx >> 20) & 0x7ffu);
+    if (ex < 949 || ex > 1150) return;
+    const uint32_t hb = __float_as_uint(h);
+    const int eh = (int)((hb >> 23) & 0xffu) + 896;   // binary64 exponent of h (h is normal here)
+    const long long mx = (long long)(((unsigned long long)((hx & 0xfffffu) | 0x100000u) << 32) | lx);
+    long long mh = (long long)((unsigned long long)((hb & 0x7fffffu) | 0x800000u) << 29);
+    if (eh == ex + 1) mh <<= 1;                        // x rounded up across a power of two
+    const long long r = mx - mh;                       // |r| <= 2^28: units of 2^(ex - 1075)
+    const float scale = __uint_as_float((uint32_t)(ex - 1075 + 127) << 23);
+    const float rl = __int2float_rn((int)r) * scale;
+    l = (hx & 0x80000000u) ? -rl : rl;
+}
+
+// binary64 -> binary32 by truncation, for inputs that are multiplied, not
+// differenced, inside a tendency rounded to binary32 anyway: error below one
+// binary32 ulp, no branches; magnitudes below 2^-126 give 0; finite inputs
+// below 2^128 only (the dycore's layer and edge factors).
+__device__ __forceinline__ float d2f_trunc(double x) {
+    const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+    const uint32_t a = hi & 0x7fffffffu;
+    uint32_t m = ((a - 0x38000000u) << 3) | (lo >> 29);
+    m = a < 0x38100000u ? 0u : m;
+    return __uint_as_float(m | (hi & 0x80000000u));
+}
+
+// a - b for two binary64 values of similar size, in binary32 arithmetic
+// from their double-float splits: the high parts subtract exactly
+// (Sterbenz, when within a factor of two), the low parts add the rest; the
+// result is the difference to about 2^-24 of itself.
+__device__ __forceinline__ float diff_df(float ah, float al, float bh, float bl) { return (ah - bh) + (al - bl); }
 
 // cv<T>(x): x in type T, through the integer conversions above.
 template <typename T> struct Cvt;

@@ -1,7 +1,8 @@
 // convert_check.cu - self-tests of the arithmetic helpers in common.cuh:
 // the integer binary32 <-> binary64 conversions (f2d, d2f) against the
-// hardware conversions, and the Newton-Raphson reciprocal (rcp_nr) against
-// the IEEE quotient 1.0 / x.
+// hardware conversions, the Newton-Raphson reciprocal (rcp_nr) against the
+// IEEE quotient 1.0 / x, and the double-float split (split_df) against its
+// error bound.
 // Each kernel compares both results in-register and counts disagreements,
 // so the 2^32-pattern sweeps need no input or output buffers.
 #include "common.cuh"
@@ -101,10 +102,54 @@ __global__ void k_check_rcp(unsigned long long n, unsigned long long seed, unsig
     atomicMax(out + 2, worst);
 }
 
+// out[0] checked, out[1] splits with h != RN32(x) or |x - (h + l)| above
+// 2^-47 |x| (the bound is exact arithmetic: h and l are floats, so
+// x - h - l is formed in binary64 without error for these magnitudes)
+__global__ void k_check_split(unsigned long long n, unsigned long long seed, unsigned long long *out) {
+    unsigned long long cnt = 0, bad = 0;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        unsigned long long b = splitmix64(seed + i);
+        // exponent in [949, 1149]: |x| in [2^-74, 2^127)
+        const unsigned long long ex = 949ull + (splitmix64(b ^ 0x2545f491ull) % 201ull);
+        b = (b & 0x800fffffffffffffull) | (ex << 52);
+        const double x = __longlong_as_double((long long)b);
+        float h, l;
+        split_df(x, h, l);
+        const double err = fabs((x - (double)h) - (double)l);
+        bad += (__float_as_uint(h) != __float_as_uint((float)x)) || !(err <= ldexp(fabs(x), -47));
+        cnt++;
+    }
+    atomicAdd(out + 0, cnt);
+    atomicAdd(out + 1, bad);
+}
+
 }  // namespace
 }  // namespace grist
 
 using namespace grist;
+
+extern "C" int grist_selftest_split(uint64_t n, uint64_t seed, uint64_t *out_checked, uint64_t *out_bad) {
+    if (!out_checked || !out_bad) return GRIST_EINVAL;
+    unsigned long long *d = nullptr;
+    if (cudaMalloc(&d, 2 * sizeof(unsigned long long)) != cudaSuccess) return GRIST_ENOMEM;
+    unsigned long long h[2] = {0, 0};
+    int rc = GRIST_OK;
+    if (cudaMemset(d, 0, sizeof(h)) != cudaSuccess) rc = GRIST_ECUDA;
+    if (rc == GRIST_OK) {
+        int dev = 0, nsm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        k_check_split<<<(unsigned)(nsm > 0 ? nsm * 8 : 1024), 256>>>((unsigned long long)n, (unsigned long long)seed, d);
+        if (cudaGetLastError() != cudaSuccess) rc = GRIST_ECUDA;
+    }
+    if (rc == GRIST_OK && cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) rc = GRIST_ECUDA;
+    cudaFree(d);
+    if (rc != GRIST_OK) return rc;
+    *out_checked = h[0];
+    *out_bad = h[1];
+    return GRIST_OK;
+}
 
 extern "C" int grist_selftest_reciprocal(uint64_t n, uint64_t seed, uint64_t *out_checked, uint64_t *out_over_1ulp,
                                          uint64_t *out_max_ulp) {

@@ -21,7 +21,7 @@
 
 #include "common.cuh"
 
-#define PN(n) (sizeof(TA) == 4 ? (sizeof(TM) == 8 ? n "/mixdbl" : n "/mix") : n "/fp64")
+#define PN(n) (P::DF ? n "/mixdf" : (sizeof(TA) == 4 ? (sizeof(TM) == 8 ? n "/mixdbl" : n "/mix") : n "/fp64"))
 
 namespace grist {
 namespace {
@@ -50,6 +50,15 @@ template <bool E> __device__ __forceinline__ double emu(double x, uint32_t mask,
     return x;
 }
 template <bool E> __device__ __forceinline__ float emu(float x, uint32_t, uint32_t) { return x; }
+
+// GRIST_MIX_DF: a double field that the momentum equation only differences
+// (layer phi, K) is stored as its double-float split (h, l) in the same
+// 8-byte slot, read back as a float2.
+__device__ __forceinline__ double pack_split(double x) {
+    float h, l;
+    split_df(x, h, l);
+    return __hiloint2double(__float_as_int(l), __float_as_int(h));
+}
 
 // Compensated single-precision accumulation (Knuth's TwoSum): a value is
 // hi + lo with |lo| <= ulp(hi)/2, so a sum of FP32 terms carries about 48
@@ -327,7 +336,7 @@ __global__ void k_theta_update(DevMesh m, DyPar d, LevelDiv Dv, const typename P
 // Eq. 8 (hydrostatic diagnostics), one warp per column: mid-layer pressure,
 // alpha = Rd theta (p/p0)^kappa / p, geopotential integrated upward from
 // phi_s by a suffix scan, layer geopotential = mean of its interfaces.
-template <bool EMU>
+template <bool EMU, bool DF>
 __global__ void k_hydro_diag(DevMesh m, DyPar d, const double *__restrict__ ps, const double *__restrict__ th,
                              double *__restrict__ p, double *__restrict__ al, double *__restrict__ phl) {
     const int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -358,7 +367,8 @@ __global__ void k_hydro_diag(DevMesh m, DyPar d, const double *__restrict__ ps, 
             const size_t x = (size_t)i * d.ld + k;
             p[x] = emu<EMU>(pk, d.emu, GRIST_ROW_EOS);
             al[x] = emu<EMU>(a, d.emu, GRIST_ROW_EOS);
-            phl[x] = emu<EMU>(carry + (v - contrib) + 0.5 * contrib, d.emu, GRIST_ROW_EOS);
+            const double ph = carry + (v - contrib) + 0.5 * contrib;
+            phl[x] = DF ? pack_split(ph) : emu<EMU>(ph, d.emu, GRIST_ROW_EOS);
         }
         carry += __shfl_sync(0xffffffffu, v, 0);
     }
@@ -409,7 +419,7 @@ __global__ void k_ke(DevMesh m, DyPar d, LevelDiv Dv, const typename P::TU *__re
         const double ue = cv<double>(ldg(u + (size_t)ldg(m.eoc + i * 6 + j) * d.ld + k));
         s += ldg(m.kec2 + i * 6 + j) * ue * ue;
     }
-    K[(size_t)i * d.ld + k] = emu<P::EMU>(s, d.emu, GRIST_ROW_KE_GRAD);
+    K[(size_t)i * d.ld + k] = P::DF ? pack_split(s) : emu<P::EMU>(s, d.emu, GRIST_ROW_KE_GRAD);
 }
 
 template <class P>
@@ -458,6 +468,38 @@ __global__ void k_momentum(DevMesh m, DyPar d, LevelDiv Dv, const typename P::TU
         pv += ldg(Coef<TA>::wpv(m) + e * 10 + j) * cv<TA>(ldg(F + y)) * ((TA)0.5 * (qee + ldg(qe + y)));
     }
     const size_t a1 = (size_t)c.x * d.ld + k, a2 = (size_t)c.y * d.ld + k;
+    if (P::DF) {
+        // GRIST_MIX_DF: the slow tendency in binary32; the differences of the
+        // double fields p, layer phi and K from their double-float splits
+        // (p split here, phi and K stored split), the factors that are only
+        // multiplied truncated to binary32, every other operation in binary32
+        // - no FP64 instruction
+        const float uk = (float)ldg(u_s + x);
+        float va32 = 0.f;
+        if (k < d.L - 1)
+            va32 = (d2f_trunc(ldg(Mv + (size_t)c.x * d.ldi + k + 1)) +
+                    d2f_trunc(ldg(Mv + (size_t)c.y * d.ldi + k + 1))) *
+                   ((float)ldg(u_s + x + 1) - uk);
+        if (k > 0)
+            va32 = fmaf(d2f_trunc(ldg(Mv + (size_t)c.x * d.ldi + k)) + d2f_trunc(ldg(Mv + (size_t)c.y * d.ldi + k)),
+                        uk - (float)ldg(u_s + x - 1), va32);
+        va32 *= d2f_trunc(ldg(d.rdB + k)) * d2f_trunc(ldg(rsum_e + e));
+        float p1h, p1l, p2h, p2l;
+        split_df(ldg(p + a1), p1h, p1l);
+        split_df(ldg(p + a2), p2h, p2l);
+        const float2 f1 = ldg(reinterpret_cast<const float2 *>(phl) + a1);
+        const float2 f2 = ldg(reinterpret_cast<const float2 *>(phl) + a2);
+        const float2 k1 = ldg(reinterpret_cast<const float2 *>(K) + a1);
+        const float2 k2 = ldg(reinterpret_cast<const float2 *>(K) + a2);
+        const float de = NH ? d2f_trunc(ldg(dpp + a1)) + d2f_trunc(ldg(dpp + a2)) : 2.f;
+        const float grad = fmaf(d2f_trunc(ldg(al + a1)) + d2f_trunc(ldg(al + a2)), diff_df(p2h, p2l, p1h, p1l),
+                                fmaf(de, diff_df(f2.x, f2.y, f1.x, f1.y), diff_df(k2.x, k2.y, k1.x, k1.y)));
+        const float tend = (float)pv + fmaf(d2f_trunc(ldg(m.hrdc + e)), grad, -va32);
+        const float v = (float)u_n[x] + d2f(dts) * tend;
+        if (!isfinite(v)) atomicOr(status, GRIST_FLAG_NONFINITE);
+        u_out[x] = (TU)v;
+        return;
+    }
     const double uk = cv<double>(ldg(u_s + x));
     double va = 0.0;
     if (k < d.L - 1)
@@ -627,7 +669,7 @@ __device__ __forceinline__ void stage_out(double *X, size_t S, int col0, int nco
 // (interface value 1 at top and bottom) for the momentum equation.  phi_out
 // may be phi_r and p may be p_r (the last stage writes the state in place):
 // each block reads all reference values of its columns before writing them.
-template <bool EMU>
+template <bool EMU, bool DF>
 __global__ void __launch_bounds__(32, kSolveMinBlocks) k_nh_solve(DevMesh m, DyPar d, const double *__restrict__ wst,
                                                  const double *__restrict__ phst, const double *__restrict__ th,
                                                  const double *__restrict__ rth_r, const double *phi_r,
@@ -743,7 +785,8 @@ __global__ void __launch_bounds__(32, kSolveMinBlocks) k_nh_solve(DevMesh m, DyP
                 }
                 sA[2 * kStage + o] = emu<EMU>(pk, d.emu, GRIST_ROW_EOS);
                 sA[3 * kStage + o] = emu<EMU>((phi_top - phi_bot) * (ldg(d.rdB + k) * rdps), d.emu, GRIST_ROW_EOS);
-                sA[4 * kStage + o] = emu<EMU>(0.5 * (phi_top + phi_bot), d.emu, GRIST_ROW_EOS);
+                sA[4 * kStage + o] = DF ? pack_split(0.5 * (phi_top + phi_bot))
+                                        : emu<EMU>(0.5 * (phi_top + phi_bot), d.emu, GRIST_ROW_EOS);
                 sA[1 * kStage + o] = phi_bot;   // w_top of this row is no longer needed
                 dtop = dcur;
                 pprev = pk;
@@ -901,11 +944,11 @@ int dycore_step(grist_mesh_s *h, grist_dycore_state *S, const grist_dycore_param
             else
                 GRIST_LAUNCH(h, PN("k_nh_explicit"), st, k_nh_explicit<P, false><<<gI, kBlock, 0, st>>>(
                     m, d, DI, u_in, rdps, Mv, w_in, phi_in, S->w, S->phi, p_n, fwn, wst, phst, h3));
-            GRIST_LAUNCH(h, PN("k_nh_solve"), st, k_nh_solve<P::EMU><<<gSolve, kSolveCols, 0, st>>>(
+            GRIST_LAUNCH(h, PN("k_nh_solve"), st, k_nh_solve<P::EMU, P::DF><<<gSolve, kSolveCols, 0, st>>>(
                 m, d, wst, phst, th_outs[s3], rthn, S->phi, p_n, ps_outs[s3], h3, w_outs[s3],
                 phi_outs[s3], p_outs[s3], alp, phl, dpp, bpos, bneg));
         } else {
-            GRIST_LAUNCH(h, PN("k_hydro_diag"), st, k_hydro_diag<P::EMU><<<gW, kBlock, 0, st>>>(
+            GRIST_LAUNCH(h, PN("k_hydro_diag"), st, k_hydro_diag<P::EMU, P::DF><<<gW, kBlock, 0, st>>>(
                 m, d, ps_outs[s3], th_outs[s3], p, alp, phl));
         }
         GRIST_LAUNCH(h, PN("k_vertex_mass"), st, k_vertex_mass<P::EMU><<<gVx, kBlock, 0, st>>>(m, d, ps_in, rdpv));
@@ -930,7 +973,8 @@ int check(grist_mesh h, grist_dycore_state *S, const grist_dycore_params *prm, g
           bool nh) {
     if (!h || !S || !prm) return GRIST_EINVAL;
     if (!(dt > 0) || !std::isfinite(dt)) return GRIST_EINVAL;
-    if (prec != GRIST_FP64 && prec != GRIST_MIX && prec != GRIST_MIX_DBL_MASS) return GRIST_EINVAL;
+    if (prec != GRIST_FP64 && prec != GRIST_MIX && prec != GRIST_MIX_DBL_MASS && prec != GRIST_MIX_DF)
+        return GRIST_EINVAL;
     const int L = prm->n_levels;
     if (L < 2 || L > GRIST_MAXL || prm->ld < L || prm->ld_int < L + 1) return GRIST_EINVAL;
     if (nh && L > kNHMax) return GRIST_EUNSUPPORTED;
@@ -965,6 +1009,7 @@ extern "C" int grist_dycore_step_hydro(grist_mesh h, grist_dycore_state *S, cons
     switch (prec) {
         case GRIST_FP64: return dycore_step<PolFP64, false>(h, S, prm, dt, st);
         case GRIST_MIX: return dycore_step<PolMIX, false>(h, S, prm, dt, st);
+        case GRIST_MIX_DF: return dycore_step<PolMIXDF, false>(h, S, prm, dt, st);
         default: return dycore_step<PolMIXDBL, false>(h, S, prm, dt, st);
     }
 }
@@ -982,6 +1027,7 @@ extern "C" int grist_dycore_step_nh(grist_mesh h, grist_dycore_state *S, const g
     switch (prec) {
         case GRIST_FP64: return dycore_step<PolFP64, true>(h, S, prm, dt, st);
         case GRIST_MIX: return dycore_step<PolMIX, true>(h, S, prm, dt, st);
+        case GRIST_MIX_DF: return dycore_step<PolMIXDF, true>(h, S, prm, dt, st);
         default: return dycore_step<PolMIXDBL, true>(h, S, prm, dt, st);
     }
 }
@@ -989,7 +1035,8 @@ extern "C" int grist_dycore_step_nh(grist_mesh h, grist_dycore_state *S, const g
 extern "C" int grist_diag_vorticity(grist_mesh h, const void *u, grist_precision prec, int32_t n_levels, int32_t ld,
                                     double *vor, void *stream) {
     if (!h || !u || !vor || n_levels < 1 || n_levels > GRIST_MAXL || ld < n_levels) return GRIST_EINVAL;
-    if (prec != GRIST_FP64 && prec != GRIST_MIX && prec != GRIST_MIX_DBL_MASS) return GRIST_EINVAL;
+    if (prec != GRIST_FP64 && prec != GRIST_MIX && prec != GRIST_MIX_DBL_MASS && prec != GRIST_MIX_DF)
+        return GRIST_EINVAL;
     if (cudaSetDevice(mesh_device(h)) != cudaSuccess) return GRIST_ECUDA;
     const DevMesh &m = dev_mesh(h);
     cudaStream_t st = (cudaStream_t)stream;

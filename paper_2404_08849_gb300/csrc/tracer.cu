@@ -992,7 +992,8 @@ int validate(const grist_tracer_batch *b, double dt) {
     if (!b || (b->n_members > 0 && !b->members) || b->n_members < 0) return GRIST_EINVAL;
     if (b->n_members > GRIST_MAX_MEMBERS) return GRIST_EUNSUPPORTED;
     if (!(dt > 0) || !std::isfinite(dt)) return GRIST_EINVAL;
-    if (b->prec != GRIST_FP64 && b->prec != GRIST_MIX && b->prec != GRIST_MIX_DBL_MASS) return GRIST_EINVAL;
+    if (b->prec != GRIST_FP64 && b->prec != GRIST_MIX && b->prec != GRIST_MIX_DBL_MASS && b->prec != GRIST_MIX_DF)
+        return GRIST_EINVAL;
     if (!std::isfinite(b->beta_upwind)) return GRIST_EINVAL;
     for (int i = 0; i < b->n_members; i++) {
         const grist_tracer_member &mb = b->members[i];

@@ -136,7 +136,7 @@ def main():
     truth = exp.run(0)
     config, kept, table = iterative_search(exp, alpha=args.alpha, truth=truth)
     single = {name: exp.error(exp.run(GRIST_ROWS[name]), truth) for name in DEFAULT_ORDER}
-    policies = {p: exp.error(exp.run(0, prec=p), truth) for p in ("mix", "mix_dbl_mass")}
+    policies = {p: exp.error(exp.run(0, prec=p), truth) for p in ("mix", "mix_dbl_mass", "mix_df")}
     print(json.dumps({"case": {"mesh_level": args.level, "n_levels": args.levels, "nonhydrostatic": args.nh,
                                "dt_s": dt, "steps": args.steps, "alpha": args.alpha},
                       "trials": table, "accepted_rows": kept, "accepted_mask": config,

@@ -37,3 +37,16 @@ def test_fma_reciprocal_within_one_ulp():
     checked, over, worst = G.selftest_reciprocal(n=1 << 28, seed=240408849)
     assert checked == 1 << 28
     assert over == 0 and worst <= 1
+
+
+def test_double_float_split_bound():
+    """The double-float split of GRIST_MIX_DF: h is x rounded to binary32
+    (bit-exact against the hardware) and h + l is within 2^-47 |x|, over
+    2^28 pseudo-random doubles of every sign and of magnitudes 2^-74..2^127."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    import paper_2404_08849_gb300 as G
+    G.load()
+    checked, bad = G.selftest_split(n=1 << 28, seed=240408849)
+    assert checked == 1 << 28 and bad == 0
