@@ -66,9 +66,11 @@ typedef enum {
  *                       GRIST_MIX computes in double, in single-precision
  *                       arithmetic whose differences of nearly equal double
  *                       fields (p, layer phi, K) come from double-float
- *                       splits (about 48 bits); no counterpart in the
- *                       paper (an FP32-dominant variant of its double rows).
- *                       Tracers: as GRIST_MIX. */
+ *                       splits (about 48 bits), and the non-hydrostatic
+ *                       equation of state (Eq. 9) as a double base value
+ *                       plus a single-precision increment; no counterpart
+ *                       in the paper (an FP32-dominant variant of its
+ *                       double rows).  Tracers: as GRIST_MIX. */
 typedef enum { GRIST_FP64 = 0, GRIST_MIX = 1, GRIST_MIX_DBL_MASS = 2, GRIST_MIX_DF = 3 } grist_precision;
 
 /* ---------------------------------------------------------------------- */

@@ -103,6 +103,7 @@ __device__ __forceinline__ double col_reduce(double part) {
 // executing the call.
 struct Binom {
     double c[10];
+    float f[6];   // the same coefficients in binary32 (GRIST_MIX_DF increments)
 };
 
 template <int N> __device__ __forceinline__ double horner(double x, const Binom &B) {
@@ -133,7 +134,23 @@ Binom binomial(double g) {
     Binom b;
     b.c[0] = 1.0;
     for (int n = 1; n < 10; n++) b.c[n] = b.c[n - 1] * (g - (n - 1)) / n;
+    for (int n = 0; n < 6; n++) b.f[n] = (float)b.c[n];
     return b;
+}
+
+// GRIST_MIX_DF form of p (1 + x)^g for |x| <= 2^-6: the increment
+// (1 + x)^g - 1 = x (C1 + x (C2 + ... + x C5)) in binary32 (the omitted
+// terms are below 2^-30 of it), added to p in FP64 - the increment's
+// binary32 rounding, about 2^-23 |g x|, is ~1e-10 of p for |x| ~ 1e-3.
+// Larger |x| (none in a stable step) falls back to the FP64 pow.
+__device__ __forceinline__ double scale_near1_df(double p, double x, double g, const Binom &B) {
+    const unsigned hx = (unsigned)__double2hiint(x) & 0x7fffffffu;
+    if (hx > 0x3f900000u) return p * pow(1.0 + x, g);
+    const float xf = d2f(x);
+    float s = B.f[5];
+#pragma unroll
+    for (int n = 4; n >= 1; n--) s = fmaf(s, xf, B.f[n]);
+    return fma(p, f2d(s * xf), p);
 }
 
 // ---------------------------------------------------------------------------
@@ -710,9 +727,9 @@ __global__ void __launch_bounds__(32, kSolveMinBlocks) k_nh_solve(DevMesh m, DyP
                 const int o = kk * kRow + lane;
                 const double fbot = sA[0 * kStage + o], rbot = sA[1 * kStage + o];
                 const double rdfj = rcp_nr(ftop - fbot);
-                const double pstj = sA[4 * kStage + o] *
-                                    pow_near1(sA[2 * kStage + o] * sA[3 * kStage + o] * ((rtop - rbot) * rdfj),
-                                              d.gamma, bg_pos, amask);
+                const double rr = sA[2 * kStage + o] * sA[3 * kStage + o] * ((rtop - rbot) * rdfj);
+                const double pstj = DF ? scale_near1_df(sA[4 * kStage + o], rr - 1.0, d.gamma, bg_pos)
+                                       : sA[4 * kStage + o] * pow_near1(rr, d.gamma, bg_pos, amask);
                 pst[j] = pstj;
                 rdf[j] = rdfj;
                 const double C = gbg * pstj * rdfj;
@@ -775,7 +792,9 @@ __global__ void __launch_bounds__(32, kSolveMinBlocks) k_nh_solve(DevMesh m, DyP
                 const double w_top = sA[1 * kStage + o];
                 const double w_bot = (kk + 1 < nk) ? sA[1 * kStage + o + kRow] : sA[6 * kStage + lane];
                 const double phi_bot = (k + 1 < L) ? fma(bg, w_bot, sA[o]) : ldg(d.phis + i);
-                const double pk = pst[k] * pow1p_near0(bg * (w_top - w_bot) * rdf[k], -d.gamma, bg_neg, amask);
+                const double xk = bg * (w_top - w_bot) * rdf[k];
+                const double pk = DF ? scale_near1_df(pst[k], xk, -d.gamma, bg_neg)
+                                     : pst[k] * pow1p_near0(xk, -d.gamma, bg_neg, amask);
                 double dcur = 1.0;
                 if (k > 0) {
                     dcur = (pk - pprev) * (ldg(d.rdBi + k) * rdps);

@@ -1,6 +1,7 @@
 """GPU: the FP32-dominant policy GRIST_MIX_DF (the pressure-gradient,
 gravity and kinetic-energy-gradient terms in binary32 arithmetic with their
-differences of double fields taken from double-float splits).  One step of
+differences of double fields taken from double-float splits; the NH
+equation of state as a double base plus a binary32 increment).  One step of
 the hydrostatic and the non-hydrostatic core against the FP64 oracle within
 the mixed-policy tolerances, and against the GRIST_MIX step (which computes
 those terms in FP64): the two agree to single-precision rounding of the
