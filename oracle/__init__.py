@@ -150,12 +150,13 @@ def _setup():
         "orc_hydro_diag": [Pp, _I, pd, pd, pd, pd, pd, pd],
         "orc_eos": [Pp, _I, pd, pd, pd],
         "orc_momentum_tend": [M, _I, pd, pd, pd, pd, pd, pd, pd, pd, pd],
-        "orc_dycore_step_hydro": [M, Pp, pd, pd, pd, pd, pd, _D],
+        "orc_dycore_step_hydro": [M, Pp, pd, pd, pd, pd, pd, pd, _D],
+        "orc_tracer_vertical": [_I, _I, _I, pd, pd, pd, _D, _D],
         "orc_interface_hadv": [M, _I, pd, pd, pd],
         "orc_interface_vadv": [_I, _I, pd, pd, pd, pd],
         "orc_thomas": [_I, pd, pd, pd, pd, pd],
         "orc_vertical_solve": [Pp, _I, pd, pd, pd, pd, _D, pd, pd, pd],
-        "orc_dycore_step_nh": [M, Pp, pd, pd, pd, pd, pd, pd, pd, _D],
+        "orc_dycore_step_nh": [M, Pp, pd, pd, pd, pd, pd, pd, pd, pd, _D],
         "orc_compensated_sum": [ctypes.c_int64, pd, pd, pd],
         "orc_dry_mass": [M, pd, _D, pd],
         "orc_tracer_mass": [M, _I, pd, pd, pd],
@@ -254,6 +255,16 @@ def tracer_step(M: Mesh, q, dpi, F, dt, beta=1.0, fct=True):
     return q
 
 
+def tracer_vertical_step(q, dpi, Mv, dt, cmax=1.0):
+    """Vertical transport delta(M q) of Eq. 10 (adaptively implicit upwind,
+    see orc_tracer_vertical); q [T][nC][L] copied and returned, dpi [nC][L]
+    the layer mass at the start, Mv [nC][L+1] the vertical mass flux."""
+    q = np.array(q, dtype=np.float64, order="C", copy=True)
+    T, nC, L = q.shape
+    _f().orc_tracer_vertical(nC, L, T, _dp(q), _dp(_f64(dpi)), _dp(_f64(Mv)), dt, cmax)
+    return q
+
+
 def mass(M: Mesh, P: Params, ps, u):
     L = P.L
     dpi = np.empty((M.nC, L)); F = np.empty((M.nE, L)); D = np.empty((M.nC, L))
@@ -291,15 +302,18 @@ def momentum_tend(M: Mesh, L, u, dpi, F, Mv, p, alpha, phi_layer, dpdpi=None):
     return out
 
 
-def dycore_step_hydro(M: Mesh, P: Params, state, dt, flux_accum=None):
-    """One HDC step; state dict with ps, u, dpi_theta (copied, returned)."""
+def dycore_step_hydro(M: Mesh, P: Params, state, dt, flux_accum=None, vflux_accum=None):
+    """One HDC step; state dict with ps, u, dpi_theta (copied, returned).
+    flux_accum [nE][L] / vflux_accum [nC][L+1]: the final stage's horizontal
+    / vertical mass flux is added in place."""
     ps = np.array(state["ps"], np.float64, copy=True)
     u = np.array(state["u"], np.float64, copy=True)
     th = np.array(state["dpi_theta"], np.float64, copy=True)
     wgt = np.zeros(1)
     fa = flux_accum if flux_accum is not None else None
+    va = vflux_accum if vflux_accum is not None else None
     _f().orc_dycore_step_hydro(M.ref, P.ref, _dp(ps), _dp(u), _dp(th), _dp(fa) if fa is not None else None,
-                               _dp(wgt), dt)
+                               _dp(va) if va is not None else None, _dp(wgt), dt)
     return {"ps": ps, "u": u, "dpi_theta": th, "accum_weight": float(wgt[0])}
 
 
@@ -331,7 +345,7 @@ def vertical_solve(P: Params, w_star, phi_star, dpi_theta, dpi, dts):
     return w, phi, p
 
 
-def dycore_step_nh(M: Mesh, P: Params, state, dt, flux_accum=None):
+def dycore_step_nh(M: Mesh, P: Params, state, dt, flux_accum=None, vflux_accum=None):
     """One NDC step; state dict with ps, u, dpi_theta, w, phi (copied)."""
     ps = np.array(state["ps"], np.float64, copy=True)
     u = np.array(state["u"], np.float64, copy=True)
@@ -340,8 +354,9 @@ def dycore_step_nh(M: Mesh, P: Params, state, dt, flux_accum=None):
     phi = np.array(state["phi"], np.float64, copy=True)
     wgt = np.zeros(1)
     fa = flux_accum if flux_accum is not None else None
+    va = vflux_accum if vflux_accum is not None else None
     _f().orc_dycore_step_nh(M.ref, P.ref, _dp(ps), _dp(u), _dp(th), _dp(w), _dp(phi),
-                            _dp(fa) if fa is not None else None, _dp(wgt), dt)
+                            _dp(fa) if fa is not None else None, _dp(va) if va is not None else None, _dp(wgt), dt)
     return {"ps": ps, "u": u, "dpi_theta": th, "w": w, "phi": phi, "accum_weight": float(wgt[0])}
 
 

@@ -510,12 +510,14 @@ void orc_momentum_tend(const orc_mesh *m, int L, const double *u, const double *
  * (Eq. 5) uses the stage-input wind for its advective terms and the new
  * pressure / geopotential for the pressure-gradient and gravity terms.
  * The final stage's mass flux is added to flux_accum (time-mean flux for
- * the tracer solver) and *accum_weight is incremented.
+ * the tracer solver), its vertical mass flux M [nC][L+1] (the delta(M q)
+ * flux of Eq. 10) to vflux_accum when given, and *accum_weight is
+ * incremented.
  * ps [nC], u [nE][L], dpi_theta [nC][L]: in/out.
  * ---------------------------------------------------------------------- */
 void orc_dycore_step_hydro(const orc_mesh *m, const orc_params *P, double *ps, double *u,
-                           double *dpi_theta, double *flux_accum, double *accum_weight,
-                           double dt) {
+                           double *dpi_theta, double *flux_accum, double *vflux_accum,
+                           double *accum_weight, double dt) {
     int L = P->L;
     size_t nC = m->nC, nCL = nC * L, nEL = (size_t)m->nE * L;
     double *ps_n = (double *)xalloc(sizeof(double) * nC), *u_n = (double *)xalloc(sizeof(double) * nEL),
@@ -548,6 +550,8 @@ void orc_dycore_step_hydro(const orc_mesh *m, const orc_params *P, double *ps, d
             for (size_t x = 0; x < nEL; x++) flux_accum[x] += F[x];
             if (accum_weight) *accum_weight += 1.0;
         }
+        if (s == 2 && vflux_accum)
+            for (size_t x = 0; x < nC * (L + 1); x++) vflux_accum[x] += M[x];
         memcpy(ps_s, ps, sizeof(double) * nC);
         memcpy(u_s, u, sizeof(double) * nEL);
         memcpy(th_s, dpi_theta, sizeof(double) * nCL);
@@ -705,7 +709,7 @@ static void dpdpi_layer(int nC, int L, const double *p, const double *dpi, doubl
  * ---------------------------------------------------------------------- */
 void orc_dycore_step_nh(const orc_mesh *m, const orc_params *P, double *ps, double *u,
                         double *dpi_theta, double *w, double *phi, double *flux_accum,
-                        double *accum_weight, double dt) {
+                        double *vflux_accum, double *accum_weight, double dt) {
     int L = P->L, Li = L + 1;
     size_t nC = m->nC, nCL = nC * L, nEL = (size_t)m->nE * L, nCI = nC * Li;
     double *ps_n = (double *)xalloc(sizeof(double) * nC), *u_n = (double *)xalloc(sizeof(double) * nEL),
@@ -779,6 +783,8 @@ void orc_dycore_step_nh(const orc_mesh *m, const orc_params *P, double *ps, doub
             for (size_t x = 0; x < nEL; x++) flux_accum[x] += F[x];
             if (accum_weight) *accum_weight += 1.0;
         }
+        if (s == 2 && vflux_accum)
+            for (size_t x = 0; x < nCI; x++) vflux_accum[x] += M[x];
         memcpy(ps_s, ps, sizeof(double) * nC); memcpy(u_s, u, sizeof(double) * nEL);
         memcpy(th_s, dpi_theta, sizeof(double) * nCL); memcpy(w_s, w, sizeof(double) * nCI);
         memcpy(phi_s, phi, sizeof(double) * nCI);
@@ -787,6 +793,66 @@ void orc_dycore_step_nh(const orc_mesh *m, const orc_params *P, double *ps, doub
     free(w_s); free(phi_s); free(dpi); free(dpi_new); free(dpi_n); free(F); free(D); free(pst); free(M);
     free(tht); free(p_n); free(p); free(hw); free(vw); free(hp); free(vp); free(wst); free(pstar);
     free(al); free(phl); free(dpp); free(ut);
+}
+
+/* ------------------------------------------------------------------------
+ * Vertical tracer transport: the delta(M q) term of Eq. 10.  Sec. 2.1 names
+ * "an adaptively implicit method" for the vertical (after Li and Zhang
+ * 2022, not available here); the reading is a Courant-number-dependent
+ * split of the vertical mass flux:
+ *   at interior interface j (between layers j-1 above and j below; M_j > 0
+ *   carries mass from j-1 into j) the donor layer is j-1 if M_j > 0, else j;
+ *   its Courant number c_j = |M_j| dt / dpi_donor; the explicit share is
+ *   Me_j = f_j M_j with f_j = min(1, cmax / c_j), the implicit share
+ *   Mi_j = M_j - Me_j (zero wherever c_j <= cmax).
+ *   Both shares are first-order upwind: the explicit one from q at the start
+ *   of the step, the implicit one from q at the end (backward Euler), so for
+ *   each layer k (M_0 = M_L = 0)
+ *     dpi+_k q+_k + dt (Fi_{k+1} - Fi_k) = dpi_k q_k - dt (Fe_{k+1} - Fe_k),
+ *     dpi+_k = dpi_k - dt (M_{k+1} - M_k),
+ *   F_j = M_j q(donor of j): a tridiagonal M-matrix system per column,
+ *   solved by the Thomas algorithm.  Constants stay constant, column mass
+ *   sum_k dpi+ q+ = sum_k dpi q is conserved, and no new extrema appear.
+ * q [T][nC][L] in/out; dpi [nC][L] the layer mass at the start of the
+ * step; Mv [nC][L+1] the (time-mean) vertical mass flux.
+ * ---------------------------------------------------------------------- */
+void orc_tracer_vertical(int nC, int L, int T, double *q, const double *dpi, const double *Mv, double dt,
+                         double cmax) {
+    const int Li = L + 1;
+#pragma omp parallel for
+    for (int i = 0; i < nC; i++) {
+        double *me = (double *)xalloc(sizeof(double) * Li), *mi = (double *)xalloc(sizeof(double) * Li);
+        double *dpn = (double *)xalloc(sizeof(double) * L);
+        double *a = (double *)xalloc(sizeof(double) * L), *b = (double *)xalloc(sizeof(double) * L),
+               *c = (double *)xalloc(sizeof(double) * L), *d = (double *)xalloc(sizeof(double) * L),
+               *x = (double *)xalloc(sizeof(double) * L);
+        const double *Mi = Mv + (size_t)i * Li, *dp = dpi + (size_t)i * L;
+        for (int j = 0; j < Li; j++) {
+            me[j] = 0.0;
+            mi[j] = 0.0;
+            if (j == 0 || j == L || Mi[j] == 0.0) continue;
+            const int donor = Mi[j] > 0.0 ? j - 1 : j;
+            const double cour = fabs(Mi[j]) * dt / dp[donor];
+            const double f = cour <= cmax ? 1.0 : cmax / cour;
+            me[j] = f * Mi[j];
+            mi[j] = Mi[j] - me[j];
+        }
+        for (int k = 0; k < L; k++) dpn[k] = dp[k] - dt * (Mi[k + 1] - Mi[k]);
+        for (int t = 0; t < T; t++) {
+            double *qt = q + ((size_t)t * nC + i) * L;
+            for (int k = 0; k < L; k++) {
+                const double qtop = (k > 0) ? (Mi[k] > 0.0 ? qt[k - 1] : qt[k]) : 0.0;
+                const double qbot = (k < L - 1) ? (Mi[k + 1] > 0.0 ? qt[k] : qt[k + 1]) : 0.0;
+                d[k] = dp[k] * qt[k] - dt * (me[k + 1] * qbot - me[k] * qtop);
+                a[k] = -dt * fmax(mi[k], 0.0);
+                b[k] = dpn[k] + dt * (fmax(mi[k + 1], 0.0) - fmin(mi[k], 0.0));
+                c[k] = dt * fmin(mi[k + 1], 0.0);
+            }
+            orc_thomas(L, a, b, c, d, x);
+            memcpy(qt, x, sizeof(double) * L);
+        }
+        free(me); free(mi); free(dpn); free(a); free(b); free(c); free(d); free(x);
+    }
 }
 
 /* ------------------------------------------------------------------------
