@@ -149,25 +149,45 @@ int grist_mesh_counts(grist_mesh mesh, int32_t *n_cells, int32_t *n_edges, int32
  *   mass_flux  device, in, [n_edges][ld] double: time-mean mass flux
  *              dpi*V_n at edges (Sec. 2.3: accumulated from the continuity
  *              equation, used in double).
+ *   vmass_flux device, in, [n_cells][ld_int] double, or NULL: time-mean
+ *              vertical mass flux M at the interfaces (M > 0 downward, 0 at
+ *              the top and the surface; e.g. the dycore's
+ *              vmass_flux_accum).  When given, the horizontal step is
+ *              followed by the vertical transport delta(M q) of Eq. 10 over
+ *              the same dt (see grist_tracer_batch.vertical_courant_max).
+ *   ld_int     leading dimension of vmass_flux (>= n_levels + 1).
  * The layer mass at each RK stage follows the tracer solver's continuity
- * with the same flux, dpi^(s) = dpi - dt_s div(mass_flux). */
+ * with the same flux, dpi^(s) = dpi - dt_s div(mass_flux); the vertical
+ * step starts from dpi - dt div(mass_flux) and ends at that minus
+ * dt (M_{k+1} - M_k), the dycore's layer mass when the fluxes are its
+ * accumulated ones. */
 typedef struct {
     int32_t n_levels, n_tracers, ld;
     void *q;
     const double *dpi;
     const double *mass_flux;
+    const double *vmass_flux;
+    int32_t ld_int;
 } grist_tracer_member;
 
 /* A batch of members (uneven tracer and level counts allowed) advanced in
  * one call.  limiter: 1 = FCT on the final RK stage, 0 = none.
  * beta_upwind: upwind weight of the third-order flux (1 = third order,
- * 0 = fourth-order centred).  prec: GRIST_FP64 or a mixed policy. */
+ * 0 = fourth-order centred).  prec: GRIST_FP64 or a mixed policy.
+ * vertical_courant_max: the vertical transport (Sec. 2.1 "adaptively
+ * implicit") moves the share of M up to this Courant number |M| dt / dpi
+ * of the donor layer explicitly (first-order upwind) and the rest by
+ * backward-Euler upwind (one tridiagonal system per column): constants stay
+ * constant, column mass is conserved, no new extrema for values <= 1.
+ * 0 = fully implicit; negative or NaN: GRIST_EINVAL (only read when a
+ * member has a vertical mass flux; the Python binding's default is 1). */
 typedef struct {
     int32_t n_members;
     const grist_tracer_member *members; /* host array of n_members */
     grist_precision prec;
     int32_t limiter;
     double beta_upwind;
+    double vertical_courant_max;        /* >= 0 (see below) */
 } grist_tracer_batch;
 
 /* Advance every member by dt with Wicker-Skamarock RK3 (dt/3, dt/2, dt),
@@ -278,7 +298,12 @@ typedef struct {
  *               p_nh_valid to 0 whenever dpi_theta or phi change outside
  *               the step.
  *   accum_scale weight of this step's flux in mass_flux_accum and
- *               accum_weight; 0 is read as 1. */
+ *               accum_weight; 0 is read as 1.
+ *   vmass_flux_accum [nC][ld_int] double or NULL: accum_scale times the
+ *               final stage's vertical mass flux M at the interfaces (the
+ *               delta(M q) flux of Eq. 10; M > 0 carries mass downward, 0 at
+ *               the top and the surface) is added to it - the flux of the
+ *               tracers' vertical transport. */
 typedef struct {
     void *u;
     double *ps;
@@ -291,6 +316,7 @@ typedef struct {
     double *p_nh;
     int32_t p_nh_valid;
     double accum_scale;
+    double *vmass_flux_accum;
 } grist_dycore_state;
 
 /* Hydrostatic step: WS-RK3, Mesinger forward-backward inside each stage

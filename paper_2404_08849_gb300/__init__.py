@@ -147,7 +147,7 @@ class Mesh:
 
     # ---- steps ---------------------------------------------------------------
     @staticmethod
-    def _batch(members, prec, limiter, beta):
+    def _batch(members, prec, limiter, beta, cmax=1.0):
         arr = (_lib.TracerMember * max(1, len(members)))()
         for i, mb in enumerate(members):
             q = mb["q"]
@@ -157,20 +157,26 @@ class Mesh:
             arr[i].q = _ptr(q)
             arr[i].dpi = _ptr(mb["dpi"])
             arr[i].mass_flux = _ptr(mb["mass_flux"])
+            vm = mb.get("vmass_flux")
+            arr[i].vmass_flux = _ptr(vm)
+            arr[i].ld_int = int(vm.shape[-1]) if vm is not None else 0
         b = _lib.TracerBatch()
         b.n_members = len(members)
         b.members = arr
         b.prec = _prec(prec)
         b.limiter = 1 if limiter else 0
         b.beta_upwind = float(beta)
+        b.vertical_courant_max = float(cmax)
         return b, arr
 
-    def tracer_step(self, members, dt, prec="fp64", limiter=True, beta=1.0, stream=None):
+    def tracer_step(self, members, dt, prec="fp64", limiter=True, beta=1.0, vertical_courant_max=1.0,
+                    stream=None):
         """members: list of dicts with torch CUDA tensors q [T][nC][ld]
         (float64 for fp64, float32 for the mixed policies), dpi [nC][ld]
-        and mass_flux [nE][ld] (float64), and int n_levels."""
+        and mass_flux [nE][ld] (float64), int n_levels, and optionally
+        vmass_flux [nC][ld_int] (float64) for the vertical transport."""
         lib = _lib.load()
-        b, keep = self._batch(members, prec, limiter, beta)
+        b, keep = self._batch(members, prec, limiter, beta, vertical_courant_max)
         _lib.check("grist_tracer_step", lib.grist_tracer_step(self.handle, ctypes.byref(b), float(dt),
                                                               _stream_handle(stream)))
 
@@ -232,6 +238,7 @@ class Mesh:
         s.p_nh = _ptr(state.get("p_nh"))
         s.p_nh_valid = 1 if state.get("p_nh_valid") else 0
         s.accum_scale = float(state.get("accum_scale", 1.0))
+        s.vmass_flux_accum = _ptr(state.get("vmass_flux_accum"))
         _lib.check(fn, getattr(lib, fn)(self.handle, ctypes.byref(s), ctypes.byref(params.c), _prec(prec),
                                         float(dt), _stream_handle(stream)))
         if state.get("p_nh") is not None:

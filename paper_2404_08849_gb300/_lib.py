@@ -36,12 +36,13 @@ class MeshDesc(ctypes.Structure):
 
 
 class TracerMember(ctypes.Structure):
-    _fields_ = [("n_levels", _I), ("n_tracers", _I), ("ld", _I), ("q", _V), ("dpi", _V), ("mass_flux", _V)]
+    _fields_ = [("n_levels", _I), ("n_tracers", _I), ("ld", _I), ("q", _V), ("dpi", _V), ("mass_flux", _V),
+                ("vmass_flux", _V), ("ld_int", _I)]
 
 
 class TracerBatch(ctypes.Structure):
     _fields_ = [("n_members", _I), ("members", _P(TracerMember)), ("prec", ctypes.c_int), ("limiter", _I),
-                ("beta_upwind", _D)]
+                ("beta_upwind", _D), ("vertical_courant_max", _D)]
 
 
 class TracerTuning(ctypes.Structure):
@@ -56,7 +57,8 @@ class DycoreParams(ctypes.Structure):
 
 class DycoreState(ctypes.Structure):
     _fields_ = [("u", _V), ("ps", _V), ("dpi_theta", _V), ("w", _V), ("phi", _V), ("mass_flux_accum", _V),
-                ("accum_weight", _V), ("dpi_start", _V), ("p_nh", _V), ("p_nh_valid", _I), ("accum_scale", _D)]
+                ("accum_weight", _V), ("dpi_start", _V), ("p_nh", _V), ("p_nh_valid", _I), ("accum_scale", _D),
+                ("vmass_flux_accum", _V)]
 
 
 EXPORTS = {

@@ -231,7 +231,8 @@ __global__ void k_mass_col(DevMesh m, DyPar d, const typename P::TM *__restrict_
                            const double *__restrict__ ps_n, double *__restrict__ ps_out,
                            const double *__restrict__ th_s, typename P::TA *__restrict__ theta,
                            double *__restrict__ Mv, double dts, double *__restrict__ dpi_out,
-                           double *__restrict__ rdps_out, double *__restrict__ rth_out) {
+                           double *__restrict__ rdps_out, double *__restrict__ rth_out,
+                           double *__restrict__ Macc, double fscale) {
     using TM = typename P::TM;
     using TA = typename P::TA;
     const int i0 = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32;
@@ -285,7 +286,11 @@ __global__ void k_mass_col(DevMesh m, DyPar d, const typename P::TM *__restrict_
                     const double t = __shfl_up_sync(0xffffffffu, v, o);
                     if (lane >= o) v += t;
                 }
-                if (k < d.L - 1) Mv[(size_t)i * d.ldi + k + 1] = -ldg(d.B + k + 1) * pst - (run + v);
+                if (k < d.L - 1) {
+                    const double mk = -ldg(d.B + k + 1) * pst - (run + v);
+                    Mv[(size_t)i * d.ldi + k + 1] = mk;
+                    if (Macc) Macc[(size_t)i * d.ldi + k + 1] += fscale * mk;
+                }
                 run += __shfl_sync(0xffffffffu, v, 31);
             } else {
                 F2 v{cv<float>(s), 0.f};
@@ -294,8 +299,11 @@ __global__ void k_mass_col(DevMesh m, DyPar d, const typename P::TM *__restrict_
                     const F2 t = f2_shfl_up(v, o);
                     if (lane >= o) v = f2_add(v, t);
                 }
-                if (k < d.L - 1)
-                    Mv[(size_t)i * d.ldi + k + 1] = -ldg(d.B + k + 1) * pst - (run + (f2d(v.hi) + f2d(v.lo)));
+                if (k < d.L - 1) {
+                    const double mk = -ldg(d.B + k + 1) * pst - (run + (f2d(v.hi) + f2d(v.lo)));
+                    Mv[(size_t)i * d.ldi + k + 1] = mk;
+                    if (Macc) Macc[(size_t)i * d.ldi + k + 1] += fscale * mk;
+                }
                 const F2 last{__shfl_sync(0xffffffffu, v.hi, 31), __shfl_sync(0xffffffffu, v.lo, 31)};
                 run += f2d(last.hi) + f2d(last.lo);
             }
@@ -952,7 +960,7 @@ int dycore_step(grist_mesh_s *h, grist_dycore_state *S, const grist_dycore_param
             m, d, ps_in, u_in, F, s3 == 2 ? S->mass_flux_accum : nullptr, ascale, rsum, fcol));
         GRIST_LAUNCH(h, PN("k_mass_col"), st, k_mass_col<P><<<gC32, kBlock, 0, st>>>(
             m, d, F, fcol, ps_in, psN, ps_outs[s3], th_in, theta, Mv, h3, s3 == 0 ? S->dpi_start : nullptr, rdps,
-            (NH && s3 == 0) ? rthn : nullptr));
+            (NH && s3 == 0) ? rthn : nullptr, s3 == 2 ? S->vmass_flux_accum : nullptr, ascale));
         GRIST_LAUNCH(h, PN("k_theta_flux"), st, k_theta_flux<P><<<gE, kBlock, 0, st>>>(m, d, DL, F, theta, Fth));
         GRIST_LAUNCH(h, PN("k_theta_update"), st, k_theta_update<P><<<gC, kBlock, 0, st>>>(
             m, d, DL, Fth, theta, Mv, S->dpi_theta, th_outs[s3], h3));

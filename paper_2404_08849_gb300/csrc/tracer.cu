@@ -38,6 +38,8 @@ struct MemberDev {
     void *FH;               // scratch edge fluxes [T][nE][ld]
     void *Rp, *Rm;          // scratch FCT ratios [T][nC][ld]
     int L, T, ld, pad;
+    const double *Mv;       // time-mean vertical mass flux [nC][ldi] or null (no vertical step)
+    int ldi;
     LevelDiv DL;            // division by L
     unsigned long long qs, fs;  // nC*ld, nE*ld
 };
@@ -100,6 +102,7 @@ void tracer_ctx_free(TracerCtx *c) {
 namespace {
 
 constexpr long long kBarrierSpinLimit = 20000000;  // x ~64 ns sleep: about a second
+constexpr int kVertMaxL = 128;   // levels supported by the vertical transport
 // Largest block of the work-list kernels (their register use, at most 128
 // per thread, lets every block up to this size launch).
 constexpr int kTracerMaxBlock = 512;
@@ -115,6 +118,7 @@ struct Batch {
     int fct;
     int beta1;
     double beta;
+    double cmax;    // vertical transport: largest explicit Courant number
 };
 
 // Cached segment lookup: returns the segment of flat index n, reusing seg
@@ -530,6 +534,148 @@ __global__ void __launch_bounds__(256) k_tr_tile_stage(DevMesh m, TileMesh tm, B
     if (bad) atomicOr(status, GRIST_FLAG_NONFINITE);
 }
 
+// ---------------------------------------------------------------------------
+// Vertical transport, the delta(M q) term of Eq. 10, by an adaptively
+// implicit upwind scheme (Sec. 2.1; the reading): at interior interface j
+// (between layers j-1 above and j below, M_j > 0 carrying mass downward)
+// the donor layer is j-1 if M_j > 0, else j, with Courant number
+// c_j = |M_j| dt / dpi*_donor; the share Me_j = min(1, cmax / c_j) M_j moves
+// explicitly (first-order upwind from q at the start), the rest
+// Mi_j = M_j - Me_j by backward-Euler upwind, so per column
+//   dpi+_k q+_k + dt (Fi_{k+1} - Fi_k) = dpi*_k q_k - dt (Fe_{k+1} - Fe_k),
+//   dpi*_k = dpi_k - dt div(F)_k (the horizontal step's end),
+//   dpi+_k = dpi*_k - dt (M_{k+1} - M_k),
+// a tridiagonal M-matrix system solved by the Thomas algorithm.  One thread
+// per column, blocks of one warp (32 columns); the column data moves
+// through shared memory in 4-level chunks (whole 32-byte sectors for
+// doubles); the flux split is formed once per column and shared by the
+// member's tracers.  Arithmetic in the tracer compute type.
+constexpr int kVertKC = 4;
+constexpr int kVertRow = 33;
+
+__device__ __forceinline__ double vinv(double x) { return rcp(x); }   // correctly rounded, as 1.0 / x
+__device__ __forceinline__ float vinv(float x) { return 1.0f / x; }
+
+template <typename T>
+__device__ __forceinline__ void vstage_in(const T *X, size_t S, int col0, int ncol, int k0, int nk, T *sm) {
+    const int lane = threadIdx.x & 31, kk = lane % kVertKC;
+#pragma unroll
+    for (int it = 0; it < kVertKC; it++) {
+        const int col = it * (32 / kVertKC) + lane / kVertKC;
+        T v = (T)0;
+        if (col < ncol && kk < nk) v = X[(size_t)(col0 + col) * S + k0 + kk];
+        sm[kk * kVertRow + col] = v;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void vstage_out(T *X, size_t S, int col0, int ncol, int k0, int nk, const T *sm) {
+    const int lane = threadIdx.x & 31, kk = lane % kVertKC;
+#pragma unroll
+    for (int it = 0; it < kVertKC; it++) {
+        const int col = it * (32 / kVertKC) + lane / kVertKC;
+        if (col < ncol && kk < nk) X[(size_t)(col0 + col) * S + k0 + kk] = sm[kk * kVertRow + col];
+    }
+}
+
+template <typename TQ, typename TC>
+__global__ void __launch_bounds__(32) k_tr_vertical(DevMesh m, MemberDev mb, double dt, double cmax,
+                                                    uint32_t *status) {
+    __shared__ double sD[3][kVertKC * kVertRow];   // dpi, div F, M at the interface below
+    __shared__ TQ sQ[(kVertKC + 1) * kVertRow];    // q of a chunk and the level after it
+    const int lane = threadIdx.x;
+    const int col0 = blockIdx.x * 32;
+    const int ncol = min(32, m.nC - col0);
+    const int i = col0 + lane;
+    const bool act = lane < ncol;
+    const int L = mb.L, ld = mb.ld, ldi = mb.ldi;
+    const TC dtc = cv<TC>(dt), cm = cv<TC>(cmax);
+    TC me[kVertMaxL + 1], mi[kVertMaxL + 1], dps[kVertMaxL], cp[kVertMaxL], dd[kVertMaxL];
+    // pass 1: the flux split at every interface and the start layer mass
+    me[0] = mi[0] = (TC)0;
+    {
+        TC dps_prev = (TC)0, m_top = (TC)0;
+        for (int k0 = 0; k0 < L; k0 += kVertKC) {
+            const int nk = min(kVertKC, L - k0);
+            __syncwarp();
+            vstage_in(mb.dpi, (size_t)ld, col0, ncol, k0, nk, sD[0]);
+            vstage_in(mb.divF, (size_t)ld, col0, ncol, k0, nk, sD[1]);
+            vstage_in(mb.Mv, (size_t)ldi, col0, ncol, k0 + 1, nk, sD[2]);
+            __syncwarp();
+            if (act) {
+                for (int kk = 0; kk < nk; kk++) {
+                    const int k = k0 + kk, o = kk * kVertRow + lane;
+                    const TC ds = cv<TC>(sD[0][o] - dt * sD[1][o]);
+                    dps[k] = ds;
+                    // interface k (top of layer k): donor k-1 when M_k > 0, else k
+                    if (k > 0 && m_top != (TC)0) {
+                        const TC cour = fabs(m_top) * dtc / (m_top > (TC)0 ? dps_prev : ds);
+                        const TC f = cour <= cm ? (TC)1 : cm / cour;
+                        me[k] = f * m_top;
+                        mi[k] = m_top - me[k];
+                    } else if (k > 0) {
+                        me[k] = mi[k] = (TC)0;
+                    }
+                    dps_prev = ds;
+                    m_top = (k + 1 < L) ? cv<TC>(sD[2][o]) : (TC)0;   // M at the bottom of layer k
+                }
+            }
+        }
+        me[L] = mi[L] = (TC)0;
+        (void)m_top;
+    }
+    // pass 2, per tracer: explicit share from q, then the implicit system
+    bool bad = false;
+    for (int t = 0; t < mb.T; t++) {
+        TQ *qt = (TQ *)mb.q + (size_t)t * mb.qs;
+        TC q_prev = (TC)0;
+        for (int k0 = 0; k0 < L; k0 += kVertKC) {
+            const int nk = min(kVertKC, L - k0);
+            __syncwarp();
+            vstage_in(qt, (size_t)ld, col0, ncol, k0, nk, sQ);
+            if (act) sQ[kVertKC * kVertRow + lane] = (k0 + nk < L) ? qt[(size_t)i * ld + k0 + nk] : (TQ)0;
+            __syncwarp();
+            if (act) {
+                for (int kk = 0; kk < nk; kk++) {
+                    const int k = k0 + kk, o = kk * kVertRow + lane;
+                    const TC qk = (TC)sQ[o];
+                    const TC qn = (TC)(kk + 1 < nk ? sQ[o + kVertRow] : sQ[kVertKC * kVertRow + lane]);
+                    // donor values at the top (k) and bottom (k + 1) interfaces
+                    const TC Mt = me[k] + mi[k], Mb = me[k + 1] + mi[k + 1];
+                    const TC q_top = Mt > (TC)0 ? q_prev : qk;
+                    const TC q_bot = Mb > (TC)0 ? qk : qn;
+                    const TC dpn = dps[k] - dtc * (Mb - Mt);
+                    const TC rhs = dps[k] * qk - dtc * (me[k + 1] * q_bot - me[k] * q_top);
+                    const TC a = -dtc * fmax_((TC)0, mi[k]);
+                    const TC b = dpn + dtc * (fmax_((TC)0, mi[k + 1]) - fmin_((TC)0, mi[k]));
+                    const TC c = dtc * fmin_((TC)0, mi[k + 1]);
+                    const TC rden = vinv(k == 0 ? b : b - a * cp[k - 1]);
+                    cp[k] = c * rden;
+                    dd[k] = (k == 0 ? rhs : rhs - a * dd[k - 1]) * rden;
+                    q_prev = qk;
+                }
+            }
+        }
+        // back substitution, bottom to top, written chunk by chunk
+        TC qb = (TC)0;
+        for (int k0 = ((L - 1) / kVertKC) * kVertKC; k0 >= 0; k0 -= kVertKC) {
+            const int nk = min(kVertKC, L - k0);
+            __syncwarp();
+            if (act) {
+                for (int kk = nk - 1; kk >= 0; kk--) {
+                    const int k = k0 + kk;
+                    qb = (k == L - 1) ? dd[k] : dd[k] - cp[k] * qb;
+                    bad |= !isfinite(qb);
+                    sQ[kk * kVertRow + lane] = (TQ)qb;
+                }
+            }
+            __syncwarp();
+            vstage_out(qt, (size_t)ld, col0, ncol, k0, nk, sQ);
+        }
+    }
+    if (bad) atomicOr(status, GRIST_FLAG_NONFINITE);
+}
+
 // Bounded wait until *gen differs from g: at most `limit` polls (~64 ns
 // apart); on giving up (or when another block already gave up) raises
 // GRIST_FLAG_TIMEOUT and returns false.
@@ -638,6 +784,8 @@ int plan_batch(const DevMesh &m, const grist_tracer_batch *b, int tpt, HostPlan 
         d.L = u.n_levels;
         d.T = u.n_tracers;
         d.ld = u.ld;
+        d.Mv = u.vmass_flux;
+        d.ldi = u.ld_int;
         d.DL = make_div((uint32_t)u.n_levels);
         d.qs = (unsigned long long)m.nC * u.ld;
         d.fs = (unsigned long long)m.nE * u.ld;
@@ -740,6 +888,7 @@ int upload_plan(grist_mesh_s *h, TracerCtx *c, HostPlan &P, const grist_tracer_b
     B.fct = b->limiter ? 1 : 0;
     B.beta1 = b->beta_upwind == 1.0 ? 1 : 0;
     B.beta = b->beta_upwind;
+    B.cmax = b->vertical_courant_max;
     return GRIST_OK;
 }
 
@@ -751,9 +900,9 @@ int sm_count(int dev) {
 
 int build_tiles(grist_mesh_s *h, TracerCtx *c);
 
-// Enqueue the step's kernels (no host synchronisation: capturable).
+// Enqueue the horizontal phases (no host synchronisation: capturable).
 template <typename TQ, typename TC>
-int enqueue_step(grist_mesh_s *h, TracerCtx *c, const Batch &B, cudaStream_t st) {
+int enqueue_horizontal(grist_mesh_s *h, TracerCtx *c, const Batch &B, cudaStream_t st) {
     const DevMesh &m = dev_mesh(h);
     uint32_t *status = status_word(h);
     const int block = c->tune.block;
@@ -837,6 +986,24 @@ int enqueue_step(grist_mesh_s *h, TracerCtx *c, const Batch &B, cudaStream_t st)
             GRIST_PHASE_CASE(P_COPY)
 #undef GRIST_PHASE_CASE
         }
+    }
+    return cudaGetLastError() == cudaSuccess ? GRIST_OK : GRIST_ECUDA;
+}
+
+// The step: the horizontal phases, then the vertical transport of every
+// member that has a vertical mass flux (one launch per such member; the
+// members' resolved descriptors are the host mirror of the device table).
+template <typename TQ, typename TC>
+int enqueue_step(grist_mesh_s *h, TracerCtx *c, const Batch &B, cudaStream_t st) {
+    int rc = enqueue_horizontal<TQ, TC>(h, c, B, st);
+    if (rc != GRIST_OK) return rc;
+    const DevMesh &m = dev_mesh(h);
+    const MemberDev *hm = reinterpret_cast<const MemberDev *>(c->htab.data());
+    for (int j = 0; j < B.nm; j++) {
+        if (!hm[j].Mv) continue;
+        GRIST_LAUNCH(h, sizeof(TC) == 4 ? "k_tr_vertical/mix" : "k_tr_vertical/fp64", st,
+                     k_tr_vertical<TQ, TC><<<grid_for(m.nC, 32), 32, 0, st>>>(m, hm[j], B.dt, B.cmax,
+                                                                              status_word(h)));
     }
     return cudaGetLastError() == cudaSuccess ? GRIST_OK : GRIST_ECUDA;
 }
@@ -944,6 +1111,7 @@ int tracer_step_t(grist_mesh_s *h, const grist_tracer_batch *b, double dt, cudaS
     unsigned long long u;
     std::memcpy(&u, &b->beta_upwind, 8); sig.push_back(u);
     std::memcpy(&u, &dt, 8); sig.push_back(u);
+    std::memcpy(&u, &b->vertical_courant_max, 8); sig.push_back(u);
     sig.push_back((unsigned long long)(uintptr_t)st);
     sig.push_back(((unsigned long long)c->tune.block << 32) | (unsigned)c->tune.tracers_per_thread);
     sig.push_back((unsigned long long)c->tune.persistent);
@@ -954,6 +1122,8 @@ int tracer_step_t(grist_mesh_s *h, const grist_tracer_batch *b, double dt, cudaS
         sig.push_back((unsigned long long)(uintptr_t)mm.mass_flux);
         sig.push_back(((unsigned long long)mm.n_levels << 40) | ((unsigned long long)mm.n_tracers << 20) |
                       (unsigned long long)mm.ld);
+        sig.push_back((unsigned long long)(uintptr_t)mm.vmass_flux);
+        sig.push_back((unsigned long long)mm.ld_int);
     }
     sig.push_back((unsigned long long)(uintptr_t)c->dtab);
     if (c->exec && sig == c->sig) {
@@ -999,7 +1169,10 @@ int validate(const grist_tracer_batch *b, double dt) {
         const grist_tracer_member &mb = b->members[i];
         if (mb.n_levels < 0 || mb.n_tracers < 0 || mb.n_levels > GRIST_MAXL || mb.ld < mb.n_levels) return GRIST_EINVAL;
         if (mb.n_levels > 0 && mb.n_tracers > 0 && (!mb.q || !mb.dpi || !mb.mass_flux)) return GRIST_EINVAL;
+        if (mb.vmass_flux && mb.ld_int < mb.n_levels + 1) return GRIST_EINVAL;
+        if (mb.vmass_flux && mb.n_levels > kVertMaxL) return GRIST_EUNSUPPORTED;
     }
+    if (!(b->vertical_courant_max >= 0.0)) return GRIST_EINVAL;   // NaN and negatives; +inf: explicit only
     return GRIST_OK;
 }
 
