@@ -6,8 +6,9 @@ four tracers on the level-9 icosahedral mesh (2,621,442 cells, 7,864,320
 edges, 5,242,880 vertices), 60 levels on a stretched 30 km-top grid, dt =
 30 s, seeded jet + perturbation + warm bubble, tracers = bell / slotted
 cylinder / 2 Gaussians.  One step = one NH dycore step (which accumulates the
-mass flux and hands dpi to the tracer solver) + one tracer step (RK3 + FCT)
-of the 4 tracers with that flux.  The FP64 GPU path runs the same step on the
+horizontal and vertical mass fluxes and hands dpi to the tracer solver) + one
+tracer step of the 4 tracers with those fluxes (horizontal RK3 + FCT, then
+the vertical transport).  The FP64 GPU path runs the same step on the
 same inputs side by side.
 
 Metric: cell-level-steps/s = n_cells * n_levels * steps / time.
@@ -37,7 +38,8 @@ UNIT = "cell-level-steps/s"
 WORKLOADS = {
     # name: mesh level, levels, non-hydrostatic, tracers, dt
     "g9nh": dict(level=9, L=60, nh=True, T=4, dt=30.0,
-                 desc="NH dycore + 4 tracers (FCT), L9 mesh 2621442 cells, 60 levels, dt 30 s"),
+                 desc="NH dycore + 4 tracers (3rd-order + FCT horizontal, adaptively implicit vertical), "
+                      "L9 mesh 2621442 cells, 60 levels, dt 30 s"),
     "g8nh": dict(level=8, L=60, nh=True, T=0, dt=60.0,
                  desc="NH dycore, L8 mesh 655362 cells, 60 levels, dt 60 s"),
     "g6hdc": dict(level=6, L=30, nh=False, T=0, dt=300.0,
@@ -77,6 +79,7 @@ def algorithmic_bytes(name, nC, nE, nV, L, T, prec):
         "k_tr_ratios": 2 * T * CL * sQ + T * EL * sC + EL * 8 + 2 * CL * 8 + 2 * T * CL * sC,
         "k_tr_final": T * CL * sQ + T * EL * sC + EL * 8 + 2 * CL * 8 + 2 * T * CL * sC + T * CL * sQ,
         "k_tr_copy": 2 * T * CL * sQ,
+        "k_tr_vertical": 2 * CL * 8 + CI * 8 + 2 * T * CL * sQ,
     }
     return table.get(base)
 
@@ -222,6 +225,7 @@ def make_state(torch, host, prec, device, nE, nC, L, T, nh):
     if T:
         s["q"] = torch.from_numpy(host["q"]).to(device=device, dtype=fdt)
         s["mass_flux_accum"] = torch.zeros((nE, L), dtype=torch.float64, device=device)
+        s["vmass_flux_accum"] = torch.zeros((nC, L + 1), dtype=torch.float64, device=device)
         s["dpi_start"] = torch.zeros((nC, L), dtype=torch.float64, device=device)
     return s
 
@@ -231,13 +235,15 @@ def step(mesh, s, P, wl, prec):
     handing dpi^n to the tracer solver) then the tracers."""
     if "mass_flux_accum" in s:
         s["mass_flux_accum"].zero_()
+        s["vmass_flux_accum"].zero_()
     if wl["nh"]:
         mesh.dycore_step_nh(s, P, wl["dt"], prec=prec)
     else:
         mesh.dycore_step_hydro(s, P, wl["dt"], prec=prec)
     if wl["T"]:
         mesh.tracer_step([{"q": s["q"], "dpi": s["dpi_start"], "mass_flux": s["mass_flux_accum"],
-                           "n_levels": wl["L"]}], wl["dt"], prec=prec, limiter=True)
+                           "vmass_flux": s["vmass_flux_accum"], "n_levels": wl["L"]}], wl["dt"], prec=prec,
+                         limiter=True)
 
 
 def timed(torch, fn, K, dist=None):
@@ -288,8 +294,8 @@ def gpu_arm(args, wl):
                 # the tracer launch configuration from the library's autotuner,
                 # on this step's own tracer inputs (restored after timing)
                 tunings[prec] = mesh.autotune_tracer(
-                    [{"q": s["q"], "dpi": s["dpi_start"], "mass_flux": s["mass_flux_accum"], "n_levels": L}],
-                    wl["dt"], prec=prec, steps=2)[0]
+                    [{"q": s["q"], "dpi": s["dpi_start"], "mass_flux": s["mass_flux_accum"],
+                      "vmass_flux": s["vmass_flux_accum"], "n_levels": L}], wl["dt"], prec=prec, steps=2)[0]
         torch.cuda.synchronize()
         cs = ClockSampler(device) if sample_clocks else None
         if cs:
@@ -403,14 +409,16 @@ def gpu_arm(args, wl):
 
         def window():
             s["mass_flux_accum"].zero_()
+            s["vmass_flux_accum"].zero_()
             for i in range(n):
                 s["dpi_start"] = dpi0 if i == 0 else None
                 if wl["nh"]:
                     mesh.dycore_step_nh(s, P, wl["dt"], prec=args.prec)
                 else:
                     mesh.dycore_step_hydro(s, P, wl["dt"], prec=args.prec)
-            mesh.tracer_step([{"q": s["q"], "dpi": dpi0, "mass_flux": s["mass_flux_accum"], "n_levels": L}],
-                             n * wl["dt"], prec=args.prec, limiter=True)
+            mesh.tracer_step([{"q": s["q"], "dpi": dpi0, "mass_flux": s["mass_flux_accum"],
+                               "vmass_flux": s["vmass_flux_accum"], "n_levels": L}], n * wl["dt"], prec=args.prec,
+                             limiter=True)
         for _ in range(max(1, W // n)):
             window()
         secs_w = reduce_max(timed(torch, window, K, dist), dist, device)
@@ -513,14 +521,16 @@ def oracle_step_rate(wl, level, steps=1):
     t0 = time.perf_counter()
     for _ in range(steps):
         fa = np.zeros((m["n_edges"], L))
-        dpi = st["dpi"] if s is st else None
+        va = np.zeros((m["n_cells"], L + 1))
         if wl["nh"]:
-            s2 = O.dycore_step_nh(M, P, s, wl["dt"], flux_accum=fa)
+            s2 = O.dycore_step_nh(M, P, s, wl["dt"], flux_accum=fa, vflux_accum=va)
         else:
-            s2 = O.dycore_step_hydro(M, P, s, wl["dt"], flux_accum=fa)
+            s2 = O.dycore_step_hydro(M, P, s, wl["dt"], flux_accum=fa, vflux_accum=va)
         if T:
             pint = st["pi_top"] + st["b_int"][None, :] * (s["ps"][:, None] - st["pi_top"])
-            q = O.tracer_step(M, q, np.diff(pint, axis=1), fa, wl["dt"])
+            dpi = np.diff(pint, axis=1)
+            q = O.tracer_step(M, q, dpi, fa, wl["dt"])
+            q = O.tracer_vertical_step(q, dpi - wl["dt"] * O.divergence(M, fa), va, wl["dt"], 1.0)
         s = dict(s, **{k: s2[k] for k in s2 if k != "accum_weight"})
     secs = time.perf_counter() - t0
     sample = "%d step(s) of the same %s physics on the level-%d mesh (%d cells x %d levels)" % (
