@@ -97,7 +97,7 @@ FP64_WORK_MIX = {
     "k_momentum": ("e", 19.88, 36.6),
     "k_nh_explicit": ("i", 28.20, 73.1),
     "k_ke": ("c", 18.00, 18.3),
-    "k_mass_col": ("c", 12.41, 41.0),
+    "k_mass_col": ("c", 12.81, 45.9),
     "k_vort": ("v", 3.00, 9.2),
     "k_eos": ("c", 93.0, 21.1),
     "k_tr_div": ("c", 12.00, 31.6),
