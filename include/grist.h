@@ -31,6 +31,11 @@
  *     errors.  Numerical faults are reported by grist_last_step_status
  *     after the stream has been synchronised.
  *   - Calls on one mesh handle must not overlap from several host threads.
+ *     The dycore steps and the tracer steps keep separate device scratch in
+ *     the handle, so a tracer step may run on one stream while a dycore step
+ *     runs on another (e.g. the tracers of step n beside the dycore of step
+ *     n + 1, with their fluxes in separate buffers); two dycore steps, or
+ *     two tracer steps, of one handle must not overlap.
  */
 #ifndef GRIST_H
 #define GRIST_H

@@ -284,6 +284,11 @@ struct HostTables {
     std::vector<int32_t> d2i;   // [nE][2][7]
 };
 const HostTables &host_tables(grist_mesh_s *m);
+// The dycore's vertical-grid table (B, dB, 1/dB, ...) as last uploaded into
+// its scratch, and the device address it went to: a step re-uploads it (and
+// waits for the copy) only when either changed.
+std::vector<double> &vg_cache(grist_mesh_s *m);
+const void *&vg_ptr(grist_mesh_s *m);
 
 // Tracer-step context (tuning, device tables, graph cache) kept in the
 // handle; defined in tracer.cu.

@@ -893,8 +893,13 @@ int dycore_step(grist_mesh_s *h, grist_dycore_state *S, const grist_dycore_param
     float *hdBf = reinterpret_cast<float *>(hrdBi + L + 1);
     for (int k = 0; k < L; k++) hdBf[k] = (float)hdB[k];
     double *dvg = (double *)(s + o_vg);
-    GRIST_CUDA_TRY(cudaMemcpyAsync(dvg, vg.data(), vg.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-    GRIST_CUDA_TRY(cudaStreamSynchronize(st));  // vg is a host temporary
+    if (vg_ptr(h) != dvg || vg_cache(h) != vg) {
+        // ordered after this stream's earlier steps, which read the old table
+        GRIST_CUDA_TRY(cudaMemcpyAsync(dvg, vg.data(), vg.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+        GRIST_CUDA_TRY(cudaStreamSynchronize(st));  // vg is a host temporary
+        vg_cache(h) = vg;
+        vg_ptr(h) = dvg;
+    }
 
     DyPar d;
     d.L = L; d.ld = ld; d.ldi = ldi;

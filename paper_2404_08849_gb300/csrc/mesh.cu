@@ -25,6 +25,9 @@ struct grist_mesh_s {
     uint32_t *status = nullptr;
     TracerCtx *tctx = nullptr;
     HostTables ht;
+    // the dycore's vertical-grid table as last uploaded, and where
+    std::vector<double> vg_cache;
+    const void *vg_ptr = nullptr;
     // profiling
     bool prof_on = false;
     std::vector<cudaEvent_t> ev;            // pool, pairs (2j, 2j+1)
@@ -41,6 +44,8 @@ uint32_t *status_word(grist_mesh_s *m) { return m->status; }
 bool profiling(grist_mesh_s *m) { return m->prof_on; }
 TracerCtx *&tracer_ctx(grist_mesh_s *m) { return m->tctx; }
 const HostTables &host_tables(grist_mesh_s *m) { return m->ht; }
+std::vector<double> &vg_cache(grist_mesh_s *m) { return m->vg_cache; }
+const void *&vg_ptr(grist_mesh_s *m) { return m->vg_ptr; }
 
 static const int kEventPairs = 4096;
 
@@ -88,6 +93,10 @@ void *scratch(grist_mesh_s *m, int slot, size_t bytes) {
         m->scr[slot] = nullptr;
         m->scr_bytes[slot] = 0;
     }
+    // a fresh allocation may reuse the freed address: whatever was uploaded
+    // into scratch (the dycore's vertical-grid table) is gone
+    m->vg_cache.clear();
+    m->vg_ptr = nullptr;
     void *p = nullptr;
     if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
     m->scr[slot] = p;

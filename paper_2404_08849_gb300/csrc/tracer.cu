@@ -81,18 +81,32 @@ struct TracerCtx {
     size_t dtab_bytes = 0;
     std::vector<char> htab;
     unsigned *barrier = nullptr;  // [0] arrival count, [1] generation, [2] abort, [3] self-test word
-    // graph cache
-    std::vector<unsigned long long> sig;
-    cudaGraphExec_t exec = nullptr;
-    cudaGraph_t graph = nullptr;
+    // graph cache: the last few captured steps, keyed by their signature
+    // (buffers, sizes, dt, tuning, stream) - alternating buffer sets, as in
+    // a pipelined caller, each keep their graph
+    struct GraphEntry {
+        std::vector<unsigned long long> sig;
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+    };
+    std::vector<GraphEntry> graphs;
     bool graph_failed = false;
     std::vector<unsigned long long> failed_sig;
+
+    void drop_graphs() {
+        for (auto &g : graphs) {
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+            if (g.graph) cudaGraphDestroy(g.graph);
+        }
+        graphs.clear();
+    }
 };
+
+constexpr size_t kGraphCache = 4;
 
 void tracer_ctx_free(TracerCtx *c) {
     if (!c) return;
-    if (c->exec) cudaGraphExecDestroy(c->exec);
-    if (c->graph) cudaGraphDestroy(c->graph);
+    c->drop_graphs();
     if (c->dtab) cudaFree(c->dtab);
     if (c->dtile) cudaFree(c->dtile);
     if (c->barrier) cudaFree(c->barrier);
@@ -868,8 +882,10 @@ int upload_plan(grist_mesh_s *h, TracerCtx *c, HostPlan &P, const grist_tracer_b
         c->htab.clear();
     }
     if (c->htab.size() != o || std::memcmp(c->htab.data(), ht.data(), o) != 0) {
-        GRIST_CUDA_TRY(cudaStreamSynchronize(st));
-        GRIST_CUDA_TRY(cudaMemcpy(c->dtab, ht.data(), o, cudaMemcpyHostToDevice));
+        // ordered on the step's stream after the kernels that read the old
+        // table; from pageable memory the call returns once the bytes are
+        // staged, so the host vector may go and no other stream waits
+        GRIST_CUDA_TRY(cudaMemcpyAsync(c->dtab, ht.data(), o, cudaMemcpyHostToDevice, st));
         c->htab = ht;
     }
     if (!c->barrier) {
@@ -1126,13 +1142,11 @@ int tracer_step_t(grist_mesh_s *h, const grist_tracer_batch *b, double dt, cudaS
         sig.push_back((unsigned long long)mm.ld_int);
     }
     sig.push_back((unsigned long long)(uintptr_t)c->dtab);
-    if (c->exec && sig == c->sig) {
-        GRIST_CUDA_TRY(cudaGraphLaunch(c->exec, st));
-        return GRIST_OK;
-    }
-    if (c->exec) { cudaGraphExecDestroy(c->exec); c->exec = nullptr; }
-    if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
-    c->sig.clear();
+    for (auto &ge : c->graphs)
+        if (ge.sig == sig) {
+            GRIST_CUDA_TRY(cudaGraphLaunch(ge.exec, st));
+            return GRIST_OK;
+        }
     cudaStreamCaptureStatus cs;
     GRIST_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
     if (cs != cudaStreamCaptureStatusNone || st == nullptr) return enqueue_step<TQ, TC>(h, c, B, st);
@@ -1140,21 +1154,30 @@ int tracer_step_t(grist_mesh_s *h, const grist_tracer_batch *b, double dt, cudaS
     GRIST_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     int erc = enqueue_step<TQ, TC>(h, c, B, st);
     cudaGraph_t g = nullptr;
+    cudaGraphExec_t ex = nullptr;
     cudaError_t ce = cudaStreamEndCapture(st, &g);
-    if (erc != GRIST_OK || ce != cudaSuccess || !g ||
-        cudaGraphInstantiate(&c->exec, g, 0) != cudaSuccess) {
+    if (erc != GRIST_OK || ce != cudaSuccess || !g || cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
         // this batch cannot be captured (e.g. the cooperative launch): run
         // it directly and remember not to retry the capture
         if (g) cudaGraphDestroy(g);
         cudaGetLastError();
-        c->exec = nullptr;
         c->graph_failed = true;
         c->failed_sig = sig;
         return enqueue_step<TQ, TC>(h, c, B, st);
     }
-    c->graph = g;
-    c->sig = sig;
-    GRIST_CUDA_TRY(cudaGraphLaunch(c->exec, st));
+    if (c->graphs.size() >= kGraphCache) {
+        // evict the oldest; its last replay may still be queued on a stream
+        GRIST_CUDA_TRY(cudaDeviceSynchronize());
+        cudaGraphExecDestroy(c->graphs.front().exec);
+        cudaGraphDestroy(c->graphs.front().graph);
+        c->graphs.erase(c->graphs.begin());
+    }
+    TracerCtx::GraphEntry ge;
+    ge.sig = sig;
+    ge.graph = g;
+    ge.exec = ex;
+    c->graphs.push_back(ge);
+    GRIST_CUDA_TRY(cudaGraphLaunch(ex, st));
     return GRIST_OK;
 }
 
@@ -1312,10 +1335,8 @@ extern "C" int grist_tracer_autotune(grist_mesh h, const grist_tracer_batch *b, 
     cudaEventDestroy(e1);
     cudaStreamSynchronize(st);
     for (void *q : copies) cudaFree(q);
-    // the cached graph refers to the freed copies: drop it
-    if (c->exec) { cudaGraphExecDestroy(c->exec); c->exec = nullptr; }
-    if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
-    c->sig.clear();
+    // the cached graphs may refer to the freed copies: drop them
+    c->drop_graphs();
     c->tune = bestt;
     *best = bestt;
     if (best_ms) *best_ms = bestms;
