@@ -15,7 +15,7 @@
 // rate), so divisions by layer masses are replaced by products with
 // reciprocals formed once per column / edge / vertex (1/(ps - pi_top)) and
 // once per level (1/dB), and the equation of state inside a stage is
-// evaluated relative to the stage-input state (see pow_near1).
+// evaluated relative to the stage-input state (see pow1p_near0).
 #include <cmath>
 #include <vector>
 
@@ -35,7 +35,8 @@ struct DyPar {
     const double *B;      // [L+1] interface coordinate
     const double *dB;     // [L]   layer thickness in B
     const double *rdB;    // [L]   1/dB
-    const double *rdBi;   // [L+1] 2/(dB[j-1] + dB[j]) at interior interfaces j
+    const double *hrdBi;  // [L+1] 1/(dB[j-1] + dB[j]) at interior interfaces j (half the reciprocal mean)
+    const double *dBi;    // [L+1] (dB[j-1] + dB[j])/2 at interior interfaces j
     const float *dBf;     // [L]   dB rounded to single precision
     const double *phis;   // [nC]  surface geopotential
     uint32_t emu;         // GRIST_ROW_* rows rounded to binary32 (precision search)
@@ -124,10 +125,6 @@ __device__ __forceinline__ double pow1p_near0(double x, double g, const Binom &B
     if (hm < 0x3f700000u) return horner<8>(x, B);    // 2^-8
     if (hx > 0x3f900000u || (hx == 0x3f900000u && __double2loint(x) != 0)) return pow(1.0 + x, g);
     return horner<10>(x, B);
-}
-
-__device__ __forceinline__ double pow_near1(double r, double g, const Binom &B, unsigned mask) {
-    return pow1p_near0(r - 1.0, g, B, mask);
 }
 
 Binom binomial(double g) {
@@ -623,7 +620,7 @@ __global__ void k_nh_explicit(DevMesh m, DyPar d, LevelDiv Dv, const typename P:
     TA vw = 0, vp = 0;
     double fw = 0.0;
     if (j > 0) {
-        const double rd2 = 0.5 * ldg(d.rdBi + j) * ldg(rdps_s + i);   // 1/(dpi_{j-1} + dpi_j)
+        const double rd2 = ldg(d.hrdBi + j) * ldg(rdps_s + i);   // 1/(dpi_{j-1} + dpi_j)
         const TA r = cv<TA>(Mv[(size_t)i * d.ldi + j] * rd2);
         vw = r * cv<TA>(w_s[xi + 1] - w_s[xi - 1]);
         vp = r * cv<TA>(phi_s[xi + 1] - phi_s[xi - 1]);
@@ -684,11 +681,15 @@ __device__ __forceinline__ void stage_out(double *X, size_t S, int col0, int nco
 // one warp of 32 consecutive columns), FP64.  Column data moves through
 // shared memory in kSolveKC-level chunks (whole-sector global access).
 // Equation of state relative to the t^n state (1/th_r, phi_r, p_r):
-//   p** = p_r ((th dphi_r) / (th_r dphi**))^gamma     (pow_near1)
+//   p** = p_r ((th dphi_r) / (th_r dphi**))^gamma     (pow1p_near0)
 // linearised about phi**: p_k = p**_k - C_k (w_k - w_{k+1}),
 // C_k = gamma p**_k beta dt g / dphi**_k; tridiagonal rows for interior
-// interfaces j = 1..L-1 (w = 0 at top and ground) solved by the Thomas
-// algorithm; phi = phi** + beta dt g w; the full EOS then gives
+// interfaces j = 1..L-1 (w = 0 at top and ground),
+//   -a_j C_{j-1} w_{j-1} + (1 + a_j (C_{j-1} + C_j)) w_j - a_j C_j w_{j+1}
+//       = w**_j + a_j (p**_j - p**_{j-1}) - beta dt g,
+// a_j = beta dt g / dpi_j at the interface; each row is divided by a_j
+// (off-diagonals -C, no product per row) and the system solved by the
+// Thomas algorithm; phi = phi** + beta dt g w; the full EOS then gives
 //   p = p** (dphi / dphi**)^(-gamma),  dphi = dphi** + beta dt g (w_k - w_{k+1});
 // finally alpha = dphi/dpi, layer phi and dp/dpi averaged to layers
 // (interface value 1 at top and bottom) for the momentum equation.  phi_out
@@ -711,8 +712,9 @@ __global__ void __launch_bounds__(32, kSolveMinBlocks) k_nh_solve(DevMesh m, DyP
     const int L = d.L;
     const double bg = d.beta * dts * d.g;
     const double gbg = d.gamma * bg;
-    const double rdps = act ? rcp(ps[i] - d.pi_top) : 1.0;
-    const double bgr = bg * rdps;
+    const double dps = act ? ps[i] - d.pi_top : 1.0;
+    const double rdps = rcp(dps);
+    const double psg = dps * rcp(bg);   // 1/a_j = dBi_j psg
     const unsigned amask = __ballot_sync(0xffffffffu, act);
     double cp[kNHMax], dd[kNHMax], pst[kNHMax], rdf[kNHMax];
     double ftop = act ? phst[(size_t)i * d.ldi] : 0.0, rtop = act ? phi_r[(size_t)i * d.ldi] : 0.0;
@@ -735,27 +737,30 @@ __global__ void __launch_bounds__(32, kSolveMinBlocks) k_nh_solve(DevMesh m, DyP
                 const int o = kk * kRow + lane;
                 const double fbot = sA[0 * kStage + o], rbot = sA[1 * kStage + o];
                 const double rdfj = rcp_nr(ftop - fbot);
-                const double rr = sA[2 * kStage + o] * sA[3 * kStage + o] * ((rtop - rbot) * rdfj);
-                const double pstj = DF ? scale_near1_df(sA[4 * kStage + o], rr - 1.0, d.gamma, bg_pos)
-                                       : sA[4 * kStage + o] * pow_near1(rr, d.gamma, bg_pos, amask);
+                // x = th dphi_r / (th_r dphi**) - 1, the ratio's offset from 1
+                const double x = fma(sA[2 * kStage + o] * sA[3 * kStage + o], (rtop - rbot) * rdfj, -1.0);
+                const double pstj = DF ? scale_near1_df(sA[4 * kStage + o], x, d.gamma, bg_pos)
+                                       : sA[4 * kStage + o] * pow1p_near0(x, d.gamma, bg_pos, amask);
                 pst[j] = pstj;
                 rdf[j] = rdfj;
                 const double C = gbg * pstj * rdfj;
                 if (j >= 1) {
-                    const double aj = bgr * ldg(d.rdBi + j);
-                    const double a = (j == 1) ? 0.0 : -aj * C_prev;
-                    const double c = (j == L - 1) ? 0.0 : -aj * C;
-                    const double b = fma(aj, C_prev + C, 1.0);
-                    const double rhs = sA[5 * kStage + o] + fma(aj, pstj - pst_prev, -bg);
+                    // row j / a_j: -C_{j-1} w_{j-1} + (1/a_j + C_{j-1} + C_j) w_j - C_j w_{j+1}
+                    //            = (w**_j - beta dt g)/a_j + p**_j - p**_{j-1}
+                    // (no w_{j+1} term in the last row: w_L = 0)
+                    const double sj = ldg(d.dBi + j) * psg;
+                    const double b = sj + (C_prev + C);
+                    const double rhs = fma(sA[5 * kStage + o] - bg, sj, pstj - pst_prev);
+                    const double cq = (j == L - 1) ? 0.0 : C;
                     const int r = j - 1;
                     if (r == 0) {
                         const double rb = rcp_nr(b);
-                        cp[0] = c * rb;
+                        cp[0] = -cq * rb;
                         dd[0] = rhs * rb;
                     } else {
-                        const double rden = rcp_nr(fma(-a, cp[r - 1], b));
-                        cp[r] = c * rden;
-                        dd[r] = fma(-a, dd[r - 1], rhs) * rden;
+                        const double rden = rcp_nr(fma(C_prev, cp[r - 1], b));
+                        cp[r] = -cq * rden;
+                        dd[r] = fma(C_prev, dd[r - 1], rhs) * rden;
                     }
                 }
                 pst_prev = pstj;
@@ -785,7 +790,9 @@ __global__ void __launch_bounds__(32, kSolveMinBlocks) k_nh_solve(DevMesh m, DyP
     }
     // phi, EOS and momentum diagnostics, top to bottom
     if (act) phi_out[(size_t)i * d.ldi] = phi_top0;
-    double phi_top = phi_top0, dtop = 1.0, pprev = 0.0;
+    // halves of dp/dpi at the interfaces (1 at top and ground), so that the
+    // layer mean is one addition
+    double phi_top = phi_top0, htop = 0.5, pprev = 0.0;
     for (int k0 = 0; k0 < L; k0 += kSolveKC) {
         const int nk = min(kSolveKC, L - k0);
         __syncwarp();
@@ -803,19 +810,20 @@ __global__ void __launch_bounds__(32, kSolveMinBlocks) k_nh_solve(DevMesh m, DyP
                 const double xk = bg * (w_top - w_bot) * rdf[k];
                 const double pk = DF ? scale_near1_df(pst[k], xk, -d.gamma, bg_neg)
                                      : pst[k] * pow1p_near0(xk, -d.gamma, bg_neg, amask);
-                double dcur = 1.0;
+                double hcur = 0.5;
                 if (k > 0) {
-                    dcur = (pk - pprev) * (ldg(d.rdBi + k) * rdps);
-                    const double dv = 0.5 * (dtop + dcur);
+                    hcur = (pk - pprev) * (ldg(d.hrdBi + k) * rdps);
+                    const double dv = htop + hcur;
                     if (kk > 0) sA[5 * kStage + o - kRow] = emu<EMU>(dv, d.emu, GRIST_ROW_EOS);   // layer k-1 of this chunk
                     else dpp[(size_t)i * d.ld + k - 1] = emu<EMU>(dv, d.emu, GRIST_ROW_EOS);        // of the previous chunk
                 }
                 sA[2 * kStage + o] = emu<EMU>(pk, d.emu, GRIST_ROW_EOS);
-                sA[3 * kStage + o] = emu<EMU>((phi_top - phi_bot) * (ldg(d.rdB + k) * rdps), d.emu, GRIST_ROW_EOS);
-                sA[4 * kStage + o] = DF ? pack_split(0.5 * (phi_top + phi_bot))
-                                        : emu<EMU>(0.5 * (phi_top + phi_bot), d.emu, GRIST_ROW_EOS);
+                const double dphi = phi_top - phi_bot;
+                sA[3 * kStage + o] = emu<EMU>(dphi * (ldg(d.rdB + k) * rdps), d.emu, GRIST_ROW_EOS);
+                const double phm = fma(0.5, dphi, phi_bot);   // layer mean (phi_top + phi_bot)/2
+                sA[4 * kStage + o] = DF ? pack_split(phm) : emu<EMU>(phm, d.emu, GRIST_ROW_EOS);
                 sA[1 * kStage + o] = phi_bot;   // w_top of this row is no longer needed
-                dtop = dcur;
+                htop = hcur;
                 pprev = pk;
                 phi_top = phi_bot;
             }
@@ -827,7 +835,7 @@ __global__ void __launch_bounds__(32, kSolveMinBlocks) k_nh_solve(DevMesh m, DyP
         stage_out(phl, d.ld, col0, ncol, k0, nk, sA + 4 * kStage);
         stage_out(dpp, d.ld, col0, ncol, k0, nk - 1, sA + 5 * kStage);
     }
-    if (act) dpp[(size_t)i * d.ld + L - 1] = emu<EMU>(0.5 * (dtop + 1.0), d.emu, GRIST_ROW_EOS);
+    if (act) dpp[(size_t)i * d.ld + L - 1] = emu<EMU>(htop + 0.5, d.emu, GRIST_ROW_EOS);
 }
 
 // Relative vorticity at the vertices (diagnostic): zeta_v = sum_j ccurl u,
@@ -861,7 +869,7 @@ int dycore_step(grist_mesh_s *h, grist_dycore_state *S, const grist_dycore_param
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off += al(bytes); return o; };
-    const size_t nvg = 4 * (size_t)L + 2 + ((size_t)L + 1) / 2;   // doubles, then L floats
+    const size_t nvg = 5 * (size_t)L + 3 + ((size_t)L + 1) / 2;   // doubles, then L floats
     const size_t o_vg = take(sizeof(double) * nvg);
     const size_t o_uA = take(nEL * sizeof(TU)), o_uB = take(nEL * sizeof(TU));
     const size_t o_psA = take(m.nC * 8), o_psB = take(m.nC * 8), o_psN = take(m.nC * 8);
@@ -881,16 +889,19 @@ int dycore_step(grist_mesh_s *h, grist_dycore_state *S, const grist_dycore_param
     char *s = (char *)scratch(h, 1, off);
     if (!s) return GRIST_ENOMEM;
 
-    // vertical grid: B (L+1) | dB (L) | 1/dB (L) | 2/(dB[j-1]+dB[j]) (L+1)
+    // vertical grid: B (L+1) | dB (L) | 1/dB (L) | 1/(dB[j-1]+dB[j]) (L+1) | (dB[j-1]+dB[j])/2 (L+1)
     std::vector<double> vg(nvg, 0.0);
-    double *hB = vg.data(), *hdB = hB + L + 1, *hrdB = hdB + L, *hrdBi = hrdB + L;
+    double *hB = vg.data(), *hdB = hB + L + 1, *hrdB = hdB + L, *hhrdBi = hrdB + L, *hdBi = hhrdBi + L + 1;
     for (int k = 0; k <= L; k++) hB[k] = prm->b_interface[k];
     for (int k = 0; k < L; k++) {
         hdB[k] = prm->b_interface[k + 1] - prm->b_interface[k];
         hrdB[k] = 1.0 / hdB[k];
     }
-    for (int j = 1; j < L; j++) hrdBi[j] = 2.0 / (hdB[j - 1] + hdB[j]);
-    float *hdBf = reinterpret_cast<float *>(hrdBi + L + 1);
+    for (int j = 1; j < L; j++) {
+        hhrdBi[j] = 1.0 / (hdB[j - 1] + hdB[j]);
+        hdBi[j] = 0.5 * (hdB[j - 1] + hdB[j]);
+    }
+    float *hdBf = reinterpret_cast<float *>(hdBi + L + 1);
     for (int k = 0; k < L; k++) hdBf[k] = (float)hdB[k];
     double *dvg = (double *)(s + o_vg);
     if (vg_ptr(h) != dvg || vg_cache(h) != vg) {
@@ -905,8 +916,9 @@ int dycore_step(grist_mesh_s *h, grist_dycore_state *S, const grist_dycore_param
     d.L = L; d.ld = ld; d.ldi = ldi;
     d.pi_top = prm->pi_top; d.p0 = prm->p0; d.rd = prm->rd; d.cp = prm->cp; d.g = prm->g;
     d.beta = prm->offcentre_beta; d.kappa = prm->rd / prm->cp; d.gamma = prm->cp / (prm->cp - prm->rd);
-    d.B = dvg; d.dB = dvg + L + 1; d.rdB = dvg + 2 * L + 1; d.rdBi = dvg + 3 * L + 1; d.phis = prm->phi_surface;
-    d.dBf = reinterpret_cast<const float *>(dvg + 4 * L + 2);
+    d.B = dvg; d.dB = dvg + L + 1; d.rdB = dvg + 2 * L + 1; d.hrdBi = dvg + 3 * L + 1; d.dBi = dvg + 4 * L + 2;
+    d.phis = prm->phi_surface;
+    d.dBf = reinterpret_cast<const float *>(dvg + 5 * L + 3);
     d.emu = prm->emulate_fp32_rows;
 
     TU *uA = (TU *)(s + o_uA), *uB = (TU *)(s + o_uB);

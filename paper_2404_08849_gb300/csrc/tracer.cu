@@ -438,8 +438,42 @@ __device__ void run_phase(const DevMesh &m, const Batch &B, uint32_t *status) {
     if (bad) atomicOr(status, GRIST_FLAG_NONFINITE);
 }
 
+// Register cap of a work-list phase kernel in the binary32 policy.  These
+// kernels are bound by the latency of their neighbour gathers: a cap trades
+// the loads each thread keeps in flight against resident warps, and the best
+// point differs per phase (measured on the level-9 mesh, 60 levels, 4
+// tracers).  Compile-time, per phase; 0 = only the limit that lets a block
+// of kTracerMaxBlock threads launch (65536 registers per SM), which is also
+// the FP64 policy's cap.
+#ifndef GRIST_TR_REGS_EDGE
+#define GRIST_TR_REGS_EDGE 56
+#endif
+#ifndef GRIST_TR_REGS_UPD
+#define GRIST_TR_REGS_UPD 64
+#endif
+#ifndef GRIST_TR_REGS_LOWRES
+#define GRIST_TR_REGS_LOWRES 64
+#endif
+#ifndef GRIST_TR_REGS_RATIOS
+#define GRIST_TR_REGS_RATIOS 0
+#endif
+#ifndef GRIST_TR_REGS_FINAL
+#define GRIST_TR_REGS_FINAL 0
+#endif
+constexpr int kTracerRegLimit = 65536 / kTracerMaxBlock;
+constexpr int cap_or_none(int r) { return r > 0 && r < kTracerRegLimit ? r : kTracerRegLimit; }
+template <typename TC, int PH> constexpr int tracer_phase_regs() {
+    return sizeof(TC) != 4                                      ? kTracerRegLimit
+           : (PH == P_EDGE0 || PH == P_EDGE1 || PH == P_EDGE2) ? cap_or_none(GRIST_TR_REGS_EDGE)
+           : (PH == P_UPD0 || PH == P_UPD1 || PH == P_UPD2)    ? cap_or_none(GRIST_TR_REGS_UPD)
+           : PH == P_LOWRES                                    ? cap_or_none(GRIST_TR_REGS_LOWRES)
+           : PH == P_RATIOS                                    ? cap_or_none(GRIST_TR_REGS_RATIOS)
+           : PH == P_FINAL                                     ? cap_or_none(GRIST_TR_REGS_FINAL)
+                                                               : kTracerRegLimit;
+}
+
 template <typename TQ, typename TC, int PH>
-__global__ void k_tracer_phase(DevMesh m, Batch B, uint32_t *status) {
+__global__ void __maxnreg__((tracer_phase_regs<TC, PH>())) k_tracer_phase(DevMesh m, Batch B, uint32_t *status) {
     run_phase<false, TQ, TC, PH>(m, B, status);
 }
 
