@@ -93,14 +93,14 @@ def algorithmic_bytes(name, nC, nE, nV, L, T, prec):
 # (L + 1 per column) "i".  Per-launch figures scale with the units processed.
 FP64_WORK_MIX = {
     # kernel: (unit, FP64 flop per unit, DRAM bytes per unit)
-    "k_nh_solve": ("c", 66.73, 282.8),
-    "k_momentum": ("e", 19.88, 36.6),
-    "k_nh_explicit": ("i", 28.20, 73.1),
+    "k_nh_solve": ("c", 63.70, 280.8),
+    "k_momentum": ("e", 19.88, 36.8),
+    "k_nh_explicit": ("i", 27.37, 72.8),
     "k_ke": ("c", 18.00, 18.3),
-    "k_mass_col": ("c", 12.81, 45.9),
+    "k_mass_col": ("c", 13.32, 46.3),
     "k_vort": ("v", 3.00, 9.2),
     "k_eos": ("c", 93.0, 21.1),
-    "k_tr_div": ("c", 12.00, 31.6),
+    "k_tr_div": ("c", 12.00, 31.5),
     "k_tr_lowres": ("c", 14.00, 72.1),
 }
 
