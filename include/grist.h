@@ -461,11 +461,13 @@ int grist_selftest_conversions(uint64_t n_random, uint64_t seed, uint64_t *out_c
 int grist_selftest_reciprocal(uint64_t n, uint64_t seed, uint64_t *out_checked, uint64_t *out_over_1ulp,
                               uint64_t *out_max_ulp);
 
-/* Diagnostic: check the double-float split used by GRIST_MIX_DF (x ~ h + l,
- * h = x rounded to binary32, l = the residual rounded to binary32) on n
- * pseudo-random binary64 values (splitmix64 of seed + i; |x| in
- * [2^-74, 2^127), any sign and fraction): counts splits whose h differs from
- * the hardware rounding of x or whose |x - (h + l)| exceeds 2^-47 |x|.
+/* Diagnostic: check the double-float splits x ~ h + l on n pseudo-random
+ * binary64 values (splitmix64 of seed + i; |x| in [2^-74, 2^127), any sign
+ * and fraction): the rounding split used by GRIST_MIX_DF (h = x rounded to
+ * binary32, l = the residual rounded to binary32) and the truncating split
+ * of the binary32 advection of w and phi (h = x truncated toward zero).
+ * Counts values where either h differs from the hardware conversion (to
+ * nearest, toward zero) or either |x - (h + l)| exceeds 2^-47 |x|.
  * Synchronous (default stream); allocates and frees 16 bytes of device
  * memory.  No counterpart in the paper. */
 int grist_selftest_split(uint64_t n, uint64_t seed, uint64_t *out_checked, uint64_t *out_bad);

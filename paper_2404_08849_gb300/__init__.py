@@ -58,8 +58,9 @@ def selftest_conversions(n_random=1 << 28, seed=2404_08849):
 
 
 def selftest_split(n=1 << 28, seed=2404_08849):
-    """grist_selftest_split: the double-float split against RN32 and its
-    2^-47 error bound.  Returns (checked, failures)."""
+    """grist_selftest_split: the rounding and truncating double-float splits
+    against RN32 / RZ32 and their 2^-47 error bound.  Returns (checked,
+    failures)."""
     lib = _lib.load()
     c, b = ctypes.c_uint64(), ctypes.c_uint64()
     _lib.check("grist_selftest_split", lib.grist_selftest_split(int(n), int(seed), ctypes.byref(c), ctypes.byref(b)))

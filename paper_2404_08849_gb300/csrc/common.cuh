@@ -236,6 +236,23 @@ __device__ __forceinline__ float d2f_trunc(double x) {
     return __uint_as_float(m | (hi & 0x80000000u));
 }
 
+// Truncating double-float split for differencing: h = x truncated toward
+// zero to binary32 (d2f_trunc), l = the 29 dropped significand bits, an
+// integer in units of 2^(e - 1075), converted to binary32 and scaled, with
+// the sign of x: |x - (h + l)| <= 2^-47 |x| for 2^-74 <= |x| < 2^128
+// (smaller magnitudes keep h only; 2^128 and above, infinities and NaN
+// give a NaN h).  About a dozen integer / binary32 instructions and no
+// branch - cheaper than split_df where only differences of the pair are
+// taken.
+__device__ __forceinline__ void split_trunc(double x, float &h, float &l) {
+    const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+    const int ex = (int)((hi >> 20) & 0x7ffu);
+    h = ex > 1150 ? __uint_as_float(0x7fc00000u) : d2f_trunc(x);
+    const float scale = (ex >= 949 && ex <= 1150) ? __uint_as_float((uint32_t)(ex - 1075 + 127) << 23) : 0.f;
+    const float rl = __uint2float_rn(lo & 0x1fffffffu) * scale;
+    l = __uint_as_float(__float_as_uint(rl) | (hi & 0x80000000u));
+}
+
 // a - b for two binary64 values of similar size, in binary32 arithmetic
 // from their double-float splits: the high parts subtract exactly
 // (Sterbenz, when within a factor of two), the low parts add the rest; the

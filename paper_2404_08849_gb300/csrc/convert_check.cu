@@ -1,8 +1,8 @@
 // convert_check.cu - self-tests of the arithmetic helpers in common.cuh:
 // the integer binary32 <-> binary64 conversions (f2d, d2f) against the
 // hardware conversions, the Newton-Raphson reciprocal (rcp_nr) against the
-// IEEE quotient 1.0 / x, and the double-float split (split_df) against its
-// error bound.
+// IEEE quotient 1.0 / x, and the double-float splits (split_df,
+// split_trunc) against their error bound.
 // Each kernel compares both results in-register and counts disagreements,
 // so the 2^32-pattern sweeps need no input or output buffers.
 #include "common.cuh"
@@ -102,9 +102,11 @@ __global__ void k_check_rcp(unsigned long long n, unsigned long long seed, unsig
     atomicMax(out + 2, worst);
 }
 
-// out[0] checked, out[1] splits with h != RN32(x) or |x - (h + l)| above
-// 2^-47 |x| (the bound is exact arithmetic: h and l are floats, so
-// x - h - l is formed in binary64 without error for these magnitudes)
+// out[0] checked, out[1] values whose split_df has h != RN32(x) or whose
+// split_trunc has h != RZ32(x) (the hardware conversion toward zero), or
+// where either gives |x - (h + l)| above 2^-47 |x| (the bound is exact
+// arithmetic: h and l are floats, so x - h - l is formed in binary64
+// without error for these magnitudes)
 __global__ void k_check_split(unsigned long long n, unsigned long long seed, unsigned long long *out) {
     unsigned long long cnt = 0, bad = 0;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
@@ -117,7 +119,11 @@ __global__ void k_check_split(unsigned long long n, unsigned long long seed, uns
         float h, l;
         split_df(x, h, l);
         const double err = fabs((x - (double)h) - (double)l);
-        bad += (__float_as_uint(h) != __float_as_uint((float)x)) || !(err <= ldexp(fabs(x), -47));
+        float th, tl;
+        split_trunc(x, th, tl);
+        const double terr = fabs((x - (double)th) - (double)tl);
+        bad += (__float_as_uint(h) != __float_as_uint((float)x)) || !(err <= ldexp(fabs(x), -47)) ||
+               (__float_as_uint(th) != __float_as_uint(__double2float_rz(x))) || !(terr <= ldexp(fabs(x), -47));
         cnt++;
     }
     atomicAdd(out + 0, cnt);

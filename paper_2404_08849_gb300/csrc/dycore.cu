@@ -576,11 +576,29 @@ __global__ void k_eos(DevMesh m, DyPar d, LevelDiv Dv, const double *__restrict_
         emu<EMU>(d.p0 * exp(d.gamma * log(d.rd * th[(size_t)i * d.ld + k] / (d.p0 * dphi))), d.emu, GRIST_ROW_EOS);
 }
 
+// A binary32 advective type takes the differences of the FP64 fields from
+// their truncating double-float splits (split_trunc; accurate to about 2^-24
+// of the difference before its binary32 rounding) instead of FP64
+// subtractions, so the binary32 advection issues no FP64 instruction.
+template <typename TA> struct AdvVal;
+template <> struct AdvVal<double> {
+    double v;
+    __device__ __forceinline__ explicit AdvVal(double x) : v(x) {}
+};
+template <> struct AdvVal<float> {
+    float h, l;
+    __device__ __forceinline__ explicit AdvVal(double x) { split_trunc(x, h, l); }
+};
+__device__ __forceinline__ double adv_diff(const AdvVal<double> &a, const AdvVal<double> &b) { return a.v - b.v; }
+__device__ __forceinline__ float adv_diff(const AdvVal<float> &a, const AdvVal<float> &b) {
+    return diff_df(a.h, a.l, b.h, b.l);
+}
+
 // Explicit parts of Eqs. 6-7 at every interface: horizontal advection
 // V.grad(x) = (1/A) sum s dv u^int (x_nb - x)/2 and vertical advection
 // M (x_{j+1} - x_{j-1}) / (dpi_{j-1} + dpi_j) of w and phi from the stage
-// input (advective type; differences of the FP64 fields taken in FP64
-// first), plus the (1 - beta) share of g (dp/dpi - 1) and g w at t^n.  The
+// input (advective type; the differences of the FP64 fields are formed to
+// about 2^-24 of themselves before the rounding to that type), plus the (1 - beta) share of g (dp/dpi - 1) and g w at t^n.  The
 // t^n forcing g (dp/dpi - 1) is formed in the first stage (FIRST) from the
 // t^n pressure and kept for the later stages.
 template <class P, bool FIRST>
@@ -602,7 +620,7 @@ __global__ void k_nh_explicit(DevMesh m, DyPar d, LevelDiv Dv, const typename P:
         phst[xi] = ldg(d.phis + i);
         return;
     }
-    const double wi = w_s[xi], pi = phi_s[xi];
+    const AdvVal<TA> wi(w_s[xi]), pi(phi_s[xi]);
     TA hw = 0, hp = 0;
 #pragma unroll
     for (int s = 0; s < GRIST_MAXE; s++) {
@@ -614,16 +632,16 @@ __global__ void k_nh_explicit(DevMesh m, DyPar d, LevelDiv Dv, const typename P:
         else ui = (TA)0.5 * (cv<TA>(ldg(u_s + ue + j - 1)) + cv<TA>(ldg(u_s + ue + j)));
         const TA cu = ldg(Coef<TA>::cdiv(m) + i * 6 + s) * ui * (TA)0.5;
         const size_t y = (size_t)nb * d.ldi + j;
-        hw += cu * cv<TA>(ldg(w_s + y) - wi);
-        hp += cu * cv<TA>(ldg(phi_s + y) - pi);
+        hw += cu * adv_diff(AdvVal<TA>(ldg(w_s + y)), wi);
+        hp += cu * adv_diff(AdvVal<TA>(ldg(phi_s + y)), pi);
     }
     TA vw = 0, vp = 0;
     double fw = 0.0;
     if (j > 0) {
         const double rd2 = ldg(d.hrdBi + j) * ldg(rdps_s + i);   // 1/(dpi_{j-1} + dpi_j)
         const TA r = cv<TA>(Mv[(size_t)i * d.ldi + j] * rd2);
-        vw = r * cv<TA>(w_s[xi + 1] - w_s[xi - 1]);
-        vp = r * cv<TA>(phi_s[xi + 1] - phi_s[xi - 1]);
+        vw = r * adv_diff(AdvVal<TA>(w_s[xi + 1]), AdvVal<TA>(w_s[xi - 1]));
+        vp = r * adv_diff(AdvVal<TA>(phi_s[xi + 1]), AdvVal<TA>(phi_s[xi - 1]));
         if (FIRST) {
             // first stage: the stage input is t^n, so rdps_s is 1/(ps^n - pi_top)
             fw = d.g * fma(p_n[(size_t)i * d.ld + j] - p_n[(size_t)i * d.ld + j - 1], 2.0 * rd2, -1.0);
