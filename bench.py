@@ -95,7 +95,7 @@ FP64_WORK_MIX = {
     # kernel: (unit, FP64 flop per unit, DRAM bytes per unit)
     "k_nh_solve": ("c", 63.70, 280.8),
     "k_momentum": ("e", 19.88, 36.8),
-    "k_nh_explicit": ("i", 27.37, 72.8),
+    "k_nh_explicit": ("i", 13.38, 73.4),
     "k_ke": ("c", 18.00, 18.3),
     "k_mass_col": ("c", 13.32, 46.3),
     "k_vort": ("v", 3.00, 9.2),
