@@ -155,6 +155,7 @@ def _setup():
         "orc_interface_hadv": [M, _I, pd, pd, pd],
         "orc_interface_vadv": [_I, _I, pd, pd, pd, pd],
         "orc_thomas": [_I, pd, pd, pd, pd, pd],
+        "orc_dpdpi_layer": [_I, _I, pd, pd, pd],
         "orc_vertical_solve": [Pp, _I, pd, pd, pd, pd, _D, pd, pd, pd],
         "orc_dycore_step_nh": [M, Pp, pd, pd, pd, pd, pd, pd, pd, pd, _D],
         "orc_compensated_sum": [ctypes.c_int64, pd, pd, pd],
@@ -343,6 +344,14 @@ def vertical_solve(P: Params, w_star, phi_star, dpi_theta, dpi, dts):
     _f().orc_vertical_solve(P.ref, nC, _dp(_f64(w_star)), _dp(_f64(phi_star)), _dp(_f64(dpi_theta)),
                             _dp(_f64(dpi)), dts, _dp(w), _dp(phi), _dp(p))
     return w, phi, p
+
+
+def dpdpi_layer(p, dpi):
+    """dp/dpi averaged to layers (the L operator of Eq. 5): p, dpi [nC][L]."""
+    p = _f64(p); nC, L = p.shape
+    out = np.empty((nC, L))
+    _f().orc_dpdpi_layer(nC, L, _dp(p), _dp(_f64(dpi)), _dp(out))
+    return out
 
 
 def dycore_step_nh(M: Mesh, P: Params, state, dt, flux_accum=None, vflux_accum=None):

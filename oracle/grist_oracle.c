@@ -679,7 +679,7 @@ void orc_vertical_solve(const orc_params *P, int nC, const double *w_star, const
 /* d p / d pi averaged to layers (the paper's L operator in Eq. 5, reading:
  * mean of the two interface values, interface value (p_j - p_{j-1}) /
  * dpi_j^int in the interior and 1 at the top and bottom). */
-static void dpdpi_layer(int nC, int L, const double *p, const double *dpi, double *out) {
+void orc_dpdpi_layer(int nC, int L, const double *p, const double *dpi, double *out) {
     for (int i = 0; i < nC; i++)
         for (int k = 0; k < L; k++) {
             double top = 1.0, bot = 1.0;
@@ -776,7 +776,7 @@ void orc_dycore_step_nh(const orc_mesh *m, const orc_params *P, double *ps, doub
                 al[i * L + k] = dphi / dpi_new[i * L + k];
                 phl[i * L + k] = 0.5 * (phi[i * Li + k] + phi[i * Li + k + 1]);
             }
-        dpdpi_layer(m->nC, L, p, dpi_new, dpp);
+        orc_dpdpi_layer(m->nC, L, p, dpi_new, dpp);
         orc_momentum_tend(m, L, u_s, dpi, F, M, p, al, phl, dpp, ut);
         for (size_t x = 0; x < nEL; x++) u[x] = u_n[x] + h * ut[x];
         if (s == 2 && flux_accum) {
