@@ -178,10 +178,20 @@ def test_nh_fp64_parity(dev_meshes):
     got = run_dycore(mesh, st, L, 120.0, nh=True)
     for k in ("u", "ps", "dpi_theta", "phi"):
         assert _rel(got[k], ref[k]) <= FP64_TOL, k
-    # w is a small residual of large pressure differences: compare it against
-    # its own scale with the bound scaled by the cancellation factor
-    # max|p| / (max|dp/dpi - 1| * max|dpi|) of the column (~1e3 here)
-    assert _rel(got["w"], ref["w"]) <= 1e-9
+    check_w_fp64(got["w"], ref["w"], 120.0)
+
+
+def check_w_fp64(w, w_ref, dt, beta=0.55):
+    """w leaves the column solve as w** + beta dt g ((p_j - p_{j-1})/dpi_j - 1):
+    the difference of two terms of size beta dt g each (dp/dpi ~ 1 in a
+    near-hydrostatic column), so its rounding error scales with beta dt g,
+    not with the small |w|.  The per-step bound of the FP64 path is held on
+    that scale; the ratio beta dt g / max|w| is the cancellation factor."""
+    scale = beta * dt * S.GRAVITY
+    dw = float(np.max(np.abs(w - w_ref)))
+    print("w: max|dw| %.3e m/s = %.2e of beta dt g (%.1f m/s); max|w| %.3e; cancellation factor %.3g"
+          % (dw, dw / scale, scale, np.max(np.abs(w_ref)), scale / np.max(np.abs(w_ref))))
+    assert dw <= FP64_TOL * scale
 
 
 @pytest.mark.parametrize("prec", ["mix", "mix_dbl_mass"])
@@ -196,7 +206,19 @@ def test_nh_mix_accuracy(dev_meshes, prec):
     assert _rel(got["ps"], ref["ps"]) <= 1e-7
     assert _rel(got["dpi_theta"], ref["dpi_theta"]) <= 5e-7
     assert _rel(got["phi"], ref["phi"]) <= 1e-9
-    assert _rel(got["w"], ref["w"]) <= 1e-3
+    check_w_mixed(got["w"], ref["w"], 120.0)
+
+
+def check_w_mixed(w, w_ref, dt, beta=0.55):
+    """Mixed path: the advective increments of w and phi are formed in
+    binary32, so each carries one binary32 rounding (2^-24 of itself) into
+    the column solve, whose terms are of size beta dt g; w can therefore be
+    off by up to 2^-24 beta dt g, but not more."""
+    scale = beta * dt * S.GRAVITY
+    dw = float(np.max(np.abs(w - w_ref)))
+    print("mixed w: max|dw| %.3e m/s, %.2e of max|w|, %.2e of beta dt g" % (
+        dw, dw / np.max(np.abs(w_ref)), dw / scale))
+    assert dw <= 2.0 ** -24 * scale
 
 
 @pytest.mark.parametrize("nh,prec", [(False, "fp64"), (False, "mix"), (True, "fp64"), (True, "mix")])
