@@ -19,8 +19,15 @@
 //     part of the array has to start at zero and stale contents from the
 //     previous call are never used;
 //   - the first call on a device looks up the array's device address
-//     (cudaGetSymbolAddress) with that device current and caches it; make
-//     that first call before any stream capture.
+//     (cudaGetSymbolAddress) with that device current and caches it for the
+//     life of the process; make that first call before any stream capture.
+//     The cache assumes the device is not reset (cudaDeviceReset) between
+//     calls: a reset reloads the module, and the cached address would no
+//     longer name the array.
+//   - the summation is the compensated method of grist_global_sums
+//     (Neumaier accumulation, then a TwoSum tree) in an order of its own:
+//     bitwise reproducible run to run, not bitwise equal to
+//     grist_global_sums.
 #include <mutex>
 
 #include "common.cuh"
@@ -126,7 +133,10 @@ extern "C" int grist_weighted_sum_noalloc(const double *x, const double *w, int6
     if (rc != GRIST_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     const int nb = n == 0 ? 0 : (int)((n + GRIST_NOALLOC_CHUNK - 1) / GRIST_NOALLOC_CHUNK);
-    if (nb > 0) k_noalloc_partial<<<nb, kNoAllocThreads, 0, st>>>(x, w, (long long)n, part);
+    if (nb > 0) {
+        k_noalloc_partial<<<nb, kNoAllocThreads, 0, st>>>(x, w, (long long)n, part);
+        if (cudaGetLastError() != cudaSuccess) return GRIST_ECUDA;
+    }
     k_noalloc_final<<<1, kNoAllocThreads, 0, st>>>(part, nb, out_sum_and_err);
     return cudaGetLastError() == cudaSuccess ? GRIST_OK : GRIST_ECUDA;
 }

@@ -54,3 +54,34 @@ def test_noalloc_weighted_sum_matches_global_sums(mesh_cache):
     assert lib.grist_weighted_sum_noalloc(ctypes.c_void_p(ones.data_ptr()), None, too_many,
                                           ctypes.c_void_p(out.data_ptr()), stream) == -1
     mesh.close()
+
+
+@pytest.mark.parametrize("n", [65536, 3 * 65536 + 17, 300 * 65536 + 17])
+def test_noalloc_multi_block(n):
+    """Several blocks: the per-block partials and their compensated merge
+    (one chunk exactly, a ragged last chunk, a few hundred chunks), then a
+    second call with fewer blocks, which must not read the first call's
+    leftover partials.  Random weights and values against math.fsum."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2404_08849_gb300 import _lib
+    lib = _lib.load()
+    torch.cuda.set_device(0)
+    out = torch.full((2,), float("nan"), dtype=torch.float64, device="cuda")
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rng = np.random.default_rng(n)
+    for nn in (n, n // 3 + 5):
+        x_host = rng.standard_normal(nn) * 100.0 + 3.0
+        w_host = rng.uniform(0.5, 2.0, nn)
+        x = torch.from_numpy(x_host).cuda()
+        w = torch.from_numpy(w_host).cuda()
+        rc = lib.grist_weighted_sum_noalloc(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(w.data_ptr()), nn,
+                                            ctypes.c_void_p(out.data_ptr()), stream)
+        assert rc == 0
+        torch.cuda.synchronize()
+        got = float(out[0].item())
+        exact = math.fsum((w_host * x_host).tolist())
+        # the products w*x are rounded once on either side; the bound is on
+        # the sum of those rounded products
+        assert abs(got - exact) <= 4 * np.spacing(abs(exact)), (nn, got, exact)
