@@ -38,18 +38,23 @@ UNIT = "cell-level-steps/s"
 WORKLOADS = {
     # name: mesh level, levels, non-hydrostatic, tracers, dt
     "g9nh": dict(level=9, L=60, nh=True, T=4, dt=30.0,
+                 phys="NH dycore + 4 tracers (3rd-order + FCT horizontal, adaptively implicit vertical), dt 30 s",
                  desc="NH dycore + 4 tracers (3rd-order + FCT horizontal, adaptively implicit vertical), "
                       "L9 mesh 2621442 cells, 60 levels, dt 30 s"),
-    "g8nh": dict(level=8, L=60, nh=True, T=0, dt=60.0,
+    "g8nh": dict(level=8, L=60, nh=True, T=0, dt=60.0, phys="NH dycore, dt 60 s",
                  desc="NH dycore, L8 mesh 655362 cells, 60 levels, dt 60 s"),
-    "g6hdc": dict(level=6, L=30, nh=False, T=0, dt=300.0,
+    "g6hdc": dict(level=6, L=30, nh=False, T=0, dt=300.0, phys="hydrostatic dycore, dt 300 s",
                   desc="hydrostatic dycore, L6 mesh 40962 cells, 30 levels, dt 300 s"),
 }
 
 
-def algorithmic_bytes(name, nC, nE, nV, L, T, prec):
+def algorithmic_bytes(name, nC, nE, nV, L, T, prec, tiled=True, fct=True):
     """Compulsory bytes of one launch: every array the kernel declares read
-    or written once (stencil re-reads, padding and index tables excluded)."""
+    or written once (stencil re-reads, padding and index tables excluded).
+    tiled: the tracer step ran the tiled stages (whose continuity pass also
+    writes the {dpi, div F} pairs and the binary32 flux); fct: with the
+    limiter (two tiled stage launches per step, else three)."""
+    n_stage = 2 if fct else 3
     base = name.split("/")[0]
     sU = sA = sM = 8
     if prec in ("mix", "mix_dbl_mass", "mix_df"):
@@ -72,7 +77,12 @@ def algorithmic_bytes(name, nC, nE, nV, L, T, prec):
         "k_nh_solve": 2 * CI * 8 + CL * 8 + nC * 8 + 2 * CI * 8 + 4 * CL * 8,
         "k_add_scalar": 16,
         "k_vertex_mass": nC * 8 + nV * 8,
-        "k_tr_div": EL * 8 + CL * 8,
+        "k_tr_div": EL * 8 + CL * 8 + (CL * 8 + 2 * CL * sC + (EL * sC if sC == 4 else 0) if tiled else 0),
+        # tiled stages (mean per launch over the step's launches): q_in, q^n,
+        # q_out (+ the copy of q^n in the first stage), binary32 flux, {dpi, div F}
+        "k_trt_stage": (3 + 1.0 / n_stage) * T * CL * sQ + EL * sC + 2 * CL * sC,
+        "k_trt_fct_a": 2 * T * CL * sQ + EL * sC + 2 * CL * sC + 2 * T * CL * sC,
+        "k_trt_fct_b": 2 * T * CL * sQ + 2 * T * CL * sC + EL * sC + 2 * CL * sC + T * CL * sQ,
         "k_tr_edge": T * CL * sQ + EL * 8 + T * EL * sC,
         "k_tr_update": T * EL * sC + T * CL * sQ + 2 * CL * 8 + T * CL * sQ,
         "k_tr_lowres": T * CL * sQ + EL * 8 + 2 * CL * 8 + T * CL * sQ,
@@ -112,6 +122,86 @@ def fp64_peak_tflops(sm_mhz):
     """FP64 peak from the unit counts and clock: 152 SMs x 2 DFMA per clock
     x 2 flop at the given SM clock."""
     return SM_COUNT * DFMA_PER_SM_CLK * 2 * sm_mhz * 1e6 / 1e12
+
+
+# Algorithmic FP64 work of the double-precision terms of the mixed step, per
+# unit, counted from the discrete formulas as written (every +, -, *, / one
+# flop, a pow one flop; the factoring, reciprocal tables and series the
+# kernels use instead are not counted):
+#   k_momentum (Eq. 5, FP64 terms of the mixed policy): -(K2 - K1)/dc (2);
+#     eta-dot du/deta = [Mb(u+ - u) + Mt(u - u-)]/(2 dpi_e) with the cell
+#     means Mb, Mt (2 x (1 add + 1 mul)), two differences, two products, a
+#     sum, 2 dpi_e (1 add) and the division (11); -alpha_e (p2 - p1)/dc with
+#     alpha_e a cell mean (5); -(dp/dpi)_e (phi2 - phi1)/dc (5 NH; 2 in the
+#     hydrostatic core, dp/dpi = 1); the four terms summed (3): 26 NH / 23 HDC
+#     per edge-level.
+#   k_nh_solve (Eqs. 6, 7, 9 implicit part): dphi** (1), the EOS p** (5),
+#     C = gamma p** beta dt g / dphi** (3), a = beta dt g / dpi at the
+#     interface with the interface mass a mean (3), the row's diagonal and
+#     right-hand side (8), Thomas forward (6) and back (2) sweeps,
+#     phi = phi** + beta dt g w (2), the final EOS (6), alpha = dphi/dpi
+#     (1), the layer phi (2), dp/dpi at the interface and its layer mean (4):
+#     43 per cell-level.
+#   k_ke (Eq. 5 KE): sum over 6 edges of (dc dv / 4A) u^2 (3 each): 18 per
+#     cell-level.
+#   k_nh_explicit (Eqs. 6-7 explicit part, FP64 share): the t^n forcing
+#     g ((p_j - p_{j-1}) / dpi_j - 1) (4 + 2 for the interface mass), w** and
+#     phi** updates (4 + 3): 13 per interface.
+#   k_eos (Eq. 9): dphi, Rd dpi_theta / (p0 dphi) (3), the pow, p0 x: 6 per
+#     cell-level.
+#   k_mass_col (Eq. 3 column part, FP64 share): the vertical mass flux
+#     M = -B dps/dt - sum D (3) and theta = dpi_theta / dpi (1): 4 per
+#     cell-level.
+#   k_tr_div (tracer continuity, Eq. 10 with the FP64 flux): 6 products and
+#     5 sums: 11 per cell-level.
+FP64_ALG = {
+    "k_momentum": ("e", 26.0, 23.0),
+    "k_nh_solve": ("c", 43.0, 43.0),
+    "k_ke": ("c", 18.0, 18.0),
+    "k_nh_explicit": ("i", 13.0, 13.0),
+    "k_eos": ("c", 6.0, 6.0),
+    "k_mass_col": ("c", 4.0, 4.0),
+    "k_tr_div": ("c", 11.0, 11.0),
+}
+
+
+def measure_fp64_peak(G, torch, device, seconds=0.25):
+    """FP64 FMA rate of this GPU from grist_bench_fp64_fma: 16 warps' worth
+    of independent FMA chains per SM scheduler slot, timed with CUDA events
+    on the launching stream (best of 5 after 3 warm-up launches), with the
+    SM clock sampled during the timed launches."""
+    blocks, threads = SM_COUNT * 8, 256
+    out = torch.empty(blocks * threads, dtype=torch.float64, device=device)
+    iters = 4096
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # size the launch to about `seconds`
+    e0.record(st)
+    fl = G.bench_fp64_fma(out, iters, blocks, threads)
+    e1.record(st)
+    torch.cuda.synchronize()
+    iters = max(4096, int(iters * seconds / max(e0.elapsed_time(e1) * 1e-3, 1e-6)))
+    for _ in range(3):
+        G.bench_fp64_fma(out, iters, blocks, threads)
+    cs = ClockSampler(device)
+    cs.start()
+    best = None
+    for _ in range(5):
+        e0.record(st)
+        fl = G.bench_fp64_fma(out, iters, blocks, threads)
+        e1.record(st)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) * 1e-3
+        best = t if best is None else min(best, t)
+    clocks = cs.stop()
+    assert bool(torch.isfinite(out).all())
+    tf = fl / best / 1e12
+    sm = clocks.get("sm_mhz")
+    return {"tflops": round(tf, 4), "launch_ms": round(best * 1e3, 3), "flop_per_launch": fl,
+            "sm_mhz": sm, "tflops_per_ghz": round(tf / (sm / 1e3), 4) if sm else None,
+            "derived_tflops_at_max_clock": round(fp64_peak_tflops(2070.0), 4),
+            "how": "grist_bench_fp64_fma: %d blocks x %d threads x 8 independent FMA chains x %d rounds, "
+                   "CUDA events, best of 5" % (blocks, threads, iters)}
 
 
 def units_of(kind, nC, nE, nV, L):
@@ -285,6 +375,8 @@ def gpu_arm(args, wl):
     K, W = args.steps, args.warmup
 
     tunings = {}
+    fp64_peak = None if args.no_fp64_peak else measure_fp64_peak(G, torch, device)
+    finals = {}
 
     def run_prec(prec, sample_clocks=False):
         s = make_state(torch, host, prec, device, nE, nC, L, T, wl["nh"])
@@ -309,14 +401,28 @@ def gpu_arm(args, wl):
             step(mesh, s, P, wl, prec)
         prof = mesh.profile_read()
         mesh.profile(False)
-        # conservation check at the end of the run
+        # conservation and the end state, for the mixed-vs-FP64 error norms
         dry = mesh.global_sum(G.GRIST_SUM_DRY_MASS, s["ps"], offset=float(P.c.pi_top))[0]
+        fin = {"ps": s["ps"].clone(), "dpi_theta": s["dpi_theta"].clone(),
+               "vor": mesh.vorticity(s["u"], L), "steps": W + 2 * K}
+        if wl["nh"]:
+            fin["w"] = s["w"].clone()
+        finals[prec] = fin
         del s
         torch.cuda.empty_cache()
         return secs, clocks, prof, status, dry
 
+    dry_start = mesh.global_sum(G.GRIST_SUM_DRY_MASS, torch.from_numpy(host["ps"]).to(device),
+                                offset=float(P.c.pi_top))[0]
     secs_mix, clocks, prof_mix, st_mix, dry_mix = run_prec(args.prec, sample_clocks=True)
     secs_64, _, prof_64, st_64, dry_64 = (run_prec("fp64") if not args.no_fp64 else (None, None, {}, 0, None))
+    accuracy = None
+    if "fp64" in finals and args.prec in finals and args.prec != "fp64":
+        accuracy = mixed_vs_fp64(torch, mesh, m, finals[args.prec], finals["fp64"], P, wl, device)
+        accuracy["dry_mass_drift"] = {args.prec: (dry_mix - dry_start) / dry_start,
+                                      "fp64": (dry_64 - dry_start) / dry_start}
+    finals.clear()
+    torch.cuda.empty_cache()
 
     # end to end through the public API with host buffers: pinned H2D of the
     # state, the step, D2H of the new state, every step
@@ -357,19 +463,28 @@ def gpu_arm(args, wl):
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    f64_peak = fp64_peak_tflops(sm_max)
+    f64_peak = fp64_peak["tflops"] if fp64_peak else fp64_peak_tflops(sm_max)
+    f64_src = ("measured: " + fp64_peak["how"]) if fp64_peak else (
+        "derived: %d SMs x %d DFMA/clk x 2 flop x %.0f MHz" % (SM_COUNT, DFMA_PER_SM_CLK, sm_max))
     fp64_table = FP64_WORK_MIX if args.prec != "fp64" else {}
     kernels = []
+    tiled = any(k.startswith("k_trt_") for k in prof_mix)
     for name, (launches, ms) in sorted(prof_mix.items(), key=lambda kv: -kv[1][1]):
-        b = algorithmic_bytes(name, nC, nE, nV, L, T, args.prec)
+        b = algorithmic_bytes(name, nC, nE, nV, L, T, args.prec, tiled=tiled)
         avg = ms / max(launches, 1)
         row = {"kernel": name, "launches": launches, "total_ms": round(ms, 3),
                "avg_ms": round(avg, 4), "share": None,
                "gbs": round(b / (avg * 1e-3) / 1e9, 1) if b else None}
-        # the table counts the GRIST_MIX kernels' FP64 work
-        w = fp64_table.get(name.split("/")[0]) if name.endswith("/mix") else None
+        # FP64 work: algorithmic (formulas) and executed (ncu count of the
+        # GRIST_MIX kernels)
+        base = name.split("/")[0]
+        a = FP64_ALG.get(base)
+        if a and args.prec != "fp64":
+            fl = (a[1] if wl["nh"] else a[2]) * units_of(a[0], nC, nE, nV, L)
+            row["fp64_alg_tflops"] = round(fl / (avg * 1e-3) / 1e12, 4)
+        w = fp64_table.get(base) if name.endswith("/mix") else None
         if w:
-            row["fp64_tflops"] = round(w[1] * units_of(w[0], nC, nE, nV, L) / (avg * 1e-3) / 1e12, 4)
+            row["fp64_exec_tflops"] = round(w[1] * units_of(w[0], nC, nE, nV, L) / (avg * 1e-3) / 1e12, 4)
         kernels.append(row)
     tot = sum(k["total_ms"] for k in kernels) or 1.0
     for k in kernels:
@@ -381,19 +496,22 @@ def gpu_arm(args, wl):
                     "frac": round(dom["gbs"] / hbm_peak, 4), "peak_source": peak_src}
                    if dom["gbs"] is not None else None)
         w = fp64_table.get(dom["kernel"].split("/")[0]) if dom["kernel"].endswith("/mix") else None
-        if w:
-            units = units_of(w[0], nC, nE, nV, L)
-            roofline = {"bound": "alu", "kernel": dom["kernel"], "achieved": dom["fp64_tflops"],
+        a = FP64_ALG.get(dom["kernel"].split("/")[0]) if args.prec != "fp64" else None
+        if a and "fp64_alg_tflops" in dom:
+            units = units_of(a[0], nC, nE, nV, L)
+            per_unit = a[1] if wl["nh"] else a[2]
+            roofline = {"bound": "alu", "kernel": dom["kernel"], "achieved": dom["fp64_alg_tflops"],
                         "peak": round(f64_peak, 4), "unit": "TFLOP/s",
-                        "frac": round(dom["fp64_tflops"] / f64_peak, 4),
-                        "traffic": (int(w[2] * units) if w[2] is not None else None),
+                        "frac": round(dom["fp64_alg_tflops"] / f64_peak, 4),
+                        "traffic": (int(w[2] * units) if w and w[2] is not None else None),
                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per unit on the "
                                           "level-7 case, times this launch's units",
-                        "algorithmic_bytes": algorithmic_bytes(dom["kernel"], nC, nE, nV, L, T, args.prec),
-                        "work": "FP64 flop per launch %.4g (%.1f per unit, ncu-counted)" % (w[1] * units, w[1]),
-                        "peak_source": "derived: %d SMs x %d DFMA/clk x 2 flop x %.0f MHz" % (
-                            SM_COUNT, DFMA_PER_SM_CLK, sm_max),
-                        "hbm": hbm_ctx}
+                        "algorithmic_bytes": algorithmic_bytes(dom["kernel"], nC, nE, nV, L, T, args.prec, tiled=tiled),
+                        "work": "algorithmic FP64 flop per launch %.4g (%.1f per unit, from the formulas)%s" % (
+                            per_unit * units, per_unit,
+                            ("; executed %.1f per unit (ncu), %.4g TFLOP/s executed" % (w[1], dom["fp64_exec_tflops"]))
+                            if w else ""),
+                        "peak_source": f64_src, "hbm": hbm_ctx}
         elif hbm_ctx:
             roofline = dict({"bound": "hbm", "kernel": dom["kernel"], "traffic": None}, **hbm_ctx)
     launches_per_step = sum(k["launches"] for k in kernels) / max(K, 1)
@@ -432,10 +550,13 @@ def gpu_arm(args, wl):
     del mesh
     torch.cuda.empty_cache()
     batched = None if args.no_batched else batched_ensemble(G, torch, device, args, dist)
+    secondary = None
+    if not args.no_secondary and args.workload == "g9nh" and args.mesh_level is None:
+        secondary = [secondary_line(G, torch, name, args, device, dist) for name in ("g6hdc", "g8nh")]
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(wl, level=args.cpu_level)
+        cpu = cpu_baseline(wl, level=args.cpu_level, steps=args.cpu_steps)
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
@@ -451,13 +572,77 @@ def gpu_arm(args, wl):
                          "speedup_mix_over_fp64": secs_64 / secs_mix} if secs_64 else None),
                "roofline": roofline, "kernels": kernels[:12], "gpu_launches": int(round(launches_per_step * K)),
                "batched_ensemble": batched, "split_coupling": split,
-               "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
+               "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks, "fp64_peak": fp64_peak,
+               "accuracy_vs_fp64": accuracy, "secondary": secondary,
                "status_flags": {"mix": st_mix, "fp64": st_64},
                "dry_mass_end": {"mix": dry_mix, "fp64": dry_64}}
         print(json.dumps(out))
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def norms_dev(torch, x, ref, w):
+    """Normalised (l1, l2, linf) of x against ref on the device in float64
+    (Eq. 2 read as the Williamson norms: I|x - r| / I|r|,
+    sqrt(I(x - r)^2 / I r^2), max|x - r| / max|r|; I the weighted sum)."""
+    d = x - ref
+    l1 = (w * d.abs()).sum() / (w * ref.abs()).sum()
+    l2 = torch.sqrt((w * d * d).sum() / (w * ref * ref).sum())
+    linf = d.abs().max() / ref.abs().max()
+    return [float(l1), float(l2), float(linf)]
+
+
+def mixed_vs_fp64(torch, mesh, m, mix, ref, P, wl, device):
+    """Error of the mixed run's end state against the FP64 GPU run's (same
+    inputs, same number of steps; the FP64 path matches the oracle to 1e-12
+    per step): normalised l1/l2/linf of the surface pressure, the relative
+    vorticity, theta and w, and the paper's E = max(L(ps), L(vor)) (Eqs. 1-2)
+    against its acceptance threshold 0.05."""
+    ca = torch.from_numpy(mesh.to_internal(m["cell_area"])).to(device)
+    va = torch.from_numpy(mesh.to_internal(m["vertex_area"], "vertex")).to(device)
+    b = torch.from_numpy(np.asarray(P.b, np.float64)).to(device)
+    db = b[1:] - b[:-1]
+    pit = float(P.c.pi_top)
+
+    def theta(f):
+        dpi = (f["ps"] - pit)[:, None] * db[None, :]
+        return f["dpi_theta"] / dpi, dpi
+    th_m, _ = theta(mix)
+    th_r, dpi_r = theta(ref)
+    out = {"steps": mix["steps"], "simulated_s": mix["steps"] * wl["dt"],
+           "ps": norms_dev(torch, mix["ps"], ref["ps"], ca),
+           "vorticity": norms_dev(torch, mix["vor"], ref["vor"], va[:, None]),
+           "theta": norms_dev(torch, th_m, th_r, ca[:, None] * dpi_r)}
+    if "w" in mix:
+        out["w"] = norms_dev(torch, mix["w"], ref["w"], ca[:, None])
+    E = max(max(out["ps"]), max(out["vorticity"]))
+    out["E"] = E
+    out["E_le_alpha_0.05"] = bool(E <= 0.05)
+    return out
+
+
+def secondary_line(G, torch, name, args, device, dist):
+    """A further benchmark configuration (hydrostatic L6 or non-hydrostatic
+    L8 dycore): the mixed and the FP64 step side by side, W untimed and K
+    timed steps each, inputs resident on the device."""
+    wl = WORKLOADS[name]
+    from grist_inputs import states as S
+    m, mesh, host, P = setup_case(G, torch, wl, S.SEED, device)
+    nC, nE, L = mesh.nC, mesh.nE, wl["L"]
+    res = {"workload": wl["desc"], "unit": UNIT}
+    for prec in (args.prec, "fp64"):
+        s = make_state(torch, host, prec, device, nE, nC, L, 0, wl["nh"])
+        for _ in range(args.warmup):
+            step(mesh, s, P, wl, prec)
+        secs = reduce_max(timed(torch, lambda: step(mesh, s, P, wl, prec), args.steps, dist), dist, device)
+        res[prec] = {"ms_per_step": secs / args.steps * 1e3, "value": nC * L * args.steps / secs,
+                     "status_flags": mesh.last_status()}
+        del s
+        torch.cuda.empty_cache()
+    res["speedup_mix_over_fp64"] = res["fp64"]["ms_per_step"] / res[args.prec]["ms_per_step"]
+    mesh.close()
+    return res
 
 
 def batched_ensemble(G, torch, device, args, dist):
@@ -505,64 +690,80 @@ def batched_ensemble(G, torch, device, args, dist):
 # ---------------------------------------------------------------------------
 # CPU oracle (baseline / reference arm)
 
-def oracle_step_rate(wl, level, steps=1):
-    """Time the FP64 CPU oracle on `steps` steps of the workload's physics on
-    the given mesh level; returns (cell-level-steps/s, threads, sample)."""
-    import oracle as O
-    from grist_inputs import states as S
-    from grist_inputs.mesh import get_mesh
-    m = get_mesh(level)
-    M = O.Mesh(m)
-    L, T = wl["L"], wl["T"]
-    st = S.dycore_jet_case(m, L, nonhydrostatic=wl["nh"], bubble=wl["nh"])
-    P = O.Params(L, st["b_int"], st["pi_top"], st["phi_s"])
-    q = S.tracer_mixture(m, T, L, np.random.default_rng(S.SEED + 7)) if T else None
-    s = st
-    t0 = time.perf_counter()
-    for _ in range(steps):
+class OracleCase:
+    """The workload's physics on a given mesh level for the FP64 CPU oracle:
+    mesh, state and parameters built once; step() advances one coupled step
+    (dycore accumulating the horizontal and vertical mass fluxes, then the
+    tracers' horizontal and vertical transport) and times only that."""
+
+    def __init__(self, wl, level):
+        import oracle as O
+        from grist_inputs import states as S
+        from grist_inputs.mesh import get_mesh
+        self.O, self.wl = O, wl
+        self.m = m = get_mesh(level)
+        self.M = O.Mesh(m)
+        self.L, self.T = wl["L"], wl["T"]
+        self.st = S.dycore_jet_case(m, self.L, nonhydrostatic=wl["nh"], bubble=wl["nh"])
+        self.P = O.Params(self.L, self.st["b_int"], self.st["pi_top"], self.st["phi_s"])
+        self.q = S.tracer_mixture(m, self.T, self.L, np.random.default_rng(S.SEED + 7)) if self.T else None
+        self.s = dict(self.st)
+        self.level = level
+        self.units = m["n_cells"] * self.L
+
+    def step(self):
+        """One oracle step; returns its wall time in seconds."""
+        O, wl, m, L, st = self.O, self.wl, self.m, self.L, self.st
+        s = self.s
+        t0 = time.perf_counter()
         fa = np.zeros((m["n_edges"], L))
         va = np.zeros((m["n_cells"], L + 1))
         if wl["nh"]:
-            s2 = O.dycore_step_nh(M, P, s, wl["dt"], flux_accum=fa, vflux_accum=va)
+            s2 = O.dycore_step_nh(self.M, self.P, s, wl["dt"], flux_accum=fa, vflux_accum=va)
         else:
-            s2 = O.dycore_step_hydro(M, P, s, wl["dt"], flux_accum=fa, vflux_accum=va)
-        if T:
+            s2 = O.dycore_step_hydro(self.M, self.P, s, wl["dt"], flux_accum=fa, vflux_accum=va)
+        if self.T:
             pint = st["pi_top"] + st["b_int"][None, :] * (s["ps"][:, None] - st["pi_top"])
             dpi = np.diff(pint, axis=1)
-            q = O.tracer_step(M, q, dpi, fa, wl["dt"])
-            q = O.tracer_vertical_step(q, dpi - wl["dt"] * O.divergence(M, fa), va, wl["dt"], 1.0)
-        s = dict(s, **{k: s2[k] for k in s2 if k != "accum_weight"})
-    secs = time.perf_counter() - t0
-    sample = "%d step(s) of the same %s physics on the level-%d mesh (%d cells x %d levels)" % (
-        steps, "NH dycore + %d tracers" % T if wl["nh"] else "HDC", level, m["n_cells"], L)
-    return m["n_cells"] * L * steps / secs, O.num_threads(), sample
+            q = O.tracer_step(self.M, self.q, dpi, fa, wl["dt"])
+            self.q = O.tracer_vertical_step(q, dpi - wl["dt"] * O.divergence(self.M, fa), va, wl["dt"], 1.0)
+        self.s = dict(s, **{k: s2[k] for k in s2 if k != "accum_weight"})
+        return time.perf_counter() - t0
+
+    def sample(self, steps):
+        return "%d step(s) of the same %s physics on the level-%d mesh (%d cells x %d levels), timed per step " \
+               "(mesh and state built once, outside the timing)" % (
+                   steps, "NH dycore + %d tracers" % self.T if self.wl["nh"] else "HDC", self.level,
+                   self.m["n_cells"], self.L)
 
 
-def cpu_baseline(wl, level):
-    rate, cores, sample = oracle_step_rate(wl, level)
-    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+def cpu_baseline(wl, level, steps=1):
+    c = OracleCase(wl, level)
+    secs = sum(c.step() for _ in range(steps))
+    return {"value": c.units * steps / secs, "unit": UNIT, "cores": c.O.num_threads(), "kind": "oracle",
+            "sample": c.sample(steps), "ms_per_step": secs / steps * 1e3}
 
 
 def reference_arm(args, wl):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    level = args.ref_level
+    c = OracleCase(wl, args.ref_level)
     for _ in range(args.warmup):
-        oracle_step_rate(wl, level)
-    rates = []
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        r, cores, sample = oracle_step_rate(wl, level)
-        rates.append(r)
-    secs = time.perf_counter() - t0
-    value = statistics.median(rates)
+        c.step()
+    secs = sum(c.step() for _ in range(args.steps))
+    value = c.units * args.steps / secs
+    sample = c.sample(args.steps)
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": wl["desc"], "precision": "fp64 oracle"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "data": "synthetic",
+        "config": {"workload": "%s; timed on a bounded sample: the level-%d mesh (%d cells), %d levels" % (
+                       wl["phys"], c.level, c.m["n_cells"], c.L),
+                   "full_workload": wl["desc"], "precision": "fp64 oracle"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": c.O.num_threads(), "kind": "oracle",
+                         "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
@@ -579,11 +780,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="default tracer launch configuration")
+    ap.add_argument("--no-fp64-peak", action="store_true", help="skip the FP64 FMA-rate measurement")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the L6 hydrostatic and L8 NH lines")
     ap.add_argument("--split", type=int, default=3,
                     help="dycore steps per tracer step of the time-splitting measurement (1 = skip it)")
     ap.add_argument("--mesh-level", type=int, default=None,
                     help="override the workload's mesh level (small cases for profiling)")
     ap.add_argument("--cpu-level", type=int, default=8)
+    ap.add_argument("--cpu-steps", type=int, default=1,
+                    help="oracle steps of the cpu_baseline sample (4 at --cpu-level 9 is the level-9 subset)")
     ap.add_argument("--ref-level", type=int, default=7)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":
@@ -592,7 +797,7 @@ def main():
     wl = dict(WORKLOADS[args.workload])
     if args.mesh_level is not None:
         wl["level"] = args.mesh_level
-        wl["desc"] = wl["desc"].split(",")[0] + ", level-%d mesh (profiling case)" % args.mesh_level
+        wl["desc"] = wl["phys"] + ", level-%d mesh (profiling case)" % args.mesh_level
     if args.impl == "reference":
         reference_arm(args, wl)
     else:

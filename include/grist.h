@@ -386,6 +386,18 @@ int grist_profile_enable(grist_mesh mesh, int enable);
 int grist_profile_read(grist_mesh mesh, int32_t max_entries, char *names, int32_t *launches, double *total_ms,
                        int32_t *n_entries);
 
+/* FP64 throughput probe: launch `blocks` x `threads` threads (threads a
+ * multiple of 32, at most 1024), each running GRIST_BENCH_FP64_CHAINS
+ * independent chains of `iters` fused multiply-adds in double precision,
+ * and write one double per thread to out (device, [blocks * threads], the
+ * chains' sums, so the work cannot be optimised away).  FP64 flop per
+ * launch = 2 * GRIST_BENCH_FP64_CHAINS * iters * blocks * threads; timing
+ * the launch with events on `stream` gives the GPU's FP64 FMA rate, the
+ * measured peak of the FP64-pipe roofline.  Asynchronous; GRIST_EINVAL for
+ * sizes out of range (iters in 1..2^40, blocks in 1..2^20). */
+#define GRIST_BENCH_FP64_CHAINS 8
+int grist_bench_fp64_fma(int64_t iters, int32_t blocks, int32_t threads, double *out, void *stream);
+
 /* ---------------------------------------------------------------------- */
 /* Allocation-free weighted sum (no counterpart in the paper)              */
 /* ---------------------------------------------------------------------- */
@@ -396,8 +408,10 @@ int grist_profile_read(grist_mesh mesh, int32_t max_entries, char *names, int32_
 #define GRIST_NOALLOC_MAX_TERMS (4096 * 65536)
 
 /* sum_i w[i] * x[i] (w NULL: sum_i x[i]) over n device doubles, with the
- * same compensated, fixed-order summation as grist_global_sums, without
- * allocating any memory.  For callers that cannot allocate device memory:
+ * compensated method of grist_global_sums (Neumaier accumulation plus a
+ * TwoSum tree) in a fixed order of its own - bitwise reproducible run to
+ * run, but not bitwise equal to grist_global_sums - without allocating any
+ * memory.  For callers that cannot allocate device memory:
  * programs whose device memory is owned by another allocator that reserves
  * it up front, and code that must not pay the device-wide synchronisation a
  * cudaMalloc / cudaFree can imply.  No mesh handle is needed.
@@ -410,9 +424,10 @@ int grist_profile_read(grist_mesh mesh, int32_t max_entries, char *names, int32_
  * kept until the process exits) that every call shares: calls whose GPU
  * work overlaps race on it, so serialise them.  Each call writes every
  * partial it reads, so nothing needs clearing between calls.  The first
- * call on a device looks up the array's address with that device current;
- * make that first call before any stream capture.  Uses the current device
- * (cudaSetDevice). */
+ * call on a device looks up the array's address with that device current
+ * and keeps it for the life of the process (a cudaDeviceReset in between
+ * would invalidate it); make that first call before any stream capture.
+ * Uses the current device (cudaSetDevice). */
 int grist_weighted_sum_noalloc(const double *x, const double *w, int64_t n, double *out_sum_and_err, void *stream);
 
 /* ---------------------------------------------------------------------- */

@@ -77,6 +77,20 @@ def selftest_reciprocal(n=1 << 28, seed=2404_08849):
     return int(c.value), int(b.value), int(w.value)
 
 
+FP64_FMA_CHAINS = 8   # GRIST_BENCH_FP64_CHAINS
+
+
+def bench_fp64_fma(out, iters, blocks, threads=256, stream=None):
+    """grist_bench_fp64_fma: enqueue the FP64 FMA throughput kernel on
+    `stream` (default: the current stream).  out: CUDA float64 tensor of at
+    least blocks * threads elements.  Returns the FP64 flop of the launch."""
+    lib = _lib.load()
+    assert out.dtype.itemsize == 8 and out.numel() >= blocks * threads and out.is_cuda
+    _lib.check("grist_bench_fp64_fma", lib.grist_bench_fp64_fma(int(iters), int(blocks), int(threads), _ptr(out),
+                                                                _stream_handle(stream)))
+    return 2 * FP64_FMA_CHAINS * int(iters) * int(blocks) * int(threads)
+
+
 class Mesh:
     """Device copy of one icosahedral Voronoi mesh (``grist_mesh_create``)."""
 

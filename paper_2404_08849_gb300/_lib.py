@@ -79,6 +79,7 @@ EXPORTS = {
     "grist_tracer_autotune": ([_V, _P(TracerBatch), _D, _I, _V, _P(TracerTuning), _P(_D)], ctypes.c_int),
     "grist_selftest_bounded_wait": ([_V, ctypes.c_int64, _V], ctypes.c_int),
     "grist_weighted_sum_noalloc": ([_V, _V, ctypes.c_int64, _V, _V], ctypes.c_int),
+    "grist_bench_fp64_fma": ([ctypes.c_int64, _I, _I, _V, _V], ctypes.c_int),
     "grist_selftest_conversions": ([ctypes.c_uint64, ctypes.c_uint64, _P(ctypes.c_uint64), _P(ctypes.c_uint64)],
                                    ctypes.c_int),
     "grist_selftest_split": ([ctypes.c_uint64, ctypes.c_uint64, _P(ctypes.c_uint64), _P(ctypes.c_uint64)],
