@@ -48,13 +48,9 @@ WORKLOADS = {
 }
 
 
-def algorithmic_bytes(name, nC, nE, nV, L, T, prec, tiled=True, fct=True):
+def algorithmic_bytes(name, nC, nE, nV, L, T, prec):
     """Compulsory bytes of one launch: every array the kernel declares read
-    or written once (stencil re-reads, padding and index tables excluded).
-    tiled: the tracer step ran the tiled stages (whose continuity pass also
-    writes the {dpi, div F} pairs and the binary32 flux); fct: with the
-    limiter (two tiled stage launches per step, else three)."""
-    n_stage = 2 if fct else 3
+    or written once (stencil re-reads, padding and index tables excluded)."""
     base = name.split("/")[0]
     sU = sA = sM = 8
     if prec in ("mix", "mix_dbl_mass", "mix_df"):
@@ -70,24 +66,20 @@ def algorithmic_bytes(name, nC, nE, nV, L, T, prec, tiled=True, fct=True):
         "k_hydro_diag": nC * 8 + CL * 8 + 3 * CL * 8,
         "k_vort": EL * sU + nC * 8 + VL * sA,
         "k_ke": EL * sU + CL * 8,
-        "k_pv_edge": VL * sA + EL * sA,
-        "k_momentum": 2 * EL * sU + EL * sM + EL * sA + CL * 8 + CI * 8 + nC * 8 + 4 * CL * 8 + EL * sU,
+        # u_s, u_n, F, vertex PV (edge PV formed in the kernel), K, M, 1/sum,
+        # p, alpha, layer phi, dp/dpi, u_out
+        "k_momentum": 2 * EL * sU + EL * sM + VL * sA + CL * 8 + CI * 8 + nC * 8 + 4 * CL * 8 + EL * sU,
         "k_eos": CL * 8 + CI * 8 + CL * 8,
         "k_nh_explicit": EL * sU + 2 * nC * 8 + CI * 8 + 4 * CI * 8 + CL * 8 + 2 * CI * 8,
         "k_nh_solve": 2 * CI * 8 + CL * 8 + nC * 8 + 2 * CI * 8 + 4 * CL * 8,
         "k_add_scalar": 16,
         "k_vertex_mass": nC * 8 + nV * 8,
-        "k_tr_div": EL * 8 + CL * 8 + (CL * 8 + 2 * CL * sC + (EL * sC if sC == 4 else 0) if tiled else 0),
-        # tiled stages (mean per launch over the step's launches): q_in, q^n,
-        # q_out (+ the copy of q^n in the first stage), binary32 flux, {dpi, div F}
-        "k_trt_stage": (3 + 1.0 / n_stage) * T * CL * sQ + EL * sC + 2 * CL * sC,
-        "k_trt_fct_a": 2 * T * CL * sQ + EL * sC + 2 * CL * sC + 2 * T * CL * sC,
-        "k_trt_fct_b": 2 * T * CL * sQ + 2 * T * CL * sC + EL * sC + 2 * CL * sC + T * CL * sQ,
-        "k_tr_edge": T * CL * sQ + EL * 8 + T * EL * sC,
+        "k_tr_div": EL * 8 + CL * 8 + (EL * 4 if sC == 4 else 0),       # + the binary32 flux copy
+        "k_tr_edge": T * CL * sQ + EL * sC + T * EL * sC,
         "k_tr_update": T * EL * sC + T * CL * sQ + 2 * CL * 8 + T * CL * sQ,
-        "k_tr_lowres": T * CL * sQ + EL * 8 + 2 * CL * 8 + T * CL * sQ,
-        "k_tr_ratios": 2 * T * CL * sQ + T * EL * sC + EL * 8 + 2 * CL * 8 + 2 * T * CL * sC,
-        "k_tr_final": T * CL * sQ + T * EL * sC + EL * 8 + 2 * CL * 8 + 2 * T * CL * sC + T * CL * sQ,
+        "k_tr_lowres": T * CL * sQ + EL * sC + 2 * CL * 8 + T * CL * sQ,
+        "k_tr_ratios": 2 * T * CL * sQ + T * EL * sC + EL * sC + 2 * CL * 8 + 2 * T * CL * sC,
+        "k_tr_final": T * CL * sQ + T * EL * sC + EL * sC + 2 * CL * 8 + 2 * T * CL * sC + T * CL * sQ,
         "k_tr_copy": 2 * T * CL * sQ,
         "k_tr_vertical": 2 * CL * 8 + CI * 8 + 2 * T * CL * sQ,
     }
@@ -468,9 +460,8 @@ def gpu_arm(args, wl):
         "derived: %d SMs x %d DFMA/clk x 2 flop x %.0f MHz" % (SM_COUNT, DFMA_PER_SM_CLK, sm_max))
     fp64_table = FP64_WORK_MIX if args.prec != "fp64" else {}
     kernels = []
-    tiled = any(k.startswith("k_trt_") for k in prof_mix)
     for name, (launches, ms) in sorted(prof_mix.items(), key=lambda kv: -kv[1][1]):
-        b = algorithmic_bytes(name, nC, nE, nV, L, T, args.prec, tiled=tiled)
+        b = algorithmic_bytes(name, nC, nE, nV, L, T, args.prec)
         avg = ms / max(launches, 1)
         row = {"kernel": name, "launches": launches, "total_ms": round(ms, 3),
                "avg_ms": round(avg, 4), "share": None,
@@ -506,7 +497,7 @@ def gpu_arm(args, wl):
                         "traffic": (int(w[2] * units) if w and w[2] is not None else None),
                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per unit on the "
                                           "level-7 case, times this launch's units",
-                        "algorithmic_bytes": algorithmic_bytes(dom["kernel"], nC, nE, nV, L, T, args.prec, tiled=tiled),
+                        "algorithmic_bytes": algorithmic_bytes(dom["kernel"], nC, nE, nV, L, T, args.prec),
                         "work": "algorithmic FP64 flop per launch %.4g (%.1f per unit, from the formulas)%s" % (
                             per_unit * units, per_unit,
                             ("; executed %.1f per unit (ncu), %.4g TFLOP/s executed" % (w[1], dom["fp64_exec_tflops"]))

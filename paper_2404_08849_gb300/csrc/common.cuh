@@ -47,6 +47,13 @@ struct DevMesh {
     const int32_t *d2i;   // [nE][2][7] pad: centre cell
     const double *d2c;    // [nE][2][7]
     const float *d2c_f;
+    // Upwind-side edge value in one weighted sum (beta = 1):
+    // q_e = sum_j d2w[e][s][j] q(d2i[e][s][j]), d2w = -2 (dc^2/12) d2c with
+    // 1/2 added on the entries of c1 and c2; d2w_ok = 0 when some stencil
+    // lacks c1 or c2 (then the separate form is used).
+    const double *d2w;    // [nE][2][7]
+    const float *d2w_f;
+    int d2w_ok;
     const int32_t *eoe;   // [nE][10] pad: e itself
     const double *wpv;    // [nE][10]
     const float *wpv_f;
@@ -113,6 +120,7 @@ template <typename T> struct Coef;
 template <> struct Coef<double> {
     static __device__ __forceinline__ const double *cdiv(const DevMesh &m) { return m.cdiv; }
     static __device__ __forceinline__ const double *d2c(const DevMesh &m) { return m.d2c; }
+    static __device__ __forceinline__ const double *d2w(const DevMesh &m) { return m.d2w; }
     static __device__ __forceinline__ const double *dc2(const DevMesh &m) { return m.dc2; }
     static __device__ __forceinline__ const double *wpv(const DevMesh &m) { return m.wpv; }
     static __device__ __forceinline__ const double *ccurl(const DevMesh &m) { return m.ccurl; }
@@ -121,6 +129,7 @@ template <> struct Coef<double> {
 template <> struct Coef<float> {
     static __device__ __forceinline__ const float *cdiv(const DevMesh &m) { return m.cdiv_f; }
     static __device__ __forceinline__ const float *d2c(const DevMesh &m) { return m.d2c_f; }
+    static __device__ __forceinline__ const float *d2w(const DevMesh &m) { return m.d2w_f; }
     static __device__ __forceinline__ const float *dc2(const DevMesh &m) { return m.dc2_f; }
     static __device__ __forceinline__ const float *wpv(const DevMesh &m) { return m.wpv_f; }
     static __device__ __forceinline__ const float *ccurl(const DevMesh &m) { return m.ccurl_f; }

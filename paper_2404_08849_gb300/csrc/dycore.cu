@@ -444,17 +444,14 @@ __global__ void k_ke(DevMesh m, DyPar d, LevelDiv Dv, const typename P::TU *__re
     K[(size_t)i * d.ld + k] = P::DF ? pack_split(s) : emu<P::EMU>(s, d.emu, GRIST_ROW_KE_GRAD);
 }
 
+// PV at edge-level (e, k): the mean of the PV at the edge's two vertices.
 template <class P>
-__global__ void k_pv_edge(DevMesh m, DyPar d, LevelDiv Dv, const typename P::TA *__restrict__ qv,
-                          typename P::TA *__restrict__ qe) {
+__device__ __forceinline__ typename P::TA pv_at_edge(const DevMesh &m, const DyPar &d,
+                                                     const typename P::TA *__restrict__ qv, int e, int k) {
     using TA = typename P::TA;
-    uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= (uint32_t)m.nE * (uint32_t)d.L) return;
-    int e, k;
-    split_index(n, Dv, e, k);
     const int2 v = ldg(m.voe + e);
-    qe[(size_t)e * d.ld + k] =
-        emu<P::EMU>((TA)0.5 * (ldg(qv + (size_t)v.x * d.ld + k) + ldg(qv + (size_t)v.y * d.ld + k)), d.emu, GRIST_ROW_PV_FLUX);
+    return emu<P::EMU>((TA)0.5 * (ldg(qv + (size_t)v.x * d.ld + k) + ldg(qv + (size_t)v.y * d.ld + k)), d.emu,
+                       GRIST_ROW_PV_FLUX);
 }
 
 // Eq. 5 momentum tendency and stage update:
@@ -468,7 +465,7 @@ __global__ void k_pv_edge(DevMesh m, DyPar d, LevelDiv Dv, const typename P::TA 
 template <class P, bool NH>
 __global__ void k_momentum(DevMesh m, DyPar d, LevelDiv Dv, const typename P::TU *__restrict__ u_s,
                            const typename P::TU *u_n, typename P::TU *u_out, const typename P::TM *__restrict__ F,
-                           const typename P::TA *__restrict__ qe, const double *__restrict__ K,
+                           const typename P::TA *__restrict__ qv, const double *__restrict__ K,
                            const double *__restrict__ Mv, const double *__restrict__ rsum_e,
                            const double *__restrict__ p, const double *__restrict__ al,
                            const double *__restrict__ phl, const double *__restrict__ dpp, double dts,
@@ -481,13 +478,16 @@ __global__ void k_momentum(DevMesh m, DyPar d, LevelDiv Dv, const typename P::TU
     split_index(n, Dv, e, k);
     const size_t x = (size_t)e * d.ld + k;
     const int2 c = ldg(m.coe + e);
-    const TA qee = ldg(qe + x);
+    // the edge PV values come from the vertex PV (the mean of the two
+    // vertices, formed here: this kernel is bound by the FP64 pipe and has
+    // load slots to spare, so no separate edge-PV pass is needed)
+    const TA qee = pv_at_edge<P>(m, d, qv, e, k);
     TA pv = 0;
 #pragma unroll
     for (int j = 0; j < GRIST_MAXEOE; j++) {
         const int e2 = ldg(m.eoe + e * 10 + j);
         const size_t y = (size_t)e2 * d.ld + k;
-        pv += ldg(Coef<TA>::wpv(m) + e * 10 + j) * cv<TA>(ldg(F + y)) * ((TA)0.5 * (qee + ldg(qe + y)));
+        pv += ldg(Coef<TA>::wpv(m) + e * 10 + j) * cv<TA>(ldg(F + y)) * ((TA)0.5 * (qee + pv_at_edge<P>(m, d, qv, e2, k)));
     }
     const size_t a1 = (size_t)c.x * d.ld + k, a2 = (size_t)c.y * d.ld + k;
     if (P::DF) {
@@ -897,7 +897,7 @@ int dycore_step(grist_mesh_s *h, grist_dycore_state *S, const grist_dycore_param
     const size_t o_F = take(nEL * sizeof(TM)), o_M = take(nCI * 8);
     const size_t o_theta = take(nCL * sizeof(TA)), o_Fth = take(nEL * sizeof(TA));
     const size_t o_p = take(nCL * 8), o_al = take(nCL * 8), o_phl = take(nCL * 8), o_dpp = take(nCL * 8);
-    const size_t o_qv = take(nVL * sizeof(TA)), o_qe = take(nEL * sizeof(TA)), o_K = take(nCL * 8);
+    const size_t o_qv = take(nVL * sizeof(TA)), o_K = take(nCL * 8);
     size_t o_wA = 0, o_wB = 0, o_phA = 0, o_phB = 0, o_wst = 0, o_phst = 0, o_pn = 0, o_fw = 0, o_rth = 0;
     if (NH) {
         o_wA = take(nCI * 8); o_wB = take(nCI * 8); o_phA = take(nCI * 8); o_phB = take(nCI * 8);
@@ -949,7 +949,7 @@ int dycore_step(grist_mesh_s *h, grist_dycore_state *S, const grist_dycore_param
     TA *theta = (TA *)(s + o_theta), *Fth = (TA *)(s + o_Fth);
     double *p = (double *)(s + o_p), *alp = (double *)(s + o_al), *phl = (double *)(s + o_phl),
            *dpp = (double *)(s + o_dpp);
-    TA *qv = (TA *)(s + o_qv), *qe = (TA *)(s + o_qe);
+    TA *qv = (TA *)(s + o_qv);
     double *K = (double *)(s + o_K);
     double *wA = (double *)(s + o_wA), *wB = (double *)(s + o_wB), *phA = (double *)(s + o_phA),
            *phB = (double *)(s + o_phB), *wst = (double *)(s + o_wst), *phst = (double *)(s + o_phst),
@@ -1016,9 +1016,8 @@ int dycore_step(grist_mesh_s *h, grist_dycore_state *S, const grist_dycore_param
         GRIST_LAUNCH(h, PN("k_vertex_mass"), st, k_vertex_mass<P::EMU><<<gVx, kBlock, 0, st>>>(m, d, ps_in, rdpv));
         GRIST_LAUNCH(h, PN("k_vort"), st, k_vort<P><<<gV, kBlock, 0, st>>>(m, d, DL, u_in, rdpv, qv));
         GRIST_LAUNCH(h, PN("k_ke"), st, k_ke<P><<<gC, kBlock, 0, st>>>(m, d, DL, u_in, K));
-        GRIST_LAUNCH(h, PN("k_pv_edge"), st, k_pv_edge<P><<<gE, kBlock, 0, st>>>(m, d, DL, qv, qe));
         GRIST_LAUNCH(h, PN("k_momentum"), st, k_momentum<P, NH><<<gE, kBlock, 0, st>>>(
-            m, d, DL, u_in, u, u_outs[s3], F, qe, K, Mv, rsum, p_outs[s3], alp, phl, dpp, h3, status));
+            m, d, DL, u_in, u, u_outs[s3], F, qv, K, Mv, rsum, p_outs[s3], alp, phl, dpp, h3, status));
         u_in = u_outs[s3];
         ps_in = ps_outs[s3];
         th_in = th_outs[s3];

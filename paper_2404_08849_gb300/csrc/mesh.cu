@@ -302,6 +302,9 @@ extern "C" int grist_mesh_create(const grist_mesh_desc *desc, int device, grist_
     std::vector<double> rdc(nE), hrdc(nE), dc2(nE), d2c(14 * (size_t)nE), wpv(10 * (size_t)nE);
     std::vector<float> dc2_f(nE), d2c_f(14 * (size_t)nE), wpv_f(10 * (size_t)nE);
     std::vector<int32_t> d2i(14 * (size_t)nE), eoe(10 * (size_t)nE);
+    std::vector<double> d2w(14 * (size_t)nE);
+    std::vector<float> d2w_f(14 * (size_t)nE);
+    int d2w_ok = 1;
     for (int e = 0; e < nE; e++) {
         int o = eold[e];
         coe[e] = make_int2(cn[desc->cells_on_edge[2 * o]], cn[desc->cells_on_edge[2 * o + 1]]);
@@ -320,6 +323,19 @@ extern "C" int grist_mesh_create(const grist_mesh_desc *desc, int device, grist_
                 d2c[x] = c >= 0 ? desc->d2_coef[(2 * o + s) * GRIST_D2P + j] : 0.0;
                 d2c_f[x] = (float)d2c[x];
             }
+            // combined weights: the mean of the edge's two cells folded into
+            // the upwind side's stencil (first entry of each cell)
+            const size_t b0 = ((size_t)e * 2 + s) * GRIST_D2P;
+            for (int j = 0; j < GRIST_D2P; j++) d2w[b0 + j] = -2.0 * dc2[e] * d2c[b0 + j];
+            const int ends[2] = {coe[e].x, coe[e].y};
+            for (int q = 0; q < 2; q++) {
+                int at = -1;
+                for (int j = 0; j < GRIST_D2P && at < 0; j++)
+                    if (d2i[b0 + j] == ends[q]) at = j;
+                if (at < 0) d2w_ok = 0;
+                else d2w[b0 + at] += 0.5;
+            }
+            for (int j = 0; j < GRIST_D2P; j++) d2w_f[b0 + j] = (float)d2w[b0 + j];
         }
         int n = desc->n_edges_on_edge[o];
         for (int j = 0; j < GRIST_MAXEOE; j++) {
@@ -361,6 +377,7 @@ extern "C" int grist_mesh_create(const grist_mesh_desc *desc, int device, grist_
            o_hrdc = ar.add(hrdc.size() * 8),
            o_dc2 = ar.add(dc2.size() * 8), o_dc2f = ar.add(dc2_f.size() * 4), o_d2i = ar.add(d2i.size() * 4),
            o_d2c = ar.add(d2c.size() * 8), o_d2cf = ar.add(d2c_f.size() * 4), o_eoe = ar.add(eoe.size() * 4),
+           o_d2w = ar.add(d2w.size() * 8), o_d2wf = ar.add(d2w_f.size() * 4),
            o_wpv = ar.add(wpv.size() * 8), o_wpvf = ar.add(wpv_f.size() * 4), o_eov = ar.add(eov.size() * 4),
            o_cov = ar.add(cov.size() * 4), o_ccurl = ar.add(ccurl.size() * 8), o_ccurlf = ar.add(ccurl_f.size() * 4),
            o_ckite = ar.add(ckite.size() * 8), o_fv = ar.add(fv.size() * 8);
@@ -374,6 +391,7 @@ extern "C" int grist_mesh_create(const grist_mesh_desc *desc, int device, grist_
     put(o_hrdc, hrdc.data(), hrdc.size() * 8);
     put(o_dc2f, dc2_f.data(), dc2_f.size() * 4); put(o_d2i, d2i.data(), d2i.size() * 4);
     put(o_d2c, d2c.data(), d2c.size() * 8); put(o_d2cf, d2c_f.data(), d2c_f.size() * 4);
+    put(o_d2w, d2w.data(), d2w.size() * 8); put(o_d2wf, d2w_f.data(), d2w_f.size() * 4);
     put(o_eoe, eoe.data(), eoe.size() * 4); put(o_wpv, wpv.data(), wpv.size() * 8);
     put(o_wpvf, wpv_f.data(), wpv_f.size() * 4); put(o_eov, eov.data(), eov.size() * 4);
     put(o_cov, cov.data(), cov.size() * 4); put(o_ccurl, ccurl.data(), ccurl.size() * 8);
@@ -402,6 +420,7 @@ extern "C" int grist_mesh_create(const grist_mesh_desc *desc, int device, grist_
     D.rdc = place<double>(dev, o_rdc); D.hrdc = place<double>(dev, o_hrdc);
     D.dc2 = place<double>(dev, o_dc2); D.dc2_f = place<float>(dev, o_dc2f);
     D.d2i = place<int32_t>(dev, o_d2i); D.d2c = place<double>(dev, o_d2c); D.d2c_f = place<float>(dev, o_d2cf);
+    D.d2w = place<double>(dev, o_d2w); D.d2w_f = place<float>(dev, o_d2wf); D.d2w_ok = d2w_ok;
     D.eoe = place<int32_t>(dev, o_eoe); D.wpv = place<double>(dev, o_wpv); D.wpv_f = place<float>(dev, o_wpvf);
     D.eov = place<int32_t>(dev, o_eov); D.cov = place<int32_t>(dev, o_cov);
     D.ccurl = place<double>(dev, o_ccurl); D.ccurl_f = place<float>(dev, o_ccurlf);

@@ -37,6 +37,7 @@ struct MemberDev {
     void *qA, *qB;          // scratch stage tracers [T][nC][ld]
     void *FH;               // scratch edge fluxes [T][nE][ld]
     void *Rp, *Rm;          // scratch FCT ratios [T][nC][ld]
+    const void *Ff;         // mass flux in the compute type [nE][ld]: a binary32 copy (scratch) or F itself
     int L, T, ld, pad;
     const double *Mv;       // time-mean vertical mass flux [nC][ldi] or null (no vertical step)
     int ldi;
@@ -163,13 +164,31 @@ template <> __device__ __forceinline__ float tiny_of<float>() { return 1.1754943
 // ---------------------------------------------------------------------------
 // phase bodies (one work item each)
 
-// Tracer continuity of the member: divF = div(mass flux), FP64.
+// Tracer continuity of the member: divF = div(mass flux), FP64.  In the
+// binary32 policy each edge's flux is also rounded once to binary32 for the
+// later phases (by the cell it leaves: positive divergence coefficient), so
+// they read 4 bytes per edge-level instead of 8.
+template <typename TC>
 __device__ __forceinline__ void item_div(const DevMesh &m, const MemberDev &mb, int i, int k) {
     double s = 0.0;
 #pragma unroll
-    for (int j = 0; j < GRIST_MAXE; j++)
-        s += ldg(m.cdiv + i * 6 + j) * ldg(mb.F + (size_t)ldg(m.eoc + i * 6 + j) * mb.ld + k);
+    for (int j = 0; j < GRIST_MAXE; j++) {
+        const int e = ldg(m.eoc + i * 6 + j);
+        const double cw = ldg(m.cdiv + i * 6 + j);
+        const double f = ldg(mb.F + (size_t)e * mb.ld + k);
+        s += cw * f;
+        if (sizeof(TC) == 4 && cw > 0.0) ((float *)mb.Ff)[(size_t)e * mb.ld + k] = cv<float>(f);
+    }
     mb.divF[(size_t)i * mb.ld + k] = s;
+}
+
+// Mass flux of edge-level x in the compute type: the binary32 copy made by
+// the continuity phase (read coherently inside the persistent launch, which
+// wrote it), or the caller's FP64 array.
+template <bool PERS, typename TC>
+__device__ __forceinline__ TC flux_at(const MemberDev &mb, size_t x) {
+    if (sizeof(TC) == 4) return (TC)lds<PERS>((const float *)mb.Ff + x);
+    return (TC)ldg(mb.F + x);
 }
 
 // Third-order upwind edge flux (Skamarock-Gassmann form):
@@ -181,12 +200,31 @@ __device__ __forceinline__ void item_edge(const DevMesh &m, const MemberDev &mb,
                                           int e, int k, bool beta1, TC beta) {
     const int ld = mb.ld;
     const int2 c = ldg(m.coe + e);
-    const TC f = static_cast<TC>(ldg(mb.F + (size_t)e * ld + k));
+    const TC f = flux_at<PERS, TC>(mb, (size_t)e * ld + k);
     const TC dc2 = ldg(Coef<TC>::dc2(m) + e);
     const int32_t *st = m.d2i + (size_t)e * 14;
     const TC *cf = Coef<TC>::d2c(m) + (size_t)e * 14;
     TC *FH = (TC *)mb.FH;
-    if (beta1) {
+    if (beta1 && m.d2w_ok) {
+        // one weighted sum over the upwind side's stencil (the mean of c1 and
+        // c2 folded into the weights)
+        const int side = f >= (TC)0 ? 0 : 1;
+        const TC *cw = Coef<TC>::d2w(m) + (size_t)e * 14 + side * GRIST_D2P;
+        int idx[GRIST_D2P];
+        TC w[GRIST_D2P];
+#pragma unroll
+        for (int j = 0; j < GRIST_D2P; j++) {
+            idx[j] = ldg(st + side * GRIST_D2P + j);
+            w[j] = ldg(cw + j);
+        }
+        for (int t = t0; t < t1; t++) {
+            const TQ *qt = q + (size_t)t * mb.qs;
+            TC v = 0;
+#pragma unroll
+            for (int j = 0; j < GRIST_D2P; j++) v += w[j] * static_cast<TC>(lds<PERS>(qt + (size_t)idx[j] * ld + k));
+            FH[(size_t)t * mb.fs + (size_t)e * ld + k] = f * v;
+        }
+    } else if (beta1) {
         const int side = f >= (TC)0 ? 0 : 1;
         int idx[GRIST_D2P];
         TC w[GRIST_D2P];
@@ -280,7 +318,7 @@ __device__ __forceinline__ void item_lowres(const DevMesh &m, const MemberDev &m
         const int e = ldg(m.eoc + i * 6 + j);
         nb[j] = ldg(m.coc + i * 6 + j);
         cw[j] = ldg(Coef<TC>::cdiv(m) + i * 6 + j);
-        fe[j] = static_cast<TC>(ldg(mb.F + (size_t)e * ld + k));
+        fe[j] = flux_at<PERS, TC>(mb, (size_t)e * ld + k);
     }
     const TQ *qn = (const TQ *)mb.q;
     TQ *qtd = (TQ *)mb.qA;
@@ -310,7 +348,7 @@ __device__ __forceinline__ void item_ratios(const DevMesh &m, const MemberDev &m
         eidx[j] = ldg(m.eoc + i * 6 + j);
         nb[j] = ldg(m.coc + i * 6 + j);
         cw[j] = ldg(Coef<TC>::cdiv(m) + i * 6 + j);
-        fe[j] = static_cast<TC>(ldg(mb.F + (size_t)eidx[j] * ld + k));
+        fe[j] = flux_at<PERS, TC>(mb, (size_t)eidx[j] * ld + k);
     }
     const TQ *qn = (const TQ *)mb.q, *qtd = (const TQ *)mb.qA;
     const TC *FH = (const TC *)mb.FH;
@@ -362,7 +400,7 @@ __device__ __forceinline__ bool item_final(const DevMesh &m, const MemberDev &mb
         eidx[j] = ldg(m.eoc + i * 6 + j);
         nb[j] = ldg(m.coc + i * 6 + j);
         cw[j] = ldg(Coef<TC>::cdiv(m) + i * 6 + j);
-        fe[j] = static_cast<TC>(ldg(mb.F + (size_t)eidx[j] * ld + k));
+        fe[j] = flux_at<PERS, TC>(mb, (size_t)eidx[j] * ld + k);
     }
     const TQ *qn = (const TQ *)mb.q;
     const TC *FH = (const TC *)mb.FH;
@@ -423,7 +461,7 @@ __device__ void run_phase(const DevMesh &m, const Batch &B, uint32_t *status) {
         split_index((uint32_t)(n - S.start[seg]), mb.DL, ent, k);
         const int t0 = mg.y * B.tpt;
         const int t1 = min(mb.T, t0 + B.tpt);
-        if (PH == P_DIV) item_div(m, mb, ent, k);
+        if (PH == P_DIV) item_div<TC>(m, mb, ent, k);
         if (PH == P_EDGE0) item_edge<PERS, TQ, TC>(m, mb, (const TQ *)mb.q, t0, t1, ent, k, B.beta1, beta);
         if (PH == P_EDGE1) item_edge<PERS, TQ, TC>(m, mb, (const TQ *)mb.qA, t0, t1, ent, k, B.beta1, beta);
         if (PH == P_EDGE2) item_edge<PERS, TQ, TC>(m, mb, (const TQ *)mb.qB, t0, t1, ent, k, B.beta1, beta);
@@ -593,132 +631,138 @@ __global__ void __launch_bounds__(256) k_tr_tile_stage(DevMesh m, TileMesh tm, B
 //   dpi+_k q+_k + dt (Fi_{k+1} - Fi_k) = dpi*_k q_k - dt (Fe_{k+1} - Fe_k),
 //   dpi*_k = dpi_k - dt div(F)_k (the horizontal step's end),
 //   dpi+_k = dpi*_k - dt (M_{k+1} - M_k),
-// a tridiagonal M-matrix system solved by the Thomas algorithm.  One thread
-// per column, blocks of one warp (32 columns); the column data moves
-// through shared memory in 4-level chunks (whole 32-byte sectors for
-// doubles); the flux split is formed once per column and shared by the
-// member's tracers.  Arithmetic in the tracer compute type.
-constexpr int kVertKC = 4;
-constexpr int kVertRow = 33;
-
+// a tridiagonal M-matrix system solved by the Thomas algorithm.  Arithmetic
+// in the tracer compute type.
 __device__ __forceinline__ double vinv(double x) { return rcp(x); }   // correctly rounded, as 1.0 / x
 __device__ __forceinline__ float vinv(float x) { return 1.0f / x; }
 
-template <typename T>
-__device__ __forceinline__ void vstage_in(const T *X, size_t S, int col0, int ncol, int k0, int nk, T *sm) {
-    const int lane = threadIdx.x & 31, kk = lane % kVertKC;
-#pragma unroll
-    for (int it = 0; it < kVertKC; it++) {
-        const int col = it * (32 / kVertKC) + lane / kVertKC;
-        T v = (T)0;
-        if (col < ncol && kk < nk) v = X[(size_t)(col0 + col) * S + k0 + kk];
-        sm[kk * kVertRow + col] = v;
-    }
-}
+// One warp per column, lanes over levels (level k = lane + 32 r, r < R;
+// R = 2 up to 64 levels, else 4).  Each lane forms the flux split
+// at the two interfaces of its layers (an interface shared by two layers is
+// split by both from the same operands, so identically).  When no interface
+// of the column has an implicit share (every Courant number <= cmax, the
+// usual case) the tridiagonal system is diagonal: the Thomas sweep then
+// reduces exactly to q+_k = rhs_k * (1 / b_k), which every lane evaluates for
+// its own levels in parallel.  Otherwise the rows go through shared memory
+// and one lane runs the Thomas sweep of the column; the diagonal case is
+// exactly what that sweep computes when the off-diagonals vanish.
+constexpr int kVertWarps = 8;
 
-template <typename T>
-__device__ __forceinline__ void vstage_out(T *X, size_t S, int col0, int ncol, int k0, int nk, const T *sm) {
-    const int lane = threadIdx.x & 31, kk = lane % kVertKC;
-#pragma unroll
-    for (int it = 0; it < kVertKC; it++) {
-        const int col = it * (32 / kVertKC) + lane / kVertKC;
-        if (col < ncol && kk < nk) X[(size_t)(col0 + col) * S + k0 + kk] = sm[kk * kVertRow + col];
-    }
-}
-
-template <typename TQ, typename TC>
-__global__ void __launch_bounds__(32) k_tr_vertical(DevMesh m, MemberDev mb, double dt, double cmax,
-                                                    uint32_t *status) {
-    __shared__ double sD[3][kVertKC * kVertRow];   // dpi, div F, M at the interface below
-    __shared__ TQ sQ[(kVertKC + 1) * kVertRow];    // q of a chunk and the level after it
-    const int lane = threadIdx.x;
-    const int col0 = blockIdx.x * 32;
-    const int ncol = min(32, m.nC - col0);
-    const int i = col0 + lane;
-    const bool act = lane < ncol;
+template <typename TQ, typename TC, int kVertR>
+__global__ void __launch_bounds__(kVertWarps * 32) k_tr_vertical(DevMesh m, MemberDev mb, double dt, double cmax,
+                                                                uint32_t *status) {
+    __shared__ TC sA[kVertWarps][kVertMaxL], sB[kVertWarps][kVertMaxL], sC[kVertWarps][kVertMaxL],
+        sD[kVertWarps][kVertMaxL];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * kVertWarps + warp;
+    if (i >= m.nC) return;   // whole warps only: no block barrier below
     const int L = mb.L, ld = mb.ld, ldi = mb.ldi;
     const TC dtc = cv<TC>(dt), cm = cv<TC>(cmax);
-    TC me[kVertMaxL + 1], mi[kVertMaxL + 1], dps[kVertMaxL], cp[kVertMaxL], dd[kVertMaxL];
-    // pass 1: the flux split at every interface and the start layer mass
-    me[0] = mi[0] = (TC)0;
-    {
-        TC dps_prev = (TC)0, m_top = (TC)0;
-        for (int k0 = 0; k0 < L; k0 += kVertKC) {
-            const int nk = min(kVertKC, L - k0);
-            __syncwarp();
-            vstage_in(mb.dpi, (size_t)ld, col0, ncol, k0, nk, sD[0]);
-            vstage_in(mb.divF, (size_t)ld, col0, ncol, k0, nk, sD[1]);
-            vstage_in(mb.Mv, (size_t)ldi, col0, ncol, k0 + 1, nk, sD[2]);
-            __syncwarp();
-            if (act) {
-                for (int kk = 0; kk < nk; kk++) {
-                    const int k = k0 + kk, o = kk * kVertRow + lane;
-                    const TC ds = cv<TC>(sD[0][o] - dt * sD[1][o]);
-                    dps[k] = ds;
-                    // interface k (top of layer k): donor k-1 when M_k > 0, else k
-                    if (k > 0 && m_top != (TC)0) {
-                        const TC cour = fabs(m_top) * dtc / (m_top > (TC)0 ? dps_prev : ds);
-                        const TC f = cour <= cm ? (TC)1 : cm / cour;
-                        me[k] = f * m_top;
-                        mi[k] = m_top - me[k];
-                    } else if (k > 0) {
-                        me[k] = mi[k] = (TC)0;
-                    }
-                    dps_prev = ds;
-                    m_top = (k + 1 < L) ? cv<TC>(sD[2][o]) : (TC)0;   // M at the bottom of layer k
-                }
-            }
+    const size_t row = (size_t)i * ld, irow = (size_t)i * ldi;
+    auto dstar = [&](int kk) -> TC { return cv<TC>(mb.dpi[row + kk] - dt * mb.divF[row + kk]); };
+    // interface j between layers j-1 (above) and j (below), with those
+    // layers' start masses: explicit and implicit shares
+    auto split = [&](int j, TC above, TC below, TC &me, TC &mi) {
+        const TC Mj = (j > 0 && j < L) ? cv<TC>(mb.Mv[irow + j]) : (TC)0;
+        me = mi = (TC)0;
+        if (Mj != (TC)0) {
+            const TC cour = fabs(Mj) * dtc / (Mj > (TC)0 ? above : below);
+            const TC f = cour <= cm ? (TC)1 : cm / cour;
+            me = f * Mj;
+            mi = Mj - me;
         }
-        me[L] = mi[L] = (TC)0;
-        (void)m_top;
+    };
+    TC dps[kVertR], met[kVertR], mit[kVertR], meb[kVertR], mib[kVertR], a[kVertR], b[kVertR], c[kVertR];
+    bool implicit = false;
+#pragma unroll
+    for (int r = 0; r < kVertR; r++) {
+        const int k = lane + 32 * r;
+        dps[r] = met[r] = mit[r] = meb[r] = mib[r] = a[r] = c[r] = (TC)0;
+        b[r] = (TC)1;
+        if (k < L) {
+            const TC d0 = dstar(k);
+            const TC dm = k > 0 ? dstar(k - 1) : (TC)0, dp = k + 1 < L ? dstar(k + 1) : (TC)0;
+            dps[r] = d0;
+            split(k, dm, d0, met[r], mit[r]);
+            split(k + 1, d0, dp, meb[r], mib[r]);
+            const TC Mt = met[r] + mit[r], Mb = meb[r] + mib[r];
+            const TC dpn = d0 - dtc * (Mb - Mt);
+            a[r] = -dtc * fmax_((TC)0, mit[r]);
+            b[r] = dpn + dtc * (fmax_((TC)0, mib[r]) - fmin_((TC)0, mit[r]));
+            c[r] = dtc * fmin_((TC)0, mib[r]);
+            implicit |= (mit[r] != (TC)0) | (mib[r] != (TC)0);
+        }
     }
-    // pass 2, per tracer: explicit share from q, then the implicit system
+    implicit = __any_sync(0xffffffffu, implicit);
+    TC rb[kVertR];
+#pragma unroll
+    for (int r = 0; r < kVertR; r++) rb[r] = vinv(b[r]);
     bool bad = false;
     for (int t = 0; t < mb.T; t++) {
-        TQ *qt = (TQ *)mb.q + (size_t)t * mb.qs;
-        TC q_prev = (TC)0;
-        for (int k0 = 0; k0 < L; k0 += kVertKC) {
-            const int nk = min(kVertKC, L - k0);
-            __syncwarp();
-            vstage_in(qt, (size_t)ld, col0, ncol, k0, nk, sQ);
-            if (act) sQ[kVertKC * kVertRow + lane] = (k0 + nk < L) ? qt[(size_t)i * ld + k0 + nk] : (TQ)0;
-            __syncwarp();
-            if (act) {
-                for (int kk = 0; kk < nk; kk++) {
-                    const int k = k0 + kk, o = kk * kVertRow + lane;
-                    const TC qk = (TC)sQ[o];
-                    const TC qn = (TC)(kk + 1 < nk ? sQ[o + kVertRow] : sQ[kVertKC * kVertRow + lane]);
-                    // donor values at the top (k) and bottom (k + 1) interfaces
-                    const TC Mt = me[k] + mi[k], Mb = me[k + 1] + mi[k + 1];
-                    const TC q_top = Mt > (TC)0 ? q_prev : qk;
-                    const TC q_bot = Mb > (TC)0 ? qk : qn;
-                    const TC dpn = dps[k] - dtc * (Mb - Mt);
-                    const TC rhs = dps[k] * qk - dtc * (me[k + 1] * q_bot - me[k] * q_top);
-                    const TC a = -dtc * fmax_((TC)0, mi[k]);
-                    const TC b = dpn + dtc * (fmax_((TC)0, mi[k + 1]) - fmin_((TC)0, mi[k]));
-                    const TC c = dtc * fmin_((TC)0, mi[k + 1]);
-                    const TC rden = vinv(k == 0 ? b : b - a * cp[k - 1]);
-                    cp[k] = c * rden;
-                    dd[k] = (k == 0 ? rhs : rhs - a * dd[k - 1]) * rden;
-                    q_prev = qk;
-                }
+        TQ *qt = (TQ *)mb.q + (size_t)t * mb.qs + row;
+        TC rhs[kVertR];
+#pragma unroll
+        for (int r = 0; r < kVertR; r++) {
+            const int k = lane + 32 * r;
+            rhs[r] = (TC)0;
+            if (k < L) {
+                const TC qk = (TC)qt[k];
+                const TC qm = k > 0 ? (TC)qt[k - 1] : (TC)0, qp = k + 1 < L ? (TC)qt[k + 1] : (TC)0;
+                const TC Mt = met[r] + mit[r], Mb = meb[r] + mib[r];
+                const TC q_top = Mt > (TC)0 ? qm : qk;
+                const TC q_bot = Mb > (TC)0 ? qk : qp;
+                rhs[r] = dps[r] * qk - dtc * (meb[r] * q_bot - met[r] * q_top);
             }
         }
-        // back substitution, bottom to top, written chunk by chunk
-        TC qb = (TC)0;
-        for (int k0 = ((L - 1) / kVertKC) * kVertKC; k0 >= 0; k0 -= kVertKC) {
-            const int nk = min(kVertKC, L - k0);
-            __syncwarp();
-            if (act) {
-                for (int kk = nk - 1; kk >= 0; kk--) {
-                    const int k = k0 + kk;
-                    qb = (k == L - 1) ? dd[k] : dd[k] - cp[k] * qb;
-                    bad |= !isfinite(qb);
-                    sQ[kk * kVertRow + lane] = (TQ)qb;
+        __syncwarp();   // every lane has read the column before any lane writes it
+        if (!implicit) {
+#pragma unroll
+            for (int r = 0; r < kVertR; r++) {
+                const int k = lane + 32 * r;
+                if (k < L) {
+                    const TC x = rhs[r] * rb[r];
+                    bad |= !isfinite(x);
+                    qt[k] = (TQ)x;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < kVertR; r++) {
+                const int k = lane + 32 * r;
+                if (k < L) {
+                    sA[warp][k] = a[r];
+                    sB[warp][k] = b[r];
+                    sC[warp][k] = c[r];
+                    sD[warp][k] = rhs[r];
                 }
             }
             __syncwarp();
-            vstage_out(qt, (size_t)ld, col0, ncol, k0, nk, sQ);
+            if (lane == 0) {
+                // Thomas sweep (forward elimination into sC / sD, back
+                // substitution into sD), the arithmetic of k_tr_vertical
+                for (int k = 0; k < L; k++) {
+                    const TC rden = vinv(k == 0 ? sB[warp][k] : sB[warp][k] - sA[warp][k] * sC[warp][k - 1]);
+                    const TC cpk = sC[warp][k] * rden;
+                    sD[warp][k] = (k == 0 ? sD[warp][k] : sD[warp][k] - sA[warp][k] * sD[warp][k - 1]) * rden;
+                    sC[warp][k] = cpk;
+                }
+                TC qb = (TC)0;
+                for (int k = L - 1; k >= 0; k--) {
+                    qb = (k == L - 1) ? sD[warp][k] : sD[warp][k] - sC[warp][k] * qb;
+                    sD[warp][k] = qb;
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int r = 0; r < kVertR; r++) {
+                const int k = lane + 32 * r;
+                if (k < L) {
+                    const TC x = sD[warp][k];
+                    bad |= !isfinite(x);
+                    qt[k] = (TQ)x;
+                }
+            }
+            __syncwarp();   // the next tracer reuses the rows
         }
     }
     if (bad) atomicOr(status, GRIST_FLAG_NONFINITE);
@@ -846,6 +890,7 @@ int plan_batch(const DevMesh &m, const grist_tracer_batch *b, int tpt, HostPlan 
         d.FH = (void *)(uintptr_t)off; off += al256(bf);
         d.Rp = (void *)(uintptr_t)off; off += al256(br);
         d.Rm = (void *)(uintptr_t)off; off += al256(br);
+        if (sizeof(TC) == 4) { d.Ff = (const void *)(uintptr_t)off; off += al256(d.fs * sizeof(float)); }
         const int idx = (int)P.mem.size();
         const int G = (d.T + tpt - 1) / tpt;
         P.sD.push_back(tD); P.mD.push_back(make_int2(idx, 0));
@@ -883,6 +928,7 @@ int upload_plan(grist_mesh_s *h, TracerCtx *c, HostPlan &P, const grist_tracer_b
         d.FH = scr + (uintptr_t)d.FH;
         d.Rp = scr + (uintptr_t)d.Rp;
         d.Rm = scr + (uintptr_t)d.Rm;
+        d.Ff = sizeof(TC) == 4 ? (const void *)(scr + (uintptr_t)d.Ff) : (const void *)d.F;
     }
     const size_t nm = P.mem.size();
     size_t o = 0;
@@ -1051,9 +1097,15 @@ int enqueue_step(grist_mesh_s *h, TracerCtx *c, const Batch &B, cudaStream_t st)
     const MemberDev *hm = reinterpret_cast<const MemberDev *>(c->htab.data());
     for (int j = 0; j < B.nm; j++) {
         if (!hm[j].Mv) continue;
-        GRIST_LAUNCH(h, sizeof(TC) == 4 ? "k_tr_vertical/mix" : "k_tr_vertical/fp64", st,
-                     k_tr_vertical<TQ, TC><<<grid_for(m.nC, 32), 32, 0, st>>>(m, hm[j], B.dt, B.cmax,
-                                                                              status_word(h)));
+        const unsigned gv = grid_for(m.nC, kVertWarps);
+        if (hm[j].L <= 64)
+            GRIST_LAUNCH(h, sizeof(TC) == 4 ? "k_tr_vertical/mix" : "k_tr_vertical/fp64", st,
+                         (k_tr_vertical<TQ, TC, 2><<<gv, kVertWarps * 32, 0, st>>>(m, hm[j], B.dt, B.cmax,
+                                                                                   status_word(h))));
+        else
+            GRIST_LAUNCH(h, sizeof(TC) == 4 ? "k_tr_vertical/mix" : "k_tr_vertical/fp64", st,
+                         (k_tr_vertical<TQ, TC, kVertMaxL / 32><<<gv, kVertWarps * 32, 0, st>>>(
+                             m, hm[j], B.dt, B.cmax, status_word(h))));
     }
     return cudaGetLastError() == cudaSuccess ? GRIST_OK : GRIST_ECUDA;
 }
