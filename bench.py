@@ -370,7 +370,11 @@ def gpu_arm(args, wl):
     fp64_peak = None if args.no_fp64_peak else measure_fp64_peak(G, torch, device)
     finals = {}
 
+    side = torch.cuda.Stream(device)   # a created stream: the step graph is captured on it
+    launch_mode = {}
+
     def run_prec(prec, sample_clocks=False):
+      with torch.cuda.stream(side):
         s = make_state(torch, host, prec, device, nE, nC, L, T, wl["nh"])
         for w in range(W):
             step(mesh, s, P, wl, prec)
@@ -381,11 +385,22 @@ def gpu_arm(args, wl):
                     [{"q": s["q"], "dpi": s["dpi_start"], "mass_flux": s["mass_flux_accum"],
                       "vmass_flux": s["vmass_flux_accum"], "n_levels": L}], wl["dt"], prec=prec, steps=2)[0]
         torch.cuda.synchronize()
+        # the timed steps: replays of one captured coupled step (the
+        # library's whole-step graph), else the calls one by one
+        graph = None
+        if not args.eager:
+            try:
+                graph = G.capture(lambda: step(mesh, s, P, wl, prec), side)
+            except G.GristError:
+                graph = None
+        launch_mode[prec] = "CUDA graph of one coupled step, replayed" if graph else "library calls per step"
         cs = ClockSampler(device) if sample_clocks else None
         if cs:
             cs.start()
-        secs = timed(torch, lambda: step(mesh, s, P, wl, prec), K, dist)
+        secs = timed(torch, (graph.launch if graph else (lambda: step(mesh, s, P, wl, prec))), K, dist)
         clocks = cs.stop() if cs else None
+        if graph:
+            graph.close()
         status = mesh.last_status()
         # per-kernel event timing over a second pass of K steps
         mesh.profile(True)
@@ -555,6 +570,7 @@ def gpu_arm(args, wl):
                "vs_baseline": None, "dtype": "mixed f32/f64" if args.prec != "fp64" else "f64",
                "data": "synthetic (seeded jet + perturbation + warm bubble, tracer mixture)",
                "config": {"workload": wl["desc"], "precision": args.prec, "n_cells": nC, "n_edges": nE,
+                          "launch": launch_mode,
                           "n_levels": L, "n_tracers": T, "dt_s": wl["dt"],
                           "l2_policy": "inputs larger than L2 (state >> 129 MB), no flush",
                           "tracer_tuning": tunings or "library default",
@@ -622,12 +638,20 @@ def secondary_line(G, torch, name, args, device, dist):
     m, mesh, host, P = setup_case(G, torch, wl, S.SEED, device)
     nC, nE, L = mesh.nC, mesh.nE, wl["L"]
     res = {"workload": wl["desc"], "unit": UNIT}
+    side = torch.cuda.Stream(device)
     for prec in (args.prec, "fp64"):
+      with torch.cuda.stream(side):
         s = make_state(torch, host, prec, device, nE, nC, L, 0, wl["nh"])
         for _ in range(args.warmup):
             step(mesh, s, P, wl, prec)
-        secs = reduce_max(timed(torch, lambda: step(mesh, s, P, wl, prec), args.steps, dist), dist, device)
+        secs_e = reduce_max(timed(torch, lambda: step(mesh, s, P, wl, prec), args.steps, dist), dist, device)
+        graph = None if args.eager else G.capture(lambda: step(mesh, s, P, wl, prec), side)
+        secs = (reduce_max(timed(torch, graph.launch, args.steps, dist), dist, device) if graph else secs_e)
+        if graph:
+            graph.close()
         res[prec] = {"ms_per_step": secs / args.steps * 1e3, "value": nC * L * args.steps / secs,
+                     "eager_ms_per_step": secs_e / args.steps * 1e3,
+                     "launch": "CUDA graph of one step" if graph else "library calls per step",
                      "status_flags": mesh.last_status()}
         del s
         torch.cuda.empty_cache()
@@ -773,6 +797,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="default tracer launch configuration")
     ap.add_argument("--no-fp64-peak", action="store_true", help="skip the FP64 FMA-rate measurement")
     ap.add_argument("--no-secondary", action="store_true", help="skip the L6 hydrostatic and L8 NH lines")
+    ap.add_argument("--eager", action="store_true",
+                    help="time the library calls step by step instead of a captured step graph")
     ap.add_argument("--split", type=int, default=3,
                     help="dycore steps per tracer step of the time-splitting measurement (1 = skip it)")
     ap.add_argument("--mesh-level", type=int, default=None,

@@ -221,20 +221,25 @@ int grist_tracer_step(grist_mesh mesh, const grist_tracer_batch *batch, double d
  *   fused               1 = RK stages without the limiter run as one tiled
  *                       kernel each (edge fluxes of a tile of cells kept in
  *                       shared memory, never written to global memory);
- *                       ignored when persistent = 1. */
+ *                       ignored when persistent = 1.
+ *   levels_per_thread   1 or 2: levels one thread of a per-phase launch
+ *                       carries (levels g and g + ceil(L/2) for 2; the
+ *                       entity's stencil tables are read once for both);
+ *                       the persistent launch uses 1. */
 typedef struct {
-    int32_t block, tracers_per_thread, persistent, use_graph, fused;
+    int32_t block, tracers_per_thread, persistent, use_graph, fused, levels_per_thread;
 } grist_tracer_tuning;
 
 /* Set / get the tuning used by later grist_tracer_step calls on the mesh
  * (default: block 256, tracers_per_thread 4, persistent 0, use_graph 0,
- * fused 0).
+ * fused 0, levels_per_thread 1).
  * GRIST_EINVAL for out-of-range values. */
 int grist_tracer_set_tuning(grist_mesh mesh, const grist_tracer_tuning *tuning);
 int grist_tracer_get_tuning(grist_mesh mesh, grist_tracer_tuning *tuning);
 
-/* Autotuner: time candidate tunings (block sizes, tracers per thread,
- * fused tiles on/off, per-phase vs persistent launch, graph on/off) on
+/* Autotuner: time candidate tunings (block sizes - hence cells per block -
+ * tracers per thread, fused tiles on/off, then levels per thread at the
+ * best of those, then per-phase vs persistent launch and graph on/off) on
  * `steps` tracer steps of
  * the given batch, keep the fastest as the mesh's tuning and return it in
  * *best (and its mean step time in milliseconds in *best_ms, may be NULL).
@@ -347,6 +352,44 @@ int grist_dycore_step_nh(grist_mesh mesh, grist_dycore_state *state, const grist
  * Asynchronous on `stream`. */
 int grist_diag_vorticity(grist_mesh mesh, const void *u, grist_precision u_prec, int32_t n_levels, int32_t ld,
                          double *vor, void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* Whole-step CUDA graphs (no counterpart in the paper)                    */
+/* ---------------------------------------------------------------------- */
+
+/* Record everything enqueued on `stream` between grist_capture_begin and
+ * grist_capture_end - e.g. one coupled model step: a dycore step and the
+ * tracer step that uses its fluxes - as one CUDA graph, and replay it with
+ * grist_graph_launch: one launch per step on the host instead of one per
+ * kernel.  Rules:
+ *   - `stream` must be a created stream (not the legacy default stream);
+ *     capture runs in thread-local mode.
+ *   - Make every recorded call once before capturing it: first calls size
+ *     the handle's scratch and upload tables (allocations and copies that a
+ *     capture cannot hold).
+ *   - A replay repeats the recorded calls with the recorded arguments
+ *     (buffers, sizes, dt, precision, tuning, and host-side choices such as
+ *     a carried NH pressure being valid); capture again when one changes.
+ *     The handle's scratch must not grow after the capture (make the
+ *     largest call first), the dycore's vertical grid (b_interface) must be
+ *     the one recorded, and a handle keeps the work-list tables of its last
+ *     64 distinct tracer batches: a graph that recorded a tracer step of a
+ *     batch dropped since then must be recorded again.  A tracer step of a
+ *     batch the handle has not run outside a capture returns
+ *     GRIST_EUNSUPPORTED inside the capture.  Keep per-kernel profiling
+ *     (grist_profile_enable) off while capturing.
+ *   - The steps enqueued while capturing do not run; the graph runs them.
+ * grist_capture_end returns GRIST_ECUDA when the capture failed (e.g. a
+ * recorded call needed an allocation); the stream is then no longer
+ * capturing. */
+typedef struct grist_graph_s *grist_graph;
+int grist_capture_begin(void *stream);
+int grist_capture_end(void *stream, grist_graph *out);
+/* Enqueue one replay of the graph on `stream` (asynchronous). */
+int grist_graph_launch(grist_graph graph, void *stream);
+/* Free the graph (NULL accepted); replays already enqueued are not waited
+ * for by this call - synchronise first. */
+int grist_graph_destroy(grist_graph graph);
 
 /* ---------------------------------------------------------------------- */
 /* Global sums (Sec. 2.3: global mass conserved to round-off)              */

@@ -77,6 +77,53 @@ def selftest_reciprocal(n=1 << 28, seed=2404_08849):
     return int(c.value), int(b.value), int(w.value)
 
 
+class StepGraph:
+    """A recorded sequence of library calls (grist_capture_begin/end),
+    replayed with launch(); see capture()."""
+
+    def __init__(self, handle, stream):
+        self.handle = handle
+        self.stream = stream
+
+    def launch(self):
+        _lib.check("grist_graph_launch", _lib.load().grist_graph_launch(self.handle, _stream_handle(self.stream)))
+
+    def close(self):
+        if self.handle:
+            _lib.load().grist_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def capture(fn, stream):
+    """Record the library calls fn() enqueues on `stream` (a created torch
+    CUDA stream, made current for the recording) into one CUDA graph and
+    return it as a StepGraph; fn's calls do not run now - the graph runs
+    them at each launch().  Make the same calls once before capturing them
+    (first calls allocate scratch and upload tables)."""
+    import torch
+    lib = _lib.load()
+    h = _stream_handle(stream)
+    with torch.cuda.stream(stream):
+        _lib.check("grist_capture_begin", lib.grist_capture_begin(h))
+        g = ctypes.c_void_p()
+        try:
+            fn()
+        except BaseException:
+            # end the capture and drop what was recorded
+            if lib.grist_capture_end(h, ctypes.byref(g)) == 0:
+                lib.grist_graph_destroy(g)
+            raise
+        rc = lib.grist_capture_end(h, ctypes.byref(g))
+    _lib.check("grist_capture_end", rc)
+    return StepGraph(g, stream)
+
+
 FP64_FMA_CHAINS = 8   # GRIST_BENCH_FP64_CHAINS
 
 
@@ -195,16 +242,17 @@ class Mesh:
         _lib.check("grist_tracer_step", lib.grist_tracer_step(self.handle, ctypes.byref(b), float(dt),
                                                               _stream_handle(stream)))
 
-    def set_tracer_tuning(self, block=256, tracers_per_thread=4, persistent=False, use_graph=False, fused=False):
+    def set_tracer_tuning(self, block=256, tracers_per_thread=4, persistent=False, use_graph=False, fused=False,
+                          levels_per_thread=1):
         t = _lib.TracerTuning(int(block), int(tracers_per_thread), int(bool(persistent)), int(bool(use_graph)),
-                              int(bool(fused)))
+                              int(bool(fused)), int(levels_per_thread))
         _lib.check("grist_tracer_set_tuning", _lib.load().grist_tracer_set_tuning(self.handle, ctypes.byref(t)))
 
     def tracer_tuning(self):
         t = _lib.TracerTuning()
         _lib.check("grist_tracer_get_tuning", _lib.load().grist_tracer_get_tuning(self.handle, ctypes.byref(t)))
         return {"block": t.block, "tracers_per_thread": t.tracers_per_thread, "persistent": bool(t.persistent),
-                "use_graph": bool(t.use_graph), "fused": bool(t.fused)}
+                "use_graph": bool(t.use_graph), "fused": bool(t.fused), "levels_per_thread": t.levels_per_thread}
 
     def autotune_tracer(self, members, dt, prec="mix", limiter=True, beta=1.0, steps=3, stream=None,
                         cache_path=None, cache_key=None):

@@ -46,7 +46,8 @@ class TracerBatch(ctypes.Structure):
 
 
 class TracerTuning(ctypes.Structure):
-    _fields_ = [("block", _I), ("tracers_per_thread", _I), ("persistent", _I), ("use_graph", _I), ("fused", _I)]
+    _fields_ = [("block", _I), ("tracers_per_thread", _I), ("persistent", _I), ("use_graph", _I), ("fused", _I),
+                ("levels_per_thread", _I)]
 
 
 class DycoreParams(ctypes.Structure):
@@ -80,6 +81,10 @@ EXPORTS = {
     "grist_selftest_bounded_wait": ([_V, ctypes.c_int64, _V], ctypes.c_int),
     "grist_weighted_sum_noalloc": ([_V, _V, ctypes.c_int64, _V, _V], ctypes.c_int),
     "grist_bench_fp64_fma": ([ctypes.c_int64, _I, _I, _V, _V], ctypes.c_int),
+    "grist_capture_begin": ([_V], ctypes.c_int),
+    "grist_capture_end": ([_V, _P(_V)], ctypes.c_int),
+    "grist_graph_launch": ([_V, _V], ctypes.c_int),
+    "grist_graph_destroy": ([_V], ctypes.c_int),
     "grist_selftest_conversions": ([ctypes.c_uint64, ctypes.c_uint64, _P(ctypes.c_uint64), _P(ctypes.c_uint64)],
                                    ctypes.c_int),
     "grist_selftest_split": ([ctypes.c_uint64, ctypes.c_uint64, _P(ctypes.c_uint64), _P(ctypes.c_uint64)],

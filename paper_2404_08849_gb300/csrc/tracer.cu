@@ -41,7 +41,8 @@ struct MemberDev {
     int L, T, ld, pad;
     const double *Mv;       // time-mean vertical mass flux [nC][ldi] or null (no vertical step)
     int ldi;
-    LevelDiv DL;            // division by L
+    LevelDiv DL;            // division by Lg
+    int Lg;                 // level groups: a thread takes levels g, g + Lg, ... (levels_per_thread of them)
     unsigned long long qs, fs;  // nC*ld, nE*ld
 };
 
@@ -73,14 +74,20 @@ struct TileMesh {
 };
 
 struct TracerCtx {
-    grist_tracer_tuning tune{256, 4, 0, 0, 0};
+    grist_tracer_tuning tune{256, 4, 0, 0, 0, 1};
     // tile tables (built on first use)
     char *dtile = nullptr;
     TileMesh tiles{};
-    // device tables (one allocation), host mirrors
-    char *dtab = nullptr;
-    size_t dtab_bytes = 0;
-    std::vector<char> htab;
+    // work-list tables (member descriptors, segment tables), one device copy
+    // per distinct batch, never rewritten: a step recorded in a graph keeps
+    // reading the table it was recorded with, whatever other batches run
+    // in between.  cur: the table of the last planned batch.
+    struct Table {
+        std::vector<char> host;
+        char *dev = nullptr;
+    };
+    std::vector<Table> tabs;
+    int cur = -1;
     unsigned *barrier = nullptr;  // [0] arrival count, [1] generation, [2] abort, [3] self-test word
     // graph cache: the last few captured steps, keyed by their signature
     // (buffers, sizes, dt, tuning, stream) - alternating buffer sets, as in
@@ -104,11 +111,13 @@ struct TracerCtx {
 };
 
 constexpr size_t kGraphCache = 4;
+constexpr size_t kTableCache = 64;   // distinct batches whose tables a handle keeps
 
 void tracer_ctx_free(TracerCtx *c) {
     if (!c) return;
     c->drop_graphs();
-    if (c->dtab) cudaFree(c->dtab);
+    for (auto &t : c->tabs)
+        if (t.dev) cudaFree(t.dev);
     if (c->dtile) cudaFree(c->dtile);
     if (c->barrier) cudaFree(c->barrier);
     delete c;
@@ -128,6 +137,7 @@ struct Batch {
     Space D, C, E;  // D: cell x level (no groups); C: cell x level x group; E: edge x level x group
     Space T;        // blocks of the fused stage kernel: segment start = first block of (member, group)
     int tpt;
+    int lpt;        // levels per thread of the work-list phases (1 or 2; the persistent launch takes 1)
     double dt;
     double dt3;     // dt / 3, the first RK stage (formed on the host)
     int fct;
@@ -445,7 +455,11 @@ __device__ __forceinline__ void item_copy(const MemberDev &mb, int t0, int t1, i
 
 enum Phase { P_DIV = 0, P_EDGE0, P_UPD0, P_EDGE1, P_UPD1, P_EDGE2, P_UPD2, P_LOWRES, P_RATIOS, P_FINAL, P_COPY };
 
-template <bool PERS, typename TQ, typename TC, int PH>
+// One pass over a work space.  A work item is (entity, level group g) of a
+// member and tracer group; the thread takes the LPT levels g, g + Lg, ...
+// (Lg = ceil(L / LPT)), so consecutive threads still touch consecutive
+// levels, and the entity's tables are read once for its LPT levels.
+template <bool PERS, typename TQ, typename TC, int PH, int LPT = 1>
 __device__ void run_phase(const DevMesh &m, const Batch &B, uint32_t *status) {
     const Space &S = (PH == P_DIV) ? B.D : (PH == P_EDGE0 || PH == P_EDGE1 || PH == P_EDGE2) ? B.E : B.C;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
@@ -457,10 +471,14 @@ __device__ void run_phase(const DevMesh &m, const Batch &B, uint32_t *status) {
         seg = find_seg(S, n, seg);
         const int2 mg = S.mg[seg];
         const MemberDev &mb = B.mem[mg.x];
-        int ent, k;
-        split_index((uint32_t)(n - S.start[seg]), mb.DL, ent, k);
+        int ent, kg;
+        split_index((uint32_t)(n - S.start[seg]), mb.DL, ent, kg);
         const int t0 = mg.y * B.tpt;
         const int t1 = min(mb.T, t0 + B.tpt);
+#pragma unroll
+        for (int u = 0; u < LPT; u++) {
+        const int k = kg + u * mb.Lg;
+        if (LPT > 1 && k >= mb.L) break;
         if (PH == P_DIV) item_div<TC>(m, mb, ent, k);
         if (PH == P_EDGE0) item_edge<PERS, TQ, TC>(m, mb, (const TQ *)mb.q, t0, t1, ent, k, B.beta1, beta);
         if (PH == P_EDGE1) item_edge<PERS, TQ, TC>(m, mb, (const TQ *)mb.qA, t0, t1, ent, k, B.beta1, beta);
@@ -472,6 +490,7 @@ __device__ void run_phase(const DevMesh &m, const Batch &B, uint32_t *status) {
         if (PH == P_RATIOS) item_ratios<PERS, TQ, TC>(m, mb, t0, t1, ent, k, B.dt);
         if (PH == P_FINAL) bad |= item_final<PERS, TQ, TC>(m, mb, t0, t1, ent, k, B.dt);
         if (PH == P_COPY) item_copy<PERS, TQ>(mb, t0, t1, ent, k);
+        }
     }
     if (bad) atomicOr(status, GRIST_FLAG_NONFINITE);
 }
@@ -510,9 +529,9 @@ template <typename TC, int PH> constexpr int tracer_phase_regs() {
                                                                : kTracerRegLimit;
 }
 
-template <typename TQ, typename TC, int PH>
+template <typename TQ, typename TC, int PH, int LPT>
 __global__ void __maxnreg__((tracer_phase_regs<TC, PH>())) k_tracer_phase(DevMesh m, Batch B, uint32_t *status) {
-    run_phase<false, TQ, TC, PH>(m, B, status);
+    run_phase<false, TQ, TC, PH, LPT>(m, B, status);
 }
 
 // Fused RK stage (no limiter) on one tile x 32 levels x the tracers of one
@@ -861,7 +880,7 @@ struct HostPlan {
 };
 
 template <typename TQ, typename TC>
-int plan_batch(const DevMesh &m, const grist_tracer_batch *b, int tpt, HostPlan &P) {
+int plan_batch(const DevMesh &m, const grist_tracer_batch *b, int tpt, int lpt, HostPlan &P) {
     P = HostPlan();
     size_t off = 0;
     unsigned long long tD = 0, tC = 0, tE = 0, tT = 0;
@@ -878,7 +897,8 @@ int plan_batch(const DevMesh &m, const grist_tracer_batch *b, int tpt, HostPlan 
         d.ld = u.ld;
         d.Mv = u.vmass_flux;
         d.ldi = u.ld_int;
-        d.DL = make_div((uint32_t)u.n_levels);
+        d.Lg = (u.n_levels + lpt - 1) / lpt;
+        d.DL = make_div((uint32_t)d.Lg);
         d.qs = (unsigned long long)m.nC * u.ld;
         d.fs = (unsigned long long)m.nE * u.ld;
         // scratch offsets (relative, resolved after allocation)
@@ -894,12 +914,12 @@ int plan_batch(const DevMesh &m, const grist_tracer_batch *b, int tpt, HostPlan 
         const int idx = (int)P.mem.size();
         const int G = (d.T + tpt - 1) / tpt;
         P.sD.push_back(tD); P.mD.push_back(make_int2(idx, 0));
-        tD += (unsigned long long)m.nC * d.L;
+        tD += (unsigned long long)m.nC * d.Lg;
         for (int g = 0; g < G; g++) {
             P.sC.push_back(tC); P.mC.push_back(make_int2(idx, g));
-            tC += (unsigned long long)m.nC * d.L;
+            tC += (unsigned long long)m.nC * d.Lg;
             P.sE.push_back(tE); P.mE.push_back(make_int2(idx, g));
-            tE += (unsigned long long)m.nE * d.L;
+            tE += (unsigned long long)m.nE * d.Lg;
             P.sT.push_back(tT); P.mT.push_back(make_int2(idx, g));
             tT += ntiles * (unsigned long long)((d.L + 31) / 32);
         }
@@ -951,34 +971,46 @@ int upload_plan(grist_mesh_s *h, TracerCtx *c, HostPlan &P, const grist_tracer_b
     std::memcpy(ht.data() + o_mE, P.mE.data(), P.mE.size() * sizeof(int2));
     std::memcpy(ht.data() + o_sT, P.sT.data(), P.sT.size() * 8);
     std::memcpy(ht.data() + o_mT, P.mT.data(), P.mT.size() * sizeof(int2));
-    if (c->dtab_bytes < o) {
-        if (c->dtab) {
-            cudaDeviceSynchronize();
-            cudaFree(c->dtab);
-            c->dtab = nullptr;
+    int ti = -1;
+    for (size_t x = 0; x < c->tabs.size() && ti < 0; x++)
+        if (c->tabs[x].host.size() == o && std::memcmp(c->tabs[x].host.data(), ht.data(), o) == 0) ti = (int)x;
+    if (ti < 0) {
+        // a batch not seen before: its table is made outside any stream
+        // capture (a recorded step must have run once without capture)
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        GRIST_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+        if (cs != cudaStreamCaptureStatusNone) return GRIST_EUNSUPPORTED;
+        if (c->tabs.size() >= kTableCache) {
+            // drop the oldest table (and the tracer graphs, which may read it)
+            GRIST_CUDA_TRY(cudaDeviceSynchronize());
+            c->drop_graphs();
+            cudaFree(c->tabs.front().dev);
+            c->tabs.erase(c->tabs.begin());
         }
-        if (cudaMalloc(&c->dtab, o) != cudaSuccess) { c->dtab_bytes = 0; return GRIST_ENOMEM; }
-        c->dtab_bytes = o;
-        c->htab.clear();
+        TracerCtx::Table t;
+        if (cudaMalloc(&t.dev, o) != cudaSuccess) return GRIST_ENOMEM;
+        if (cudaMemcpy(t.dev, ht.data(), o, cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaFree(t.dev);
+            return GRIST_ECUDA;
+        }
+        t.host = ht;
+        c->tabs.push_back(std::move(t));
+        ti = (int)c->tabs.size() - 1;
     }
-    if (c->htab.size() != o || std::memcmp(c->htab.data(), ht.data(), o) != 0) {
-        // ordered on the step's stream after the kernels that read the old
-        // table; from pageable memory the call returns once the bytes are
-        // staged, so the host vector may go and no other stream waits
-        GRIST_CUDA_TRY(cudaMemcpyAsync(c->dtab, ht.data(), o, cudaMemcpyHostToDevice, st));
-        c->htab = ht;
-    }
+    c->cur = ti;
+    char *dtab = c->tabs[ti].dev;
     if (!c->barrier) {
         if (cudaMalloc(&c->barrier, 4 * sizeof(unsigned)) != cudaSuccess) return GRIST_ENOMEM;
         GRIST_CUDA_TRY(cudaMemset(c->barrier, 0, 4 * sizeof(unsigned)));
     }
-    B.mem = (const MemberDev *)(c->dtab + o_mem);
+    B.mem = (const MemberDev *)(dtab + o_mem);
     B.nm = (int)nm;
-    B.D = Space{(const unsigned long long *)(c->dtab + o_sD), (const int2 *)(c->dtab + o_mD), (int)P.mD.size(), P.sD.back()};
-    B.C = Space{(const unsigned long long *)(c->dtab + o_sC), (const int2 *)(c->dtab + o_mC), (int)P.mC.size(), P.sC.back()};
-    B.E = Space{(const unsigned long long *)(c->dtab + o_sE), (const int2 *)(c->dtab + o_mE), (int)P.mE.size(), P.sE.back()};
-    B.T = Space{(const unsigned long long *)(c->dtab + o_sT), (const int2 *)(c->dtab + o_mT), (int)P.mT.size(), P.sT.back()};
+    B.D = Space{(const unsigned long long *)(dtab + o_sD), (const int2 *)(dtab + o_mD), (int)P.mD.size(), P.sD.back()};
+    B.C = Space{(const unsigned long long *)(dtab + o_sC), (const int2 *)(dtab + o_mC), (int)P.mC.size(), P.sC.back()};
+    B.E = Space{(const unsigned long long *)(dtab + o_sE), (const int2 *)(dtab + o_mE), (int)P.mE.size(), P.sE.back()};
+    B.T = Space{(const unsigned long long *)(dtab + o_sT), (const int2 *)(dtab + o_mT), (int)P.mT.size(), P.sT.back()};
     B.tpt = c->tune.tracers_per_thread;
+    B.lpt = c->tune.persistent ? 1 : c->tune.levels_per_thread;
     B.dt = dt;
     B.dt3 = dt / 3.0;
     B.fct = b->limiter ? 1 : 0;
@@ -1068,7 +1100,10 @@ int enqueue_horizontal(grist_mesh_s *h, TracerCtx *c, const Batch &B, cudaStream
         const char *nm = sizeof(TC) == 4 ? names_f[ph] : names_d[ph];
         switch (ph) {
 #define GRIST_PHASE_CASE(P_) \
-    case P_: GRIST_LAUNCH(h, nm, st, k_tracer_phase<TQ, TC, P_><<<grid, block, 0, st>>>(m, B, status)); break;
+    case P_:                                                                                                   \
+        if (B.lpt == 2) GRIST_LAUNCH(h, nm, st, (k_tracer_phase<TQ, TC, P_, 2><<<grid, block, 0, st>>>(m, B, status))); \
+        else GRIST_LAUNCH(h, nm, st, (k_tracer_phase<TQ, TC, P_, 1><<<grid, block, 0, st>>>(m, B, status)));   \
+        break;
             GRIST_PHASE_CASE(P_DIV)
             GRIST_PHASE_CASE(P_EDGE0)
             GRIST_PHASE_CASE(P_UPD0)
@@ -1094,7 +1129,7 @@ int enqueue_step(grist_mesh_s *h, TracerCtx *c, const Batch &B, cudaStream_t st)
     int rc = enqueue_horizontal<TQ, TC>(h, c, B, st);
     if (rc != GRIST_OK) return rc;
     const DevMesh &m = dev_mesh(h);
-    const MemberDev *hm = reinterpret_cast<const MemberDev *>(c->htab.data());
+    const MemberDev *hm = reinterpret_cast<const MemberDev *>(c->tabs[c->cur].host.data());
     for (int j = 0; j < B.nm; j++) {
         if (!hm[j].Mv) continue;
         const unsigned gv = grid_for(m.nC, kVertWarps);
@@ -1200,7 +1235,7 @@ int tracer_step_t(grist_mesh_s *h, const grist_tracer_batch *b, double dt, cudaS
     TracerCtx *c = ctx_of(h);
     const DevMesh &m = dev_mesh(h);
     HostPlan P;
-    int rc = plan_batch<TQ, TC>(m, b, c->tune.tracers_per_thread, P);
+    int rc = plan_batch<TQ, TC>(m, b, c->tune.tracers_per_thread, c->tune.persistent ? 1 : c->tune.levels_per_thread, P);
     if (rc != GRIST_OK) return rc;
     Batch B;
     rc = upload_plan<TQ, TC>(h, c, P, b, dt, B, st);
@@ -1216,7 +1251,8 @@ int tracer_step_t(grist_mesh_s *h, const grist_tracer_batch *b, double dt, cudaS
     std::memcpy(&u, &b->vertical_courant_max, 8); sig.push_back(u);
     sig.push_back((unsigned long long)(uintptr_t)st);
     sig.push_back(((unsigned long long)c->tune.block << 32) | (unsigned)c->tune.tracers_per_thread);
-    sig.push_back((unsigned long long)c->tune.persistent);
+    sig.push_back((unsigned long long)c->tune.persistent | ((unsigned long long)c->tune.levels_per_thread << 8) |
+                  ((unsigned long long)c->tune.fused << 16));
     for (int i = 0; i < b->n_members; i++) {
         const grist_tracer_member &mm = b->members[i];
         sig.push_back((unsigned long long)(uintptr_t)mm.q);
@@ -1227,15 +1263,17 @@ int tracer_step_t(grist_mesh_s *h, const grist_tracer_batch *b, double dt, cudaS
         sig.push_back((unsigned long long)(uintptr_t)mm.vmass_flux);
         sig.push_back((unsigned long long)mm.ld_int);
     }
-    sig.push_back((unsigned long long)(uintptr_t)c->dtab);
+    sig.push_back((unsigned long long)(uintptr_t)c->tabs[c->cur].dev);
+    // inside a caller's capture (a whole-step graph) the kernels are
+    // recorded directly into that graph
+    cudaStreamCaptureStatus cs;
+    GRIST_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+    if (cs != cudaStreamCaptureStatusNone || st == nullptr) return enqueue_step<TQ, TC>(h, c, B, st);
     for (auto &ge : c->graphs)
         if (ge.sig == sig) {
             GRIST_CUDA_TRY(cudaGraphLaunch(ge.exec, st));
             return GRIST_OK;
         }
-    cudaStreamCaptureStatus cs;
-    GRIST_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
-    if (cs != cudaStreamCaptureStatusNone || st == nullptr) return enqueue_step<TQ, TC>(h, c, B, st);
     if (c->graph_failed && sig == c->failed_sig) return enqueue_step<TQ, TC>(h, c, B, st);
     GRIST_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     int erc = enqueue_step<TQ, TC>(h, c, B, st);
@@ -1296,6 +1334,7 @@ int check_tuning(const grist_tracer_tuning *t) {
     if (t->persistent != 0 && t->persistent != 1) return GRIST_EINVAL;
     if (t->use_graph != 0 && t->use_graph != 1) return GRIST_EINVAL;
     if (t->fused != 0 && t->fused != 1) return GRIST_EINVAL;
+    if (t->levels_per_thread != 1 && t->levels_per_thread != 2) return GRIST_EINVAL;
     return GRIST_OK;
 }
 
@@ -1400,10 +1439,20 @@ extern "C" int grist_tracer_autotune(grist_mesh h, const grist_tracer_batch *b, 
         for (int bl : blocks) {
             for (int tp : tpts) {
                 if (tp > 1 && tp / 2 >= maxT) continue;
-                grist_tracer_tuning t{bl, tp, 0, 0, fu};
+                grist_tracer_tuning t{bl, tp, 0, 0, fu, 1};
                 double ms = 0;
                 if (time_cfg(t, &ms) == GRIST_OK && ms < bestms) { bestms = ms; bestt = t; }
             }
+        }
+    }
+    // two levels per thread (work-list phases) at the best tracers per
+    // thread, every block size
+    {
+        const int tp = bestt.tracers_per_thread, fu = bestt.fused;
+        for (int bl : blocks) {
+            grist_tracer_tuning t{bl, tp, 0, 0, fu, 2};
+            double ms = 0;
+            if (time_cfg(t, &ms) == GRIST_OK && ms < bestms) { bestms = ms; bestt = t; }
         }
     }
     for (int pers = 0; pers <= 1; pers++) {
@@ -1412,7 +1461,10 @@ extern "C" int grist_tracer_autotune(grist_mesh h, const grist_tracer_batch *b, 
             grist_tracer_tuning t = bestt;
             t.persistent = pers;
             t.use_graph = gr;
-            if (pers) t.fused = 0;
+            if (pers) {
+                t.fused = 0;
+                t.levels_per_thread = 1;
+            }
             double ms = 0;
             if (time_cfg(t, &ms) == GRIST_OK && ms < bestms) { bestms = ms; bestt = t; }
         }

@@ -59,7 +59,9 @@ TUNINGS = [None,
            {"block": 256, "tracers_per_thread": 3, "fused": True},
            {"block": 256, "tracers_per_thread": 4, "persistent": True},
            {"block": 256, "tracers_per_thread": 2, "use_graph": True},
-           {"block": 256, "tracers_per_thread": 4, "persistent": True, "use_graph": True}]
+           {"block": 256, "tracers_per_thread": 4, "persistent": True, "use_graph": True},
+           {"block": 256, "tracers_per_thread": 4, "levels_per_thread": 2},
+           {"block": 512, "tracers_per_thread": 1, "levels_per_thread": 2, "use_graph": True}]
 
 
 @pytest.mark.parametrize("tuning", TUNINGS)
@@ -128,6 +130,7 @@ def test_autotune_keeps_caller_data_and_picks_valid_tuning(G, mesh_cache, tmp_pa
     cache = str(tmp_path / "tune.json")
     t, ms = mesh.autotune_tracer(dev, 300.0, prec="mix", steps=2, cache_path=cache, cache_key="L4-test")
     assert t["block"] in (128, 256, 512) and t["tracers_per_thread"] in (1, 2, 4, 8)
+    assert t["levels_per_thread"] in (1, 2)
     assert ms is not None and ms > 0
     for d, b in zip(dev, before):
         assert torch.equal(d["q"], b)
