@@ -577,7 +577,7 @@ def gpu_arm(args, wl):
                           "parallelism": "independent ensemble member per GPU" if world > 1 else "single GPU"},
                "fp64": ({"value": total_units / secs_64, "ms_per_step": secs_64 / K * 1e3,
                          "speedup_mix_over_fp64": secs_64 / secs_mix} if secs_64 else None),
-               "roofline": roofline, "kernels": kernels[:12], "gpu_launches": int(round(launches_per_step * K)),
+               "roofline": roofline, "kernels": kernels, "gpu_launches": int(round(launches_per_step * K)),
                "batched_ensemble": batched, "split_coupling": split,
                "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks, "fp64_peak": fp64_peak,
                "accuracy_vs_fp64": accuracy, "secondary": secondary,

@@ -242,8 +242,8 @@ class Mesh:
         _lib.check("grist_tracer_step", lib.grist_tracer_step(self.handle, ctypes.byref(b), float(dt),
                                                               _stream_handle(stream)))
 
-    def set_tracer_tuning(self, block=256, tracers_per_thread=4, persistent=False, use_graph=False, fused=False,
-                          levels_per_thread=1):
+    def set_tracer_tuning(self, block=128, tracers_per_thread=4, persistent=False, use_graph=False, fused=False,
+                          levels_per_thread=2):
         t = _lib.TracerTuning(int(block), int(tracers_per_thread), int(bool(persistent)), int(bool(use_graph)),
                               int(bool(fused)), int(levels_per_thread))
         _lib.check("grist_tracer_set_tuning", _lib.load().grist_tracer_set_tuning(self.handle, ctypes.byref(t)))

@@ -318,17 +318,27 @@ __global__ void k_theta_flux(DevMesh m, DyPar d, LevelDiv Dv, const typename P::
     if (n >= (uint32_t)m.nE * (uint32_t)d.L) return;
     int e, k;
     split_index(n, Dv, e, k);
-    const int2 c = ldg(m.coe + e);
     const size_t x = (size_t)e * d.ld + k;
     const TA f = cv<TA>(F[x]);
     const int side = f >= (TA)0 ? 0 : 1;
     const int32_t *st = m.d2i + (size_t)e * 14 + side * GRIST_D2P;
-    const TA *cf = Coef<TA>::d2c(m) + (size_t)e * 14 + side * GRIST_D2P;
-    TA s = 0;
+    TA te;
+    if (m.d2w_ok) {
+        // one weighted sum over the upwind side's stencil (the mean of the
+        // edge's two cells folded into the weights)
+        const TA *cw = Coef<TA>::d2w(m) + (size_t)e * 14 + side * GRIST_D2P;
+        te = 0;
 #pragma unroll
-    for (int j = 0; j < GRIST_D2P; j++) s += ldg(cf + j) * ldg(th + (size_t)ldg(st + j) * d.ld + k);
-    const TA te = (TA)0.5 * (ldg(th + (size_t)c.x * d.ld + k) + ldg(th + (size_t)c.y * d.ld + k)) -
-                  (TA)2 * ldg(Coef<TA>::dc2(m) + e) * s;
+        for (int j = 0; j < GRIST_D2P; j++) te += ldg(cw + j) * ldg(th + (size_t)ldg(st + j) * d.ld + k);
+    } else {
+        const int2 c = ldg(m.coe + e);
+        const TA *cf = Coef<TA>::d2c(m) + (size_t)e * 14 + side * GRIST_D2P;
+        TA s = 0;
+#pragma unroll
+        for (int j = 0; j < GRIST_D2P; j++) s += ldg(cf + j) * ldg(th + (size_t)ldg(st + j) * d.ld + k);
+        te = (TA)0.5 * (ldg(th + (size_t)c.x * d.ld + k) + ldg(th + (size_t)c.y * d.ld + k)) -
+             (TA)2 * ldg(Coef<TA>::dc2(m) + e) * s;
+    }
     Fth[x] = emu<P::EMU>(f * te, d.emu, GRIST_ROW_THETA);
 }
 

@@ -74,7 +74,7 @@ struct TileMesh {
 };
 
 struct TracerCtx {
-    grist_tracer_tuning tune{256, 4, 0, 0, 0, 1};
+    grist_tracer_tuning tune{128, 4, 0, 0, 0, 2};
     // tile tables (built on first use)
     char *dtile = nullptr;
     TileMesh tiles{};

@@ -45,5 +45,14 @@ def test_mix_df_step_against_oracle_and_mix(G, mesh_cache, nh):
     # against GRIST_MIX: the same except for the binary32 rounding inside
     # the slow tendency (~2^-24 of it), far below the policy's own error
     assert O.max_rel_diff(df["u"], mix["u"]) <= 2e-6
-    assert O.max_rel_diff(df["ps"], mix["ps"]) <= 1e-9
+    # the surface pressure sees the wind difference only through the column
+    # mass flux: |d ps / dt| changes by at most max_i sum_j (dv_j / A_i) *
+    # (ps - pi_top) * max|du| per unit time, so over the step
+    # |dps| / ps <= dt * max_i sum_j dv_j / A_i * max|du|
+    import numpy as np
+    dv = m["edge_dv"][np.maximum(m["edges_on_cell"], 0)] * (m["edges_on_cell"] >= 0)
+    perim = np.max(dv.sum(axis=1) / m["cell_area"])
+    du = float(np.max(np.abs(df["u"] - mix["u"])))
+    assert O.max_rel_diff(df["ps"], mix["ps"]) <= dt * perim * du, (O.max_rel_diff(df["ps"], mix["ps"]),
+                                                                     dt * perim * du)
     mesh.close()
