@@ -74,14 +74,15 @@ def algorithmic_bytes(name, nC, nE, nV, L, T, prec):
         "k_nh_solve": 2 * CI * 8 + CL * 8 + nC * 8 + 2 * CI * 8 + 4 * CL * 8,
         "k_add_scalar": 16,
         "k_vertex_mass": nC * 8 + nV * 8,
-        "k_tr_div": EL * 8 + CL * 8 + (EL * 4 if sC == 4 else 0),       # + the binary32 flux copy
+        # F, dpi^n -> the {dpi^n, div F} pair (+ the binary32 flux copy)
+        "k_tr_div": EL * 8 + CL * 8 + 2 * CL * sC + (EL * 4 if sC == 4 else 0),
         "k_tr_edge": T * CL * sQ + EL * sC + T * EL * sC,
-        "k_tr_update": T * EL * sC + T * CL * sQ + 2 * CL * 8 + T * CL * sQ,
-        "k_tr_lowres": T * CL * sQ + EL * sC + 2 * CL * 8 + T * CL * sQ,
-        "k_tr_ratios": 2 * T * CL * sQ + T * EL * sC + EL * sC + 2 * CL * 8 + 2 * T * CL * sC,
-        "k_tr_final": T * CL * sQ + T * EL * sC + EL * sC + 2 * CL * 8 + 2 * T * CL * sC + T * CL * sQ,
+        "k_tr_update": T * EL * sC + T * CL * sQ + 2 * CL * sC + T * CL * sQ,
+        "k_tr_lowres": T * CL * sQ + EL * sC + 2 * CL * sC + T * CL * sQ,
+        "k_tr_ratios": 2 * T * CL * sQ + T * EL * sC + EL * sC + 2 * CL * sC + 2 * T * CL * sC,
+        "k_tr_final": T * CL * sQ + T * EL * sC + EL * sC + 2 * CL * sC + 2 * T * CL * sC + T * CL * sQ,
         "k_tr_copy": 2 * T * CL * sQ,
-        "k_tr_vertical": 2 * CL * 8 + CI * 8 + 2 * T * CL * sQ,
+        "k_tr_vertical": 2 * CL * sC + CI * 8 + 2 * T * CL * sQ,
     }
     return table.get(base)
 

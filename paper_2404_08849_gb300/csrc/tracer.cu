@@ -33,11 +33,11 @@ struct MemberDev {
     void *q;                // [T][nC][ld] caller's tracers (q^n in, q^{n+1} out)
     const double *dpi;      // [nC][ld]
     const double *F;        // [nE][ld]
-    double *divF;           // scratch [nC][ld]
     void *qA, *qB;          // scratch stage tracers [T][nC][ld]
     void *FH;               // scratch edge fluxes [T][nE][ld]
     void *Rp, *Rm;          // scratch FCT ratios [T][nC][ld]
     const void *Ff;         // mass flux in the compute type [nE][ld]: a binary32 copy (scratch) or F itself
+    void *DV;               // scratch {dpi, div F} pairs in the compute type [nC][ld]
     int L, T, ld, pad;
     const double *Mv;       // time-mean vertical mass flux [nC][ldi] or null (no vertical step)
     int ldi;
@@ -174,10 +174,41 @@ template <> __device__ __forceinline__ float tiny_of<float>() { return 1.1754943
 // ---------------------------------------------------------------------------
 // phase bodies (one work item each)
 
-// Tracer continuity of the member: divF = div(mass flux), FP64.  In the
-// binary32 policy each edge's flux is also rounded once to binary32 for the
-// later phases (by the cell it leaves: positive divergence coefficient), so
-// they read 4 bytes per edge-level instead of 8.
+// {dpi, div F} pair in the compute type.
+template <typename TC> struct Vec2;
+template <> struct Vec2<float> { using T = float2; };
+template <> struct Vec2<double> { using T = double2; };
+
+// Stage ratios r1 = dpi^n / dpi^(s) and r2 = dt_s / dpi^(s) of the update
+// q^(s) = r1 q^n - r2 div F^H, with dpi^(s) = dpi^n - dt_s div F: FP64 in the
+// FP64 policy (the oracle's arithmetic); in the binary32 policy in binary32
+// from the rounded pair, so the binary32 phases issue no FP64 instruction
+// (the ratios are rounded to binary32 either way).
+__device__ __forceinline__ void stage_ratios(double2 dv, double dts, float, double &r1, double &r2) {
+    const double rinv = rcp(dv.x - dts * dv.y);
+    r1 = dv.x * rinv;
+    r2 = dts * rinv;
+}
+__device__ __forceinline__ void stage_ratios(float2 dv, double, float dtsf, float &r1, float &r2) {
+    const float rinv = __frcp_rn(fmaf(-dtsf, dv.y, dv.x));
+    r1 = dv.x * rinv;
+    r2 = dtsf * rinv;
+}
+// Layer mass at the end of the step, dpi^n - dt div F, in the compute type.
+__device__ __forceinline__ double end_mass(double2 dv, double dt, float) { return dv.x - dt * dv.y; }
+__device__ __forceinline__ float end_mass(float2 dv, double, float dtf) { return fmaf(-dtf, dv.y, dv.x); }
+
+template <bool PERS, typename TC>
+__device__ __forceinline__ typename Vec2<TC>::T dv_at(const MemberDev &mb, size_t x) {
+    return lds<PERS>((const typename Vec2<TC>::T *)mb.DV + x);
+}
+
+// Tracer continuity of the member: div F of the FP64 time-mean mass flux,
+// summed in FP64, stored with dpi^n as the {dpi, div F} pair of the later
+// phases (rounded to binary32 in the binary32 policy).  In that policy each
+// edge's flux is also rounded once to binary32 for the later phases (by the
+// cell it leaves: positive divergence coefficient), so they read 4 bytes
+// per edge-level instead of 8.
 template <typename TC>
 __device__ __forceinline__ void item_div(const DevMesh &m, const MemberDev &mb, int i, int k) {
     double s = 0.0;
@@ -189,7 +220,9 @@ __device__ __forceinline__ void item_div(const DevMesh &m, const MemberDev &mb, 
         s += cw * f;
         if (sizeof(TC) == 4 && cw > 0.0) ((float *)mb.Ff)[(size_t)e * mb.ld + k] = cv<float>(f);
     }
-    mb.divF[(size_t)i * mb.ld + k] = s;
+    const size_t x = (size_t)i * mb.ld + k;
+    if (sizeof(TC) == 4) ((float2 *)mb.DV)[x] = make_float2(cv<float>(ldg(mb.dpi + x)), cv<float>(s));
+    else ((double2 *)mb.DV)[x] = make_double2(ldg(mb.dpi + x), s);
 }
 
 // Mass flux of edge-level x in the compute type: the binary32 copy made by
@@ -274,12 +307,11 @@ __device__ __forceinline__ void item_edge(const DevMesh &m, const MemberDev &mb,
 // (Sec. 2.2 (ii): no mixed-kind products inside the tracer loop).
 template <bool PERS, typename TQ, typename TC>
 __device__ __forceinline__ bool item_update(const DevMesh &m, const MemberDev &mb, TQ *qout, int t0, int t1, int i,
-                                            int k, double dts) {
+                                            int k, double dts, float dtsf) {
     const int ld = mb.ld;
     const size_t x = (size_t)i * ld + k;
-    const double dp = mb.dpi[x];
-    const double rinv = rcp(dp - dts * lds<PERS>(mb.divF + x));
-    const TC r1 = static_cast<TC>(dp * rinv), r2 = static_cast<TC>(dts * rinv);
+    TC r1, r2;
+    stage_ratios(dv_at<PERS, TC>(mb, x), dts, dtsf, r1, r2);
     int eidx[GRIST_MAXE];
     TC cw[GRIST_MAXE];
 #pragma unroll
@@ -315,12 +347,11 @@ __device__ __forceinline__ TC upwind_flux(TC f, TC cw, int i, int nb, const TQ *
 // FCT 1: low-order solution q^td = (dpi^n q^n - dt div F^L) / dpi^(3).
 template <bool PERS, typename TQ, typename TC>
 __device__ __forceinline__ void item_lowres(const DevMesh &m, const MemberDev &mb, int t0, int t1, int i, int k,
-                                            double dt) {
+                                            double dt, float dtf) {
     const int ld = mb.ld;
     const size_t x = (size_t)i * ld + k;
-    const double dp = mb.dpi[x];
-    const double rinv = rcp(dp - dt * lds<PERS>(mb.divF + x));
-    const TC r1 = static_cast<TC>(dp * rinv), r2 = static_cast<TC>(dt * rinv);
+    TC r1, r2;
+    stage_ratios(dv_at<PERS, TC>(mb, x), dt, dtf, r1, r2);
     int nb[GRIST_MAXE];
     TC cw[GRIST_MAXE], fe[GRIST_MAXE];
 #pragma unroll
@@ -346,11 +377,11 @@ __device__ __forceinline__ void item_lowres(const DevMesh &m, const MemberDev &m
 // R+- = min(1, Q / (P + TINY)) (Sec. 2.2 (iii): TINY of the working type).
 template <bool PERS, typename TQ, typename TC>
 __device__ __forceinline__ void item_ratios(const DevMesh &m, const MemberDev &mb, int t0, int t1, int i, int k,
-                                            double dt) {
+                                            double dt, float dtf) {
     const int ld = mb.ld;
     const size_t x = (size_t)i * ld + k;
-    const TC dp3 = static_cast<TC>(mb.dpi[x] - dt * lds<PERS>(mb.divF + x));
-    const TC dtc = static_cast<TC>(dt);
+    const TC dp3 = static_cast<TC>(end_mass(dv_at<PERS, TC>(mb, x), dt, dtf));
+    const TC dtc = sizeof(TC) == 4 ? (TC)dtf : (TC)dt;
     int nb[GRIST_MAXE], eidx[GRIST_MAXE];
     TC cw[GRIST_MAXE], fe[GRIST_MAXE];
 #pragma unroll
@@ -397,12 +428,11 @@ __device__ __forceinline__ void item_ratios(const DevMesh &m, const MemberDev &m
 // q^{n+1} = (dpi^n q^n - dt div(F^L + C A)) / dpi^(3) into qB.
 template <bool PERS, typename TQ, typename TC>
 __device__ __forceinline__ bool item_final(const DevMesh &m, const MemberDev &mb, int t0, int t1, int i, int k,
-                                           double dt) {
+                                           double dt, float dtf) {
     const int ld = mb.ld;
     const size_t x = (size_t)i * ld + k;
-    const double dp = mb.dpi[x];
-    const double rinv = rcp(dp - dt * lds<PERS>(mb.divF + x));
-    const TC r1 = static_cast<TC>(dp * rinv), r2 = static_cast<TC>(dt * rinv);
+    TC r1, r2;
+    stage_ratios(dv_at<PERS, TC>(mb, x), dt, dtf, r1, r2);
     int nb[GRIST_MAXE], eidx[GRIST_MAXE];
     TC cw[GRIST_MAXE], fe[GRIST_MAXE];
 #pragma unroll
@@ -466,6 +496,7 @@ __device__ void run_phase(const DevMesh &m, const Batch &B, uint32_t *status) {
     int seg = -1;
     bool bad = false;
     const double dts = PH <= P_UPD0 ? B.dt3 : (PH <= P_UPD1 ? 0.5 * B.dt : B.dt);
+    const float dtsf = cv<float>(dts), dtf = cv<float>(B.dt);
     const TC beta = static_cast<TC>(B.beta);
     for (unsigned long long n = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; n < S.total; n += stride) {
         seg = find_seg(S, n, seg);
@@ -483,12 +514,12 @@ __device__ void run_phase(const DevMesh &m, const Batch &B, uint32_t *status) {
         if (PH == P_EDGE0) item_edge<PERS, TQ, TC>(m, mb, (const TQ *)mb.q, t0, t1, ent, k, B.beta1, beta);
         if (PH == P_EDGE1) item_edge<PERS, TQ, TC>(m, mb, (const TQ *)mb.qA, t0, t1, ent, k, B.beta1, beta);
         if (PH == P_EDGE2) item_edge<PERS, TQ, TC>(m, mb, (const TQ *)mb.qB, t0, t1, ent, k, B.beta1, beta);
-        if (PH == P_UPD0) bad |= item_update<PERS, TQ, TC>(m, mb, (TQ *)mb.qA, t0, t1, ent, k, dts);
-        if (PH == P_UPD1) bad |= item_update<PERS, TQ, TC>(m, mb, (TQ *)mb.qB, t0, t1, ent, k, dts);
-        if (PH == P_UPD2) bad |= item_update<PERS, TQ, TC>(m, mb, (TQ *)mb.q, t0, t1, ent, k, dts);
-        if (PH == P_LOWRES) item_lowres<PERS, TQ, TC>(m, mb, t0, t1, ent, k, B.dt);
-        if (PH == P_RATIOS) item_ratios<PERS, TQ, TC>(m, mb, t0, t1, ent, k, B.dt);
-        if (PH == P_FINAL) bad |= item_final<PERS, TQ, TC>(m, mb, t0, t1, ent, k, B.dt);
+        if (PH == P_UPD0) bad |= item_update<PERS, TQ, TC>(m, mb, (TQ *)mb.qA, t0, t1, ent, k, dts, dtsf);
+        if (PH == P_UPD1) bad |= item_update<PERS, TQ, TC>(m, mb, (TQ *)mb.qB, t0, t1, ent, k, dts, dtsf);
+        if (PH == P_UPD2) bad |= item_update<PERS, TQ, TC>(m, mb, (TQ *)mb.q, t0, t1, ent, k, dts, dtsf);
+        if (PH == P_LOWRES) item_lowres<PERS, TQ, TC>(m, mb, t0, t1, ent, k, B.dt, dtf);
+        if (PH == P_RATIOS) item_ratios<PERS, TQ, TC>(m, mb, t0, t1, ent, k, B.dt, dtf);
+        if (PH == P_FINAL) bad |= item_final<PERS, TQ, TC>(m, mb, t0, t1, ent, k, B.dt, dtf);
         if (PH == P_COPY) item_copy<PERS, TQ>(mb, t0, t1, ent, k);
         }
     }
@@ -576,10 +607,7 @@ __global__ void __launch_bounds__(256) k_tr_tile_stage(DevMesh m, TileMesh tm, B
         r1v[idx] = r2v[idx] = (TC)0;
         if (ci < nc && kin) {
             const size_t x = (size_t)(c0 + ci) * ld + k;
-            const double dp = mb.dpi[x];
-            const double rinv = rcp(dp - dts * mb.divF[x]);
-            r1v[idx] = static_cast<TC>(dp * rinv);
-            r2v[idx] = static_cast<TC>(dts * rinv);
+            stage_ratios(((const typename Vec2<TC>::T *)mb.DV)[x], dts, cv<float>(dts), r1v[idx], r2v[idx]);
         }
     }
     const int t0 = mg.y * B.tpt, t1 = min(mb.T, t0 + B.tpt);
@@ -678,7 +706,10 @@ __global__ void __launch_bounds__(kVertWarps * 32) k_tr_vertical(DevMesh m, Memb
     const int L = mb.L, ld = mb.ld, ldi = mb.ldi;
     const TC dtc = cv<TC>(dt), cm = cv<TC>(cmax);
     const size_t row = (size_t)i * ld, irow = (size_t)i * ldi;
-    auto dstar = [&](int kk) -> TC { return cv<TC>(mb.dpi[row + kk] - dt * mb.divF[row + kk]); };
+    // start layer mass of the vertical step: the end of the horizontal one
+    const typename Vec2<TC>::T *DV = (const typename Vec2<TC>::T *)mb.DV;
+    const float dtf = cv<float>(dt);
+    auto dstar = [&](int kk) -> TC { return (TC)end_mass(DV[row + kk], dt, dtf); };
     // interface j between layers j-1 (above) and j (below), with those
     // layers' start masses: explicit and implicit shares
     auto split = [&](int j, TC above, TC below, TC &me, TC &mi) {
@@ -903,14 +934,14 @@ int plan_batch(const DevMesh &m, const grist_tracer_batch *b, int tpt, int lpt, 
         d.fs = (unsigned long long)m.nE * u.ld;
         // scratch offsets (relative, resolved after allocation)
         const size_t bq = (size_t)d.T * d.qs * sizeof(TQ), bf = (size_t)d.T * d.fs * sizeof(TC),
-                     br = (size_t)d.T * d.qs * sizeof(TC), bd = d.qs * sizeof(double);
-        d.divF = (double *)(uintptr_t)off; off += al256(bd);
+                     br = (size_t)d.T * d.qs * sizeof(TC);
         d.qA = (void *)(uintptr_t)off; off += al256(bq);
         d.qB = (void *)(uintptr_t)off; off += al256(bq);
         d.FH = (void *)(uintptr_t)off; off += al256(bf);
         d.Rp = (void *)(uintptr_t)off; off += al256(br);
         d.Rm = (void *)(uintptr_t)off; off += al256(br);
         if (sizeof(TC) == 4) { d.Ff = (const void *)(uintptr_t)off; off += al256(d.fs * sizeof(float)); }
+        d.DV = (void *)(uintptr_t)off; off += al256(d.qs * 2 * sizeof(TC));
         const int idx = (int)P.mem.size();
         const int G = (d.T + tpt - 1) / tpt;
         P.sD.push_back(tD); P.mD.push_back(make_int2(idx, 0));
@@ -942,13 +973,13 @@ int upload_plan(grist_mesh_s *h, TracerCtx *c, HostPlan &P, const grist_tracer_b
     char *scr = (char *)scratch(h, 0, P.scratch_bytes + 256);
     if (!scr) return GRIST_ENOMEM;
     for (auto &d : P.mem) {
-        d.divF = (double *)(scr + (uintptr_t)d.divF);
         d.qA = scr + (uintptr_t)d.qA;
         d.qB = scr + (uintptr_t)d.qB;
         d.FH = scr + (uintptr_t)d.FH;
         d.Rp = scr + (uintptr_t)d.Rp;
         d.Rm = scr + (uintptr_t)d.Rm;
         d.Ff = sizeof(TC) == 4 ? (const void *)(scr + (uintptr_t)d.Ff) : (const void *)d.F;
+        d.DV = scr + (uintptr_t)d.DV;
     }
     const size_t nm = P.mem.size();
     size_t o = 0;
