@@ -35,6 +35,12 @@ struct DevMesh {
     const int32_t *coc;   // [nC][6]  pad: i itself
     const double *cdiv;   // [nC][6]
     const float *cdiv_f;
+    // the same three lists in rows of 8 (entries 6, 7: eoc[i][0], i, 0), read
+    // as 16-byte vectors by the gather kernels
+    const int32_t *eoc8;  // [nC][8]
+    const int32_t *coc8;  // [nC][8]
+    const double *cdiv8;  // [nC][8]
+    const float *cdiv8_f;
     const double *kec2;   // [nC][6] dc dv / (2 A): twice the kinetic-energy weight
     const double *area;   // [nC]
     // edges
@@ -48,10 +54,12 @@ struct DevMesh {
     const double *d2c;    // [nE][2][7]
     const float *d2c_f;
     // Upwind-side edge value in one weighted sum (beta = 1):
-    // q_e = sum_j d2w[e][s][j] q(d2i[e][s][j]), d2w = -2 (dc^2/12) d2c with
+    // q_e = sum_j d2w[e][s][j] q(d2wi[e][s][j]), d2w = -2 (dc^2/12) d2c with
     // 1/2 added on the entries of c1 and c2; d2w_ok = 0 when some stencil
-    // lacks c1 or c2 (then the separate form is used).
-    const double *d2w;    // [nE][2][7]
+    // lacks c1 or c2 (then the separate form is used).  Rows of 8 (entry 7:
+    // the side's centre cell, weight 0), read as 16-byte vectors.
+    const int32_t *d2wi;  // [nE][2][8]
+    const double *d2w;    // [nE][2][8]
     const float *d2w_f;
     int d2w_ok;
     const int32_t *eoe;   // [nE][10] pad: e itself
@@ -119,6 +127,7 @@ struct PolMIXDF {
 template <typename T> struct Coef;
 template <> struct Coef<double> {
     static __device__ __forceinline__ const double *cdiv(const DevMesh &m) { return m.cdiv; }
+    static __device__ __forceinline__ const double *cdiv8(const DevMesh &m) { return m.cdiv8; }
     static __device__ __forceinline__ const double *d2c(const DevMesh &m) { return m.d2c; }
     static __device__ __forceinline__ const double *d2w(const DevMesh &m) { return m.d2w; }
     static __device__ __forceinline__ const double *dc2(const DevMesh &m) { return m.dc2; }
@@ -128,6 +137,7 @@ template <> struct Coef<double> {
 };
 template <> struct Coef<float> {
     static __device__ __forceinline__ const float *cdiv(const DevMesh &m) { return m.cdiv_f; }
+    static __device__ __forceinline__ const float *cdiv8(const DevMesh &m) { return m.cdiv8_f; }
     static __device__ __forceinline__ const float *d2c(const DevMesh &m) { return m.d2c_f; }
     static __device__ __forceinline__ const float *d2w(const DevMesh &m) { return m.d2w_f; }
     static __device__ __forceinline__ const float *dc2(const DevMesh &m) { return m.dc2_f; }
@@ -138,6 +148,44 @@ template <> struct Coef<float> {
 
 __device__ __forceinline__ double fmin_(double a, double b) { return fmin(a, b); }
 __device__ __forceinline__ float fmin_(float a, float b) { return fminf(a, b); }
+
+// Entries 0..5 of row i of a [n][8] table, read as 16-byte vectors.
+__device__ __forceinline__ void load_row6(const int32_t *t, int i, int (&v)[6]) {
+    const int4 *p = (const int4 *)(t + (size_t)i * 8);
+    const int4 a = __ldg(p), b = __ldg(p + 1);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y;
+}
+__device__ __forceinline__ void load_row6(const float *t, int i, float (&v)[6]) {
+    const float4 *p = (const float4 *)(t + (size_t)i * 8);
+    const float4 a = __ldg(p), b = __ldg(p + 1);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y;
+}
+__device__ __forceinline__ void load_row6(const double *t, int i, double (&v)[6]) {
+    const double2 *p = (const double2 *)(t + (size_t)i * 8);
+    const double2 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y; v[4] = c.x; v[5] = c.y;
+}
+
+// The combined upwind stencil of edge e on side s (0: c1's, 1: c2's): its
+// 7 cells and weights, read as 16-byte vectors from the rows of 8.
+static_assert(GRIST_D2P == 7, "combined stencil rows of 8 hold 7 entries");
+__device__ __forceinline__ void load_d2w(const DevMesh &m, int e, int s, int (&c)[GRIST_D2P],
+                                         float (&w)[GRIST_D2P]) {
+    const size_t r = ((size_t)e * 2 + s) * 8;
+    const int4 a = __ldg((const int4 *)(m.d2wi + r)), b = __ldg((const int4 *)(m.d2wi + r) + 1);
+    const float4 u = __ldg((const float4 *)(m.d2w_f + r)), v = __ldg((const float4 *)(m.d2w_f + r) + 1);
+    c[0] = a.x; c[1] = a.y; c[2] = a.z; c[3] = a.w; c[4] = b.x; c[5] = b.y; c[6] = b.z;
+    w[0] = u.x; w[1] = u.y; w[2] = u.z; w[3] = u.w; w[4] = v.x; w[5] = v.y; w[6] = v.z;
+}
+__device__ __forceinline__ void load_d2w(const DevMesh &m, int e, int s, int (&c)[GRIST_D2P],
+                                         double (&w)[GRIST_D2P]) {
+    const size_t r = ((size_t)e * 2 + s) * 8;
+    const int4 a = __ldg((const int4 *)(m.d2wi + r)), b = __ldg((const int4 *)(m.d2wi + r) + 1);
+    const double2 *p = (const double2 *)(m.d2w + r);
+    const double2 u0 = __ldg(p), u1 = __ldg(p + 1), u2 = __ldg(p + 2), u3 = __ldg(p + 3);
+    c[0] = a.x; c[1] = a.y; c[2] = a.z; c[3] = a.w; c[4] = b.x; c[5] = b.y; c[6] = b.z;
+    w[0] = u0.x; w[1] = u0.y; w[2] = u1.x; w[3] = u1.y; w[4] = u2.x; w[5] = u2.y; w[6] = u3.x;
+}
 __device__ __forceinline__ double fmax_(double a, double b) { return fmax(a, b); }
 __device__ __forceinline__ float fmax_(float a, float b) { return fmaxf(a, b); }
 

@@ -309,37 +309,51 @@ __global__ void k_mass_col(DevMesh m, DyPar d, const typename P::TM *__restrict_
 }
 
 // Eq. 4 horizontal flux: third-order upwind (beta = 1) edge value of theta
-// times the mass flux.
+// times the mass flux.  A thread takes levels kg and kg + Lh (Lh = ceil(L/2))
+// of one edge, so the upwind stencil row (4 vector loads) serves both
+// levels unless their fluxes run opposite ways.
 template <class P>
-__global__ void k_theta_flux(DevMesh m, DyPar d, LevelDiv Dv, const typename P::TM *__restrict__ F,
+__global__ void k_theta_flux(DevMesh m, DyPar d, LevelDiv Dh, const typename P::TM *__restrict__ F,
                              const typename P::TA *__restrict__ th, typename P::TA *__restrict__ Fth) {
     using TA = typename P::TA;
+    const int Lh = (int)Dh.d;
     uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= (uint32_t)m.nE * (uint32_t)d.L) return;
-    int e, k;
-    split_index(n, Dv, e, k);
-    const size_t x = (size_t)e * d.ld + k;
-    const TA f = cv<TA>(F[x]);
-    const int side = f >= (TA)0 ? 0 : 1;
-    const int32_t *st = m.d2i + (size_t)e * 14 + side * GRIST_D2P;
-    TA te;
-    if (m.d2w_ok) {
-        // one weighted sum over the upwind side's stencil (the mean of the
-        // edge's two cells folded into the weights)
-        const TA *cw = Coef<TA>::d2w(m) + (size_t)e * 14 + side * GRIST_D2P;
-        te = 0;
+    if (n >= (uint32_t)m.nE * (uint32_t)Lh) return;
+    int e, kg;
+    split_index(n, Dh, e, kg);
+    int c[GRIST_D2P];
+    TA w[GRIST_D2P];
+    int loaded = -1;
 #pragma unroll
-        for (int j = 0; j < GRIST_D2P; j++) te += ldg(cw + j) * ldg(th + (size_t)ldg(st + j) * d.ld + k);
-    } else {
-        const int2 c = ldg(m.coe + e);
-        const TA *cf = Coef<TA>::d2c(m) + (size_t)e * 14 + side * GRIST_D2P;
-        TA s = 0;
+    for (int u = 0; u < 2; u++) {
+        const int k = kg + u * Lh;
+        if (k >= d.L) break;
+        const size_t x = (size_t)e * d.ld + k;
+        const TA f = cv<TA>(F[x]);
+        const int side = f >= (TA)0 ? 0 : 1;
+        TA te;
+        if (m.d2w_ok) {
+            // one weighted sum over the upwind side's stencil (the mean of
+            // the edge's two cells folded into the weights)
+            if (side != loaded) {
+                load_d2w(m, e, side, c, w);
+                loaded = side;
+            }
+            te = 0;
 #pragma unroll
-        for (int j = 0; j < GRIST_D2P; j++) s += ldg(cf + j) * ldg(th + (size_t)ldg(st + j) * d.ld + k);
-        te = (TA)0.5 * (ldg(th + (size_t)c.x * d.ld + k) + ldg(th + (size_t)c.y * d.ld + k)) -
-             (TA)2 * ldg(Coef<TA>::dc2(m) + e) * s;
+            for (int j = 0; j < GRIST_D2P; j++) te += w[j] * ldg(th + (size_t)c[j] * d.ld + k);
+        } else {
+            const int32_t *st = m.d2i + (size_t)e * 14 + side * GRIST_D2P;
+            const int2 ce = ldg(m.coe + e);
+            const TA *cf = Coef<TA>::d2c(m) + (size_t)e * 14 + side * GRIST_D2P;
+            TA sm = 0;
+#pragma unroll
+            for (int j = 0; j < GRIST_D2P; j++) sm += ldg(cf + j) * ldg(th + (size_t)ldg(st + j) * d.ld + k);
+            te = (TA)0.5 * (ldg(th + (size_t)ce.x * d.ld + k) + ldg(th + (size_t)ce.y * d.ld + k)) -
+                 (TA)2 * ldg(Coef<TA>::dc2(m) + e) * sm;
+        }
+        Fth[x] = emu<P::EMU>(f * te, d.emu, GRIST_ROW_THETA);
     }
-    Fth[x] = emu<P::EMU>(f * te, d.emu, GRIST_ROW_THETA);
 }
 
 // Eq. 4 update: dpi theta^(s) = dpi theta^n + dt_s (-div F_theta - delta(M theta)).
@@ -967,12 +981,12 @@ int dycore_step(grist_mesh_s *h, grist_dycore_state *S, const grist_dycore_param
 
     TU *u = (TU *)S->u;
     uint32_t *status = status_word(h);
-    const LevelDiv DL = make_div((uint32_t)L), DI = make_div((uint32_t)(L + 1));
+    const LevelDiv DL = make_div((uint32_t)L), DI = make_div((uint32_t)(L + 1)), DH = make_div((uint32_t)(L + 1) / 2);
     const unsigned gC = grid_for((long long)m.nC * L, kBlock), gE = grid_for((long long)m.nE * L, kBlock),
                    gV = grid_for((long long)m.nV * L, kBlock), gW = grid_for((long long)m.nC * 32, kBlock),
                    gI = grid_for((long long)m.nC * (L + 1), kBlock), gSolve = grid_for(m.nC, kSolveCols),
                    gVx = grid_for(m.nV, kBlock), gE32 = grid_for((long long)m.nE + 31, kBlock),
-                   gC32 = grid_for((long long)m.nC + 31, kBlock);
+                   gC32 = grid_for((long long)m.nC + 31, kBlock), gEH = grid_for((long long)m.nE * DH.d, kBlock);
     const double dts[3] = {dt / 3.0, dt / 2.0, dt};
     const double ascale = S->accum_scale != 0.0 ? S->accum_scale : 1.0;
 
@@ -1006,7 +1020,7 @@ int dycore_step(grist_mesh_s *h, grist_dycore_state *S, const grist_dycore_param
         GRIST_LAUNCH(h, PN("k_mass_col"), st, k_mass_col<P><<<gC32, kBlock, 0, st>>>(
             m, d, F, fcol, ps_in, psN, ps_outs[s3], th_in, theta, Mv, h3, s3 == 0 ? S->dpi_start : nullptr, rdps,
             (NH && s3 == 0) ? rthn : nullptr, s3 == 2 ? S->vmass_flux_accum : nullptr, ascale));
-        GRIST_LAUNCH(h, PN("k_theta_flux"), st, k_theta_flux<P><<<gE, kBlock, 0, st>>>(m, d, DL, F, theta, Fth));
+        GRIST_LAUNCH(h, PN("k_theta_flux"), st, k_theta_flux<P><<<gEH, kBlock, 0, st>>>(m, d, DH, F, theta, Fth));
         GRIST_LAUNCH(h, PN("k_theta_update"), st, k_theta_update<P><<<gC, kBlock, 0, st>>>(
             m, d, DL, Fth, theta, Mv, S->dpi_theta, th_outs[s3], h3));
         if (NH) {

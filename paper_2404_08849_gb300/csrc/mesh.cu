@@ -298,12 +298,27 @@ extern "C" int grist_mesh_create(const grist_mesh_desc *desc, int device, grist_
             cdiv_f[x] = (float)cdiv[x];
         }
     }
+    // padded rows of 8 of the per-cell lists (entries 6 and 7: eoc[i][0],
+    // the cell itself, weight 0) for 16-byte vector reads
+    std::vector<int32_t> eoc8(8 * (size_t)nC), coc8(8 * (size_t)nC);
+    std::vector<double> cdiv8(8 * (size_t)nC);
+    std::vector<float> cdiv8_f(8 * (size_t)nC);
+    for (int i = 0; i < nC; i++) {
+        for (int j = 0; j < 8; j++) {
+            const size_t x = (size_t)i * 8 + j, y = (size_t)i * 6 + j;
+            eoc8[x] = j < 6 ? eoc[y] : eoc[(size_t)i * 6];
+            coc8[x] = j < 6 ? coc[y] : i;
+            cdiv8[x] = j < 6 ? cdiv[y] : 0.0;
+            cdiv8_f[x] = (float)cdiv8[x];
+        }
+    }
     std::vector<int2> coe(nE), voe(nE);
     std::vector<double> rdc(nE), hrdc(nE), dc2(nE), d2c(14 * (size_t)nE), wpv(10 * (size_t)nE);
     std::vector<float> dc2_f(nE), d2c_f(14 * (size_t)nE), wpv_f(10 * (size_t)nE);
     std::vector<int32_t> d2i(14 * (size_t)nE), eoe(10 * (size_t)nE);
-    std::vector<double> d2w(14 * (size_t)nE);
-    std::vector<float> d2w_f(14 * (size_t)nE);
+    std::vector<int32_t> d2wi(16 * (size_t)nE);
+    std::vector<double> d2w(16 * (size_t)nE);
+    std::vector<float> d2w_f(16 * (size_t)nE);
     int d2w_ok = 1;
     for (int e = 0; e < nE; e++) {
         int o = eold[e];
@@ -325,17 +340,24 @@ extern "C" int grist_mesh_create(const grist_mesh_desc *desc, int device, grist_
             }
             // combined weights: the mean of the edge's two cells folded into
             // the upwind side's stencil (first entry of each cell)
-            const size_t b0 = ((size_t)e * 2 + s) * GRIST_D2P;
-            for (int j = 0; j < GRIST_D2P; j++) d2w[b0 + j] = -2.0 * dc2[e] * d2c[b0 + j];
+            // (rows of 8: the eighth entry is padding, the side's centre cell
+            // with weight 0, so that a row is two 16-byte index vectors)
+            const size_t b0 = ((size_t)e * 2 + s) * GRIST_D2P, w0 = ((size_t)e * 2 + s) * 8;
+            for (int j = 0; j < GRIST_D2P; j++) {
+                d2wi[w0 + j] = d2i[b0 + j];
+                d2w[w0 + j] = -2.0 * dc2[e] * d2c[b0 + j];
+            }
+            d2wi[w0 + 7] = cn[centre];
+            d2w[w0 + 7] = 0.0;
             const int ends[2] = {coe[e].x, coe[e].y};
             for (int q = 0; q < 2; q++) {
                 int at = -1;
                 for (int j = 0; j < GRIST_D2P && at < 0; j++)
                     if (d2i[b0 + j] == ends[q]) at = j;
                 if (at < 0) d2w_ok = 0;
-                else d2w[b0 + at] += 0.5;
+                else d2w[w0 + at] += 0.5;
             }
-            for (int j = 0; j < GRIST_D2P; j++) d2w_f[b0 + j] = (float)d2w[b0 + j];
+            for (int j = 0; j < 8; j++) d2w_f[w0 + j] = (float)d2w[w0 + j];
         }
         int n = desc->n_edges_on_edge[o];
         for (int j = 0; j < GRIST_MAXEOE; j++) {
@@ -377,10 +399,11 @@ extern "C" int grist_mesh_create(const grist_mesh_desc *desc, int device, grist_
            o_hrdc = ar.add(hrdc.size() * 8),
            o_dc2 = ar.add(dc2.size() * 8), o_dc2f = ar.add(dc2_f.size() * 4), o_d2i = ar.add(d2i.size() * 4),
            o_d2c = ar.add(d2c.size() * 8), o_d2cf = ar.add(d2c_f.size() * 4), o_eoe = ar.add(eoe.size() * 4),
-           o_d2w = ar.add(d2w.size() * 8), o_d2wf = ar.add(d2w_f.size() * 4),
+           o_d2w = ar.add(d2w.size() * 8), o_d2wf = ar.add(d2w_f.size() * 4), o_d2wi = ar.add(d2wi.size() * 4),
            o_wpv = ar.add(wpv.size() * 8), o_wpvf = ar.add(wpv_f.size() * 4), o_eov = ar.add(eov.size() * 4),
            o_cov = ar.add(cov.size() * 4), o_ccurl = ar.add(ccurl.size() * 8), o_ccurlf = ar.add(ccurl_f.size() * 4),
-           o_ckite = ar.add(ckite.size() * 8), o_fv = ar.add(fv.size() * 8);
+           o_ckite = ar.add(ckite.size() * 8), o_fv = ar.add(fv.size() * 8), o_eoc8 = ar.add(eoc8.size() * 4),
+           o_coc8 = ar.add(coc8.size() * 4), o_cdiv8 = ar.add(cdiv8.size() * 8), o_cdiv8f = ar.add(cdiv8_f.size() * 4);
     std::vector<char> host(ar.total);
     auto put = [&](size_t off, const void *src, size_t bytes) { std::memcpy(host.data() + off, src, bytes); };
     put(o_eoc, eoc.data(), eoc.size() * 4); put(o_coc, coc.data(), coc.size() * 4);
@@ -392,11 +415,14 @@ extern "C" int grist_mesh_create(const grist_mesh_desc *desc, int device, grist_
     put(o_dc2f, dc2_f.data(), dc2_f.size() * 4); put(o_d2i, d2i.data(), d2i.size() * 4);
     put(o_d2c, d2c.data(), d2c.size() * 8); put(o_d2cf, d2c_f.data(), d2c_f.size() * 4);
     put(o_d2w, d2w.data(), d2w.size() * 8); put(o_d2wf, d2w_f.data(), d2w_f.size() * 4);
+    put(o_d2wi, d2wi.data(), d2wi.size() * 4);
     put(o_eoe, eoe.data(), eoe.size() * 4); put(o_wpv, wpv.data(), wpv.size() * 8);
     put(o_wpvf, wpv_f.data(), wpv_f.size() * 4); put(o_eov, eov.data(), eov.size() * 4);
     put(o_cov, cov.data(), cov.size() * 4); put(o_ccurl, ccurl.data(), ccurl.size() * 8);
     put(o_ccurlf, ccurl_f.data(), ccurl_f.size() * 4); put(o_ckite, ckite.data(), ckite.size() * 8);
     put(o_fv, fv.data(), fv.size() * 8);
+    put(o_eoc8, eoc8.data(), eoc8.size() * 4); put(o_coc8, coc8.data(), coc8.size() * 4);
+    put(o_cdiv8, cdiv8.data(), cdiv8.size() * 8); put(o_cdiv8f, cdiv8_f.data(), cdiv8_f.size() * 4);
 
     char *dev = nullptr;
     if (cudaMalloc(&dev, ar.total) != cudaSuccess) { delete m; return GRIST_ENOMEM; }
@@ -415,12 +441,15 @@ extern "C" int grist_mesh_create(const grist_mesh_desc *desc, int device, grist_
     D.nC = nC; D.nE = nE; D.nV = nV;
     D.eoc = place<int32_t>(dev, o_eoc); D.coc = place<int32_t>(dev, o_coc);
     D.cdiv = place<double>(dev, o_cdiv); D.cdiv_f = place<float>(dev, o_cdivf);
+    D.eoc8 = place<int32_t>(dev, o_eoc8); D.coc8 = place<int32_t>(dev, o_coc8);
+    D.cdiv8 = place<double>(dev, o_cdiv8); D.cdiv8_f = place<float>(dev, o_cdiv8f);
     D.kec2 = place<double>(dev, o_kec); D.area = place<double>(dev, o_area);
     D.coe = place<int2>(dev, o_coe); D.voe = place<int2>(dev, o_voe);
     D.rdc = place<double>(dev, o_rdc); D.hrdc = place<double>(dev, o_hrdc);
     D.dc2 = place<double>(dev, o_dc2); D.dc2_f = place<float>(dev, o_dc2f);
     D.d2i = place<int32_t>(dev, o_d2i); D.d2c = place<double>(dev, o_d2c); D.d2c_f = place<float>(dev, o_d2cf);
-    D.d2w = place<double>(dev, o_d2w); D.d2w_f = place<float>(dev, o_d2wf); D.d2w_ok = d2w_ok;
+    D.d2w = place<double>(dev, o_d2w); D.d2w_f = place<float>(dev, o_d2wf); D.d2wi = place<int32_t>(dev, o_d2wi);
+    D.d2w_ok = d2w_ok;
     D.eoe = place<int32_t>(dev, o_eoe); D.wpv = place<double>(dev, o_wpv); D.wpv_f = place<float>(dev, o_wpvf);
     D.eov = place<int32_t>(dev, o_eov); D.cov = place<int32_t>(dev, o_cov);
     D.ccurl = place<double>(dev, o_ccurl); D.ccurl_f = place<float>(dev, o_ccurlf);

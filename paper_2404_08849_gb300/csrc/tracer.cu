@@ -203,6 +203,20 @@ __device__ __forceinline__ typename Vec2<TC>::T dv_at(const MemberDev &mb, size_
     return lds<PERS>((const typename Vec2<TC>::T *)mb.DV + x);
 }
 
+// A cell's edges, neighbours and divergence weights, read once per work
+// item (rows of 8, 16-byte vectors) and shared by its levels.
+static_assert(GRIST_MAXE == 6, "cell rows hold 6 entries");
+template <typename TW> struct CellRow {
+    int e[GRIST_MAXE], nb[GRIST_MAXE];
+    TW cw[GRIST_MAXE];
+};
+template <bool NB, typename TW>
+__device__ __forceinline__ void load_cell_row(const DevMesh &m, int i, CellRow<TW> &r) {
+    load_row6(m.eoc8, i, r.e);
+    if (NB) load_row6(m.coc8, i, r.nb);
+    load_row6(Coef<TW>::cdiv8(m), i, r.cw);
+}
+
 // Tracer continuity of the member: div F of the FP64 time-mean mass flux,
 // summed in FP64, stored with dpi^n as the {dpi, div F} pair of the later
 // phases (rounded to binary32 in the binary32 policy).  In that policy each
@@ -210,12 +224,12 @@ __device__ __forceinline__ typename Vec2<TC>::T dv_at(const MemberDev &mb, size_
 // cell it leaves: positive divergence coefficient), so they read 4 bytes
 // per edge-level instead of 8.
 template <typename TC>
-__device__ __forceinline__ void item_div(const DevMesh &m, const MemberDev &mb, int i, int k) {
+__device__ __forceinline__ void item_div(const MemberDev &mb, const CellRow<double> &r, int i, int k) {
     double s = 0.0;
 #pragma unroll
     for (int j = 0; j < GRIST_MAXE; j++) {
-        const int e = ldg(m.eoc + i * 6 + j);
-        const double cw = ldg(m.cdiv + i * 6 + j);
+        const int e = r.e[j];
+        const double cw = r.cw[j];
         const double f = ldg(mb.F + (size_t)e * mb.ld + k);
         s += cw * f;
         if (sizeof(TC) == 4 && cw > 0.0) ((float *)mb.Ff)[(size_t)e * mb.ld + k] = cv<float>(f);
@@ -252,14 +266,9 @@ __device__ __forceinline__ void item_edge(const DevMesh &m, const MemberDev &mb,
         // one weighted sum over the upwind side's stencil (the mean of c1 and
         // c2 folded into the weights)
         const int side = f >= (TC)0 ? 0 : 1;
-        const TC *cw = Coef<TC>::d2w(m) + (size_t)e * 14 + side * GRIST_D2P;
         int idx[GRIST_D2P];
         TC w[GRIST_D2P];
-#pragma unroll
-        for (int j = 0; j < GRIST_D2P; j++) {
-            idx[j] = ldg(st + side * GRIST_D2P + j);
-            w[j] = ldg(cw + j);
-        }
+        load_d2w(m, e, side, idx, w);
         for (int t = t0; t < t1; t++) {
             const TQ *qt = q + (size_t)t * mb.qs;
             TC v = 0;
@@ -301,24 +310,59 @@ __device__ __forceinline__ void item_edge(const DevMesh &m, const MemberDev &mb,
     }
 }
 
+// The edge item over a thread's LPT levels kg, kg + Lg, ...  With the
+// combined weights, the upwind side's stencil (4 vector loads) is read once
+// and read again only for a level whose flux runs the other way.
+template <bool PERS, typename TQ, typename TC, int LPT>
+__device__ __forceinline__ void item_edge_levels(const DevMesh &m, const MemberDev &mb, const TQ *q, int t0, int t1,
+                                                 int e, int kg, bool beta1, TC beta) {
+    if (!(beta1 && m.d2w_ok)) {
+#pragma unroll
+        for (int u = 0; u < LPT; u++) {
+            const int k = kg + u * mb.Lg;
+            if (LPT > 1 && k >= mb.L) break;
+            item_edge<PERS, TQ, TC>(m, mb, q, t0, t1, e, k, beta1, beta);
+        }
+        return;
+    }
+    const int ld = mb.ld;
+    TC *FH = (TC *)mb.FH;
+    int idx[GRIST_D2P];
+    TC w[GRIST_D2P];
+    int loaded = -1;
+#pragma unroll
+    for (int u = 0; u < LPT; u++) {
+        const int k = kg + u * mb.Lg;
+        if (LPT > 1 && k >= mb.L) break;
+        const TC f = flux_at<PERS, TC>(mb, (size_t)e * ld + k);
+        const int side = f >= (TC)0 ? 0 : 1;
+        if (side != loaded) {
+            load_d2w(m, e, side, idx, w);
+            loaded = side;
+        }
+        for (int t = t0; t < t1; t++) {
+            const TQ *qt = q + (size_t)t * mb.qs;
+            TC v = 0;
+#pragma unroll
+            for (int j = 0; j < GRIST_D2P; j++) v += w[j] * static_cast<TC>(lds<PERS>(qt + (size_t)idx[j] * ld + k));
+            FH[(size_t)t * mb.fs + (size_t)e * ld + k] = f * v;
+        }
+    }
+}
+
 // RK stage update: q^(s) = (dpi^n q^n - dt_s div F^H) / dpi^(s),
 // written as r1 q^n - r2 div with r1 = dpi^n/dpi^(s), r2 = dt_s/dpi^(s)
 // taken once per (cell, level) in FP64 and rounded to the tracer type
 // (Sec. 2.2 (ii): no mixed-kind products inside the tracer loop).
 template <bool PERS, typename TQ, typename TC>
-__device__ __forceinline__ bool item_update(const DevMesh &m, const MemberDev &mb, TQ *qout, int t0, int t1, int i,
+__device__ __forceinline__ bool item_update(const CellRow<TC> &r, const MemberDev &mb, TQ *qout, int t0, int t1, int i,
                                             int k, double dts, float dtsf) {
     const int ld = mb.ld;
     const size_t x = (size_t)i * ld + k;
     TC r1, r2;
     stage_ratios(dv_at<PERS, TC>(mb, x), dts, dtsf, r1, r2);
-    int eidx[GRIST_MAXE];
-    TC cw[GRIST_MAXE];
-#pragma unroll
-    for (int j = 0; j < GRIST_MAXE; j++) {
-        eidx[j] = ldg(m.eoc + i * 6 + j);
-        cw[j] = ldg(Coef<TC>::cdiv(m) + i * 6 + j);
-    }
+    const int *eidx = r.e;
+    const TC *cw = r.cw;
     const TQ *qn = (const TQ *)mb.q;
     const TC *FH = (const TC *)mb.FH;
     bool bad = false;
@@ -346,21 +390,17 @@ __device__ __forceinline__ TC upwind_flux(TC f, TC cw, int i, int nb, const TQ *
 
 // FCT 1: low-order solution q^td = (dpi^n q^n - dt div F^L) / dpi^(3).
 template <bool PERS, typename TQ, typename TC>
-__device__ __forceinline__ void item_lowres(const DevMesh &m, const MemberDev &mb, int t0, int t1, int i, int k,
+__device__ __forceinline__ void item_lowres(const CellRow<TC> &r, const MemberDev &mb, int t0, int t1, int i, int k,
                                             double dt, float dtf) {
     const int ld = mb.ld;
     const size_t x = (size_t)i * ld + k;
     TC r1, r2;
     stage_ratios(dv_at<PERS, TC>(mb, x), dt, dtf, r1, r2);
-    int nb[GRIST_MAXE];
-    TC cw[GRIST_MAXE], fe[GRIST_MAXE];
+    const int *nb = r.nb;
+    const TC *cw = r.cw;
+    TC fe[GRIST_MAXE];
 #pragma unroll
-    for (int j = 0; j < GRIST_MAXE; j++) {
-        const int e = ldg(m.eoc + i * 6 + j);
-        nb[j] = ldg(m.coc + i * 6 + j);
-        cw[j] = ldg(Coef<TC>::cdiv(m) + i * 6 + j);
-        fe[j] = flux_at<PERS, TC>(mb, (size_t)e * ld + k);
-    }
+    for (int j = 0; j < GRIST_MAXE; j++) fe[j] = flux_at<PERS, TC>(mb, (size_t)r.e[j] * ld + k);
     const TQ *qn = (const TQ *)mb.q;
     TQ *qtd = (TQ *)mb.qA;
     for (int t = t0; t < t1; t++) {
@@ -376,21 +416,17 @@ __device__ __forceinline__ void item_lowres(const DevMesh &m, const MemberDev &m
 // antidiffusive in/out sums P+-, allowed changes Q+-, ratios
 // R+- = min(1, Q / (P + TINY)) (Sec. 2.2 (iii): TINY of the working type).
 template <bool PERS, typename TQ, typename TC>
-__device__ __forceinline__ void item_ratios(const DevMesh &m, const MemberDev &mb, int t0, int t1, int i, int k,
+__device__ __forceinline__ void item_ratios(const CellRow<TC> &r, const MemberDev &mb, int t0, int t1, int i, int k,
                                             double dt, float dtf) {
     const int ld = mb.ld;
     const size_t x = (size_t)i * ld + k;
     const TC dp3 = static_cast<TC>(end_mass(dv_at<PERS, TC>(mb, x), dt, dtf));
     const TC dtc = sizeof(TC) == 4 ? (TC)dtf : (TC)dt;
-    int nb[GRIST_MAXE], eidx[GRIST_MAXE];
-    TC cw[GRIST_MAXE], fe[GRIST_MAXE];
+    const int *nb = r.nb, *eidx = r.e;
+    const TC *cw = r.cw;
+    TC fe[GRIST_MAXE];
 #pragma unroll
-    for (int j = 0; j < GRIST_MAXE; j++) {
-        eidx[j] = ldg(m.eoc + i * 6 + j);
-        nb[j] = ldg(m.coc + i * 6 + j);
-        cw[j] = ldg(Coef<TC>::cdiv(m) + i * 6 + j);
-        fe[j] = flux_at<PERS, TC>(mb, (size_t)eidx[j] * ld + k);
-    }
+    for (int j = 0; j < GRIST_MAXE; j++) fe[j] = flux_at<PERS, TC>(mb, (size_t)eidx[j] * ld + k);
     const TQ *qn = (const TQ *)mb.q, *qtd = (const TQ *)mb.qA;
     const TC *FH = (const TC *)mb.FH;
     TC *Rp = (TC *)mb.Rp, *Rm = (TC *)mb.Rm;
@@ -427,21 +463,17 @@ __device__ __forceinline__ void item_ratios(const DevMesh &m, const MemberDev &m
 // antidiffusive flux A runs c1 -> c2 (A >= 0), min(R+(c1), R-(c2)) else;
 // q^{n+1} = (dpi^n q^n - dt div(F^L + C A)) / dpi^(3) into qB.
 template <bool PERS, typename TQ, typename TC>
-__device__ __forceinline__ bool item_final(const DevMesh &m, const MemberDev &mb, int t0, int t1, int i, int k,
+__device__ __forceinline__ bool item_final(const CellRow<TC> &r, const MemberDev &mb, int t0, int t1, int i, int k,
                                            double dt, float dtf) {
     const int ld = mb.ld;
     const size_t x = (size_t)i * ld + k;
     TC r1, r2;
     stage_ratios(dv_at<PERS, TC>(mb, x), dt, dtf, r1, r2);
-    int nb[GRIST_MAXE], eidx[GRIST_MAXE];
-    TC cw[GRIST_MAXE], fe[GRIST_MAXE];
+    const int *nb = r.nb, *eidx = r.e;
+    const TC *cw = r.cw;
+    TC fe[GRIST_MAXE];
 #pragma unroll
-    for (int j = 0; j < GRIST_MAXE; j++) {
-        eidx[j] = ldg(m.eoc + i * 6 + j);
-        nb[j] = ldg(m.coc + i * 6 + j);
-        cw[j] = ldg(Coef<TC>::cdiv(m) + i * 6 + j);
-        fe[j] = flux_at<PERS, TC>(mb, (size_t)eidx[j] * ld + k);
-    }
+    for (int j = 0; j < GRIST_MAXE; j++) fe[j] = flux_at<PERS, TC>(mb, (size_t)eidx[j] * ld + k);
     const TQ *qn = (const TQ *)mb.q;
     const TC *FH = (const TC *)mb.FH;
     const TC *Rp = (const TC *)mb.Rp, *Rm = (const TC *)mb.Rm;
@@ -506,21 +538,31 @@ __device__ void run_phase(const DevMesh &m, const Batch &B, uint32_t *status) {
         split_index((uint32_t)(n - S.start[seg]), mb.DL, ent, kg);
         const int t0 = mg.y * B.tpt;
         const int t1 = min(mb.T, t0 + B.tpt);
+        if (PH == P_EDGE0) item_edge_levels<PERS, TQ, TC, LPT>(m, mb, (const TQ *)mb.q, t0, t1, ent, kg, B.beta1, beta);
+        if (PH == P_EDGE1) item_edge_levels<PERS, TQ, TC, LPT>(m, mb, (const TQ *)mb.qA, t0, t1, ent, kg, B.beta1, beta);
+        if (PH == P_EDGE2) item_edge_levels<PERS, TQ, TC, LPT>(m, mb, (const TQ *)mb.qB, t0, t1, ent, kg, B.beta1, beta);
+        if (PH == P_EDGE0 || PH == P_EDGE1 || PH == P_EDGE2) continue;
+        // the cell's row, once for its LPT levels (FP64 weights for the
+        // continuity phase); the limited-flux phase, the one with the most
+        // live values per level, reads it again for each level instead
+        using TW = typename std::conditional<PH == P_DIV, double, TC>::type;
+        constexpr bool kNb = PH == P_LOWRES || PH == P_RATIOS || PH == P_FINAL;
+        constexpr bool kRowPerLevel = PH == P_FINAL;
+        CellRow<TW> r;
+        if (PH != P_COPY && !kRowPerLevel) load_cell_row<kNb>(m, ent, r);
 #pragma unroll
         for (int u = 0; u < LPT; u++) {
         const int k = kg + u * mb.Lg;
         if (LPT > 1 && k >= mb.L) break;
-        if (PH == P_DIV) item_div<TC>(m, mb, ent, k);
-        if (PH == P_EDGE0) item_edge<PERS, TQ, TC>(m, mb, (const TQ *)mb.q, t0, t1, ent, k, B.beta1, beta);
-        if (PH == P_EDGE1) item_edge<PERS, TQ, TC>(m, mb, (const TQ *)mb.qA, t0, t1, ent, k, B.beta1, beta);
-        if (PH == P_EDGE2) item_edge<PERS, TQ, TC>(m, mb, (const TQ *)mb.qB, t0, t1, ent, k, B.beta1, beta);
-        if (PH == P_UPD0) bad |= item_update<PERS, TQ, TC>(m, mb, (TQ *)mb.qA, t0, t1, ent, k, dts, dtsf);
-        if (PH == P_UPD1) bad |= item_update<PERS, TQ, TC>(m, mb, (TQ *)mb.qB, t0, t1, ent, k, dts, dtsf);
-        if (PH == P_UPD2) bad |= item_update<PERS, TQ, TC>(m, mb, (TQ *)mb.q, t0, t1, ent, k, dts, dtsf);
-        if (PH == P_LOWRES) item_lowres<PERS, TQ, TC>(m, mb, t0, t1, ent, k, B.dt, dtf);
-        if (PH == P_RATIOS) item_ratios<PERS, TQ, TC>(m, mb, t0, t1, ent, k, B.dt, dtf);
-        if (PH == P_FINAL) bad |= item_final<PERS, TQ, TC>(m, mb, t0, t1, ent, k, B.dt, dtf);
-        if (PH == P_COPY) item_copy<PERS, TQ>(mb, t0, t1, ent, k);
+        if (kRowPerLevel) load_cell_row<kNb>(m, ent, r);
+        if constexpr (PH == P_DIV) item_div<TC>(mb, r, ent, k);
+        if constexpr (PH == P_UPD0) bad |= item_update<PERS, TQ, TC>(r, mb, (TQ *)mb.qA, t0, t1, ent, k, dts, dtsf);
+        if constexpr (PH == P_UPD1) bad |= item_update<PERS, TQ, TC>(r, mb, (TQ *)mb.qB, t0, t1, ent, k, dts, dtsf);
+        if constexpr (PH == P_UPD2) bad |= item_update<PERS, TQ, TC>(r, mb, (TQ *)mb.q, t0, t1, ent, k, dts, dtsf);
+        if constexpr (PH == P_LOWRES) item_lowres<PERS, TQ, TC>(r, mb, t0, t1, ent, k, B.dt, dtf);
+        if constexpr (PH == P_RATIOS) item_ratios<PERS, TQ, TC>(r, mb, t0, t1, ent, k, B.dt, dtf);
+        if constexpr (PH == P_FINAL) bad |= item_final<PERS, TQ, TC>(r, mb, t0, t1, ent, k, B.dt, dtf);
+        if constexpr (PH == P_COPY) item_copy<PERS, TQ>(mb, t0, t1, ent, k);
         }
     }
     if (bad) atomicOr(status, GRIST_FLAG_NONFINITE);
@@ -543,7 +585,7 @@ __device__ void run_phase(const DevMesh &m, const Batch &B, uint32_t *status) {
 #define GRIST_TR_REGS_LOWRES 64
 #endif
 #ifndef GRIST_TR_REGS_RATIOS
-#define GRIST_TR_REGS_RATIOS 0
+#define GRIST_TR_REGS_RATIOS 96
 #endif
 #ifndef GRIST_TR_REGS_FINAL
 #define GRIST_TR_REGS_FINAL 0
