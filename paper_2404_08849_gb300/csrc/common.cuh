@@ -72,6 +72,7 @@ struct DevMesh {
     const float *ccurl_f;
     const double *ckite;  // [nV][3]
     const double *fv;     // [nV]
+    const float *fv_f;
 };
 
 // Division of a flat (entity, level) index by the level count without a

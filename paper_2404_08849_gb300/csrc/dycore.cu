@@ -256,12 +256,10 @@ __global__ void k_mass_col(DevMesh m, DyPar d, const typename P::TM *__restrict_
         const double rdps = __shfl_sync(0xffffffffu, rdps_l, c);
         int eidx[GRIST_MAXE];
         TM cw[GRIST_MAXE];
-#pragma unroll
-        for (int j = 0; j < GRIST_MAXE; j++) {
-            eidx[j] = ldg(m.eoc + i * 6 + j);
-            cw[j] = ldg(Coef<TM>::cdiv(m) + i * 6 + j);
-        }
+        load_row6(m.eoc8, i, eidx);
+        load_row6(Coef<TM>::cdiv8(m), i, cw);
         double run = 0.0;
+        F2 runf{0.f, 0.f};
         for (int ch = 0; ch < nch; ch++) {
             const int k = ch * 32 + lane;
             TM s = 0;
@@ -290,19 +288,21 @@ __global__ void k_mass_col(DevMesh m, DyPar d, const typename P::TM *__restrict_
                 }
                 run += __shfl_sync(0xffffffffu, v, 31);
             } else {
+                // the earlier chunks' total is carried as a compensated pair
+                // too, so the prefix reaches FP64 once, at M
                 F2 v{cv<float>(s), 0.f};
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
                     const F2 t = f2_shfl_up(v, o);
                     if (lane >= o) v = f2_add(v, t);
                 }
+                v = f2_add(v, runf);
                 if (k < d.L - 1) {
-                    const double mk = -ldg(d.B + k + 1) * pst - (run + (f2d(v.hi) + f2d(v.lo)));
+                    const double mk = -ldg(d.B + k + 1) * pst - (f2d(v.hi) + f2d(v.lo));
                     Mv[(size_t)i * d.ldi + k + 1] = mk;
                     if (Macc) Macc[(size_t)i * d.ldi + k + 1] += fscale * mk;
                 }
-                const F2 last{__shfl_sync(0xffffffffu, v.hi, 31), __shfl_sync(0xffffffffu, v.lo, 31)};
-                run += f2d(last.hi) + f2d(last.lo);
+                runf = F2{__shfl_sync(0xffffffffu, v.hi, 31), __shfl_sync(0xffffffffu, v.lo, 31)};
             }
         }
     }
@@ -358,25 +358,35 @@ __global__ void k_theta_flux(DevMesh m, DyPar d, LevelDiv Dh, const typename P::
 
 // Eq. 4 update: dpi theta^(s) = dpi theta^n + dt_s (-div F_theta - delta(M theta)).
 template <class P>
-__global__ void k_theta_update(DevMesh m, DyPar d, LevelDiv Dv, const typename P::TA *__restrict__ Fth,
+__global__ void k_theta_update(DevMesh m, DyPar d, LevelDiv Dh, const typename P::TA *__restrict__ Fth,
                                const typename P::TA *__restrict__ th, const double *__restrict__ Mv,
                                const double *__restrict__ th_n, double *__restrict__ th_out, double dts) {
     using TA = typename P::TA;
+    const int Lh = (int)Dh.d;
     uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= (uint32_t)m.nC * (uint32_t)d.L) return;
-    int i, k;
-    split_index(n, Dv, i, k);
-    TA div = 0;
+    if (n >= (uint32_t)m.nC * (uint32_t)Lh) return;
+    int i, kg;
+    split_index(n, Dh, i, kg);
+    // the cell's row once for its two levels kg and kg + Lh
+    int eidx[GRIST_MAXE];
+    TA cw[GRIST_MAXE];
+    load_row6(m.eoc8, i, eidx);
+    load_row6(Coef<TA>::cdiv8(m), i, cw);
 #pragma unroll
-    for (int j = 0; j < GRIST_MAXE; j++)
-        div += ldg(Coef<TA>::cdiv(m) + i * 6 + j) * ldg(Fth + (size_t)ldg(m.eoc + i * 6 + j) * d.ld + k);
-    const size_t x = (size_t)i * d.ld + k;
-    const TA tk = th[x];
-    TA top = 0, bot = 0;
-    if (k > 0) top = cv<TA>(Mv[(size_t)i * d.ldi + k]) * ((TA)0.5 * (th[x - 1] + tk));
-    if (k < d.L - 1) bot = cv<TA>(Mv[(size_t)i * d.ldi + k + 1]) * ((TA)0.5 * (tk + th[x + 1]));
-    const TA tend = -div - (bot - top);
-    th_out[x] = th_n[x] + dts * cv<double>(tend);
+    for (int u = 0; u < 2; u++) {
+        const int k = kg + u * Lh;
+        if (k >= d.L) break;
+        TA div = 0;
+#pragma unroll
+        for (int j = 0; j < GRIST_MAXE; j++) div += cw[j] * ldg(Fth + (size_t)eidx[j] * d.ld + k);
+        const size_t x = (size_t)i * d.ld + k;
+        const TA tk = th[x];
+        TA top = 0, bot = 0;
+        if (k > 0) top = cv<TA>(Mv[(size_t)i * d.ldi + k]) * ((TA)0.5 * (th[x - 1] + tk));
+        if (k < d.L - 1) bot = cv<TA>(Mv[(size_t)i * d.ldi + k + 1]) * ((TA)0.5 * (tk + th[x + 1]));
+        const TA tend = -div - (bot - top);
+        th_out[x] = th_n[x] + dts * cv<double>(tend);
+    }
 }
 
 // Eq. 8 (hydrostatic diagnostics), one warp per column: mid-layer pressure,
@@ -434,21 +444,42 @@ __global__ void k_vertex_mass(DevMesh m, DyPar d, const double *__restrict__ ps_
 
 // Vertex PV, Sec. 2.3: zeta_p = (zeta + f) / dpi_v, the relative vorticity
 // from the circulation of u (advective type), dpi_v the kite-weighted remap
-// of the FP64 layer mass (dpi must be double for zeta_p).
+// of the FP64 layer mass (dpi must be double for zeta_p).  In a binary32
+// advective type the FP64 factor 1/dpi_v = (1/dB_k)(1/dpi_col) is formed
+// first and rounded once, then the rest is binary32 arithmetic (Sec. 2.2
+// (ii): no mixed-kind expression): one FP64 product per vertex-level.
 template <class P>
-__global__ void k_vort(DevMesh m, DyPar d, LevelDiv Dv, const typename P::TU *__restrict__ u,
+__global__ void k_vort(DevMesh m, DyPar d, LevelDiv Dh, const typename P::TU *__restrict__ u,
                        const double *__restrict__ rdpv, typename P::TA *__restrict__ qv) {
     using TA = typename P::TA;
+    const int Lh = (int)Dh.d;
     uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= (uint32_t)m.nV * (uint32_t)d.L) return;
-    int v, k;
-    split_index(n, Dv, v, k);
-    TA z = 0;
+    if (n >= (uint32_t)m.nV * (uint32_t)Lh) return;
+    int v, kg;
+    split_index(n, Dh, v, kg);
+    // the vertex's edges and weights once for its two levels kg and kg + Lh
+    int ev[3];
+    TA cc[3];
 #pragma unroll
-    for (int j = 0; j < 3; j++)
-        z += ldg(Coef<TA>::ccurl(m) + v * 3 + j) * cv<TA>(ldg(u + (size_t)ldg(m.eov + v * 3 + j) * d.ld + k));
-    qv[(size_t)v * d.ld + k] =
-        emu<P::EMU>(cv<TA>((cv<double>(z) + ldg(m.fv + v)) * (ldg(d.rdB + k) * ldg(rdpv + v))), d.emu, GRIST_ROW_PV_FLUX);
+    for (int j = 0; j < 3; j++) {
+        ev[j] = ldg(m.eov + v * 3 + j);
+        cc[j] = ldg(Coef<TA>::ccurl(m) + v * 3 + j);
+    }
+    const double rv = ldg(rdpv + v);
+#pragma unroll
+    for (int w = 0; w < 2; w++) {
+        const int k = kg + w * Lh;
+        if (k >= d.L) break;
+        TA z = 0;
+#pragma unroll
+        for (int j = 0; j < 3; j++) z += cc[j] * cv<TA>(ldg(u + (size_t)ev[j] * d.ld + k));
+        if constexpr (sizeof(TA) == 4) {
+            qv[(size_t)v * d.ld + k] = (z + ldg(m.fv_f + v)) * d2f(ldg(d.rdB + k) * rv);
+        } else {
+            qv[(size_t)v * d.ld + k] = emu<P::EMU>(cv<TA>((cv<double>(z) + ldg(m.fv + v)) * (ldg(d.rdB + k) * rv)),
+                                                   d.emu, GRIST_ROW_PV_FLUX);
+        }
+    }
 }
 
 // Cell kinetic energy, stored doubled: 2K = sum (dc dv / 2A) u^2 (FP64:
@@ -986,7 +1017,8 @@ int dycore_step(grist_mesh_s *h, grist_dycore_state *S, const grist_dycore_param
                    gV = grid_for((long long)m.nV * L, kBlock), gW = grid_for((long long)m.nC * 32, kBlock),
                    gI = grid_for((long long)m.nC * (L + 1), kBlock), gSolve = grid_for(m.nC, kSolveCols),
                    gVx = grid_for(m.nV, kBlock), gE32 = grid_for((long long)m.nE + 31, kBlock),
-                   gC32 = grid_for((long long)m.nC + 31, kBlock), gEH = grid_for((long long)m.nE * DH.d, kBlock);
+                   gC32 = grid_for((long long)m.nC + 31, kBlock), gEH = grid_for((long long)m.nE * DH.d, kBlock),
+                   gCH = grid_for((long long)m.nC * DH.d, kBlock), gVH = grid_for((long long)m.nV * DH.d, kBlock);
     const double dts[3] = {dt / 3.0, dt / 2.0, dt};
     const double ascale = S->accum_scale != 0.0 ? S->accum_scale : 1.0;
 
@@ -1021,8 +1053,8 @@ int dycore_step(grist_mesh_s *h, grist_dycore_state *S, const grist_dycore_param
             m, d, F, fcol, ps_in, psN, ps_outs[s3], th_in, theta, Mv, h3, s3 == 0 ? S->dpi_start : nullptr, rdps,
             (NH && s3 == 0) ? rthn : nullptr, s3 == 2 ? S->vmass_flux_accum : nullptr, ascale));
         GRIST_LAUNCH(h, PN("k_theta_flux"), st, k_theta_flux<P><<<gEH, kBlock, 0, st>>>(m, d, DH, F, theta, Fth));
-        GRIST_LAUNCH(h, PN("k_theta_update"), st, k_theta_update<P><<<gC, kBlock, 0, st>>>(
-            m, d, DL, Fth, theta, Mv, S->dpi_theta, th_outs[s3], h3));
+        GRIST_LAUNCH(h, PN("k_theta_update"), st, k_theta_update<P><<<gCH, kBlock, 0, st>>>(
+            m, d, DH, Fth, theta, Mv, S->dpi_theta, th_outs[s3], h3));
         if (NH) {
             if (s3 == 0)
                 GRIST_LAUNCH(h, PN("k_nh_explicit"), st, k_nh_explicit<P, true><<<gI, kBlock, 0, st>>>(
@@ -1038,7 +1070,7 @@ int dycore_step(grist_mesh_s *h, grist_dycore_state *S, const grist_dycore_param
                 m, d, ps_outs[s3], th_outs[s3], p, alp, phl));
         }
         GRIST_LAUNCH(h, PN("k_vertex_mass"), st, k_vertex_mass<P::EMU><<<gVx, kBlock, 0, st>>>(m, d, ps_in, rdpv));
-        GRIST_LAUNCH(h, PN("k_vort"), st, k_vort<P><<<gV, kBlock, 0, st>>>(m, d, DL, u_in, rdpv, qv));
+        GRIST_LAUNCH(h, PN("k_vort"), st, k_vort<P><<<gVH, kBlock, 0, st>>>(m, d, DH, u_in, rdpv, qv));
         GRIST_LAUNCH(h, PN("k_ke"), st, k_ke<P><<<gC, kBlock, 0, st>>>(m, d, DL, u_in, K));
         GRIST_LAUNCH(h, PN("k_momentum"), st, k_momentum<P, NH><<<gE, kBlock, 0, st>>>(
             m, d, DL, u_in, u, u_outs[s3], F, qv, K, Mv, rsum, p_outs[s3], alp, phl, dpp, h3, status));

@@ -375,11 +375,13 @@ extern "C" int grist_mesh_create(const grist_mesh_desc *desc, int device, grist_
     }
     std::vector<int32_t> eov(3 * (size_t)nV), cov(3 * (size_t)nV);
     std::vector<double> ccurl(3 * (size_t)nV), ckite(3 * (size_t)nV), fv(nV);
+    std::vector<float> fv_f(nV);
     std::vector<float> ccurl_f(3 * (size_t)nV);
     for (int v = 0; v < nV; v++) {
         int o = vold[v];
         double Av = desc->vertex_area[o];
         fv[v] = desc->f_vertex[o];
+        fv_f[v] = (float)fv[v];
         for (int j = 0; j < 3; j++) {
             size_t x = (size_t)v * 3 + j;
             int e = desc->edges_on_vertex[3 * o + j];
@@ -402,7 +404,7 @@ extern "C" int grist_mesh_create(const grist_mesh_desc *desc, int device, grist_
            o_d2w = ar.add(d2w.size() * 8), o_d2wf = ar.add(d2w_f.size() * 4), o_d2wi = ar.add(d2wi.size() * 4),
            o_wpv = ar.add(wpv.size() * 8), o_wpvf = ar.add(wpv_f.size() * 4), o_eov = ar.add(eov.size() * 4),
            o_cov = ar.add(cov.size() * 4), o_ccurl = ar.add(ccurl.size() * 8), o_ccurlf = ar.add(ccurl_f.size() * 4),
-           o_ckite = ar.add(ckite.size() * 8), o_fv = ar.add(fv.size() * 8), o_eoc8 = ar.add(eoc8.size() * 4),
+           o_ckite = ar.add(ckite.size() * 8), o_fv = ar.add(fv.size() * 8), o_fvf = ar.add(fv_f.size() * 4), o_eoc8 = ar.add(eoc8.size() * 4),
            o_coc8 = ar.add(coc8.size() * 4), o_cdiv8 = ar.add(cdiv8.size() * 8), o_cdiv8f = ar.add(cdiv8_f.size() * 4);
     std::vector<char> host(ar.total);
     auto put = [&](size_t off, const void *src, size_t bytes) { std::memcpy(host.data() + off, src, bytes); };
@@ -420,7 +422,7 @@ extern "C" int grist_mesh_create(const grist_mesh_desc *desc, int device, grist_
     put(o_wpvf, wpv_f.data(), wpv_f.size() * 4); put(o_eov, eov.data(), eov.size() * 4);
     put(o_cov, cov.data(), cov.size() * 4); put(o_ccurl, ccurl.data(), ccurl.size() * 8);
     put(o_ccurlf, ccurl_f.data(), ccurl_f.size() * 4); put(o_ckite, ckite.data(), ckite.size() * 8);
-    put(o_fv, fv.data(), fv.size() * 8);
+    put(o_fv, fv.data(), fv.size() * 8); put(o_fvf, fv_f.data(), fv_f.size() * 4);
     put(o_eoc8, eoc8.data(), eoc8.size() * 4); put(o_coc8, coc8.data(), coc8.size() * 4);
     put(o_cdiv8, cdiv8.data(), cdiv8.size() * 8); put(o_cdiv8f, cdiv8_f.data(), cdiv8_f.size() * 4);
 
@@ -453,7 +455,7 @@ extern "C" int grist_mesh_create(const grist_mesh_desc *desc, int device, grist_
     D.eoe = place<int32_t>(dev, o_eoe); D.wpv = place<double>(dev, o_wpv); D.wpv_f = place<float>(dev, o_wpvf);
     D.eov = place<int32_t>(dev, o_eov); D.cov = place<int32_t>(dev, o_cov);
     D.ccurl = place<double>(dev, o_ccurl); D.ccurl_f = place<float>(dev, o_ccurlf);
-    D.ckite = place<double>(dev, o_ckite); D.fv = place<double>(dev, o_fv);
+    D.ckite = place<double>(dev, o_ckite); D.fv = place<double>(dev, o_fv); D.fv_f = place<float>(dev, o_fvf);
     *out = m;
     return GRIST_OK;
 }
