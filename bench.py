@@ -377,9 +377,12 @@ def gpu_arm(args, wl):
     def run_prec(prec, sample_clocks=False):
       with torch.cuda.stream(side):
         s = make_state(torch, host, prec, device, nE, nC, L, T, wl["nh"])
+        if args.tracer_tuning:
+            mesh.set_tracer_tuning(**json.loads(args.tracer_tuning))
+            tunings[prec] = mesh.tracer_tuning()
         for w in range(W):
             step(mesh, s, P, wl, prec)
-            if w == 0 and T and not args.no_autotune:
+            if w == 0 and T and not args.no_autotune and not args.tracer_tuning:
                 # the tracer launch configuration from the library's autotuner,
                 # on this step's own tracer inputs (restored after timing)
                 tunings[prec] = mesh.autotune_tracer(
@@ -796,6 +799,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="default tracer launch configuration")
+    ap.add_argument("--tracer-tuning", default=None,
+                    help="tracer launch configuration as JSON (keys of Mesh.set_tracer_tuning), no autotuning")
     ap.add_argument("--no-fp64-peak", action="store_true", help="skip the FP64 FMA-rate measurement")
     ap.add_argument("--no-secondary", action="store_true", help="skip the L6 hydrostatic and L8 NH lines")
     ap.add_argument("--eager", action="store_true",

@@ -142,6 +142,21 @@ int grist_mesh_permutation(grist_mesh mesh, int32_t *cell_new_of_old, int32_t *e
 /* Entity counts of the handle (any pointer may be NULL). */
 int grist_mesh_counts(grist_mesh mesh, int32_t *n_cells, int32_t *n_edges, int32_t *n_vertices);
 
+/* Properties of the mesh's stencils found at creation, as bits of *flags:
+ *   GRIST_MESH_COMBINED_STENCIL  every edge side's stencil contains c1 and
+ *                                c2, so with beta_upwind = 1 the edge value
+ *                                is one weighted sum (Sec. 2.1's third-order
+ *                                flux, the cell mean folded into the weights)
+ *   GRIST_MESH_RING_STENCIL      in addition every edge side's stencil is its
+ *                                cell's neighbour ring in the cell's order,
+ *                                and the cell is c1 exactly when its
+ *                                divergence sign is positive (the condition
+ *                                of grist_tracer_tuning.cell_edges)
+ * GRIST_EINVAL for a NULL argument.  Host only. */
+#define GRIST_MESH_COMBINED_STENCIL 1u
+#define GRIST_MESH_RING_STENCIL 2u
+int grist_mesh_features(grist_mesh mesh, uint32_t *flags);
+
 /* ---------------------------------------------------------------------- */
 /* Tracer transport (Eq. 10, horizontal; Sec. 2.1, Sec. 2.3)               */
 /* ---------------------------------------------------------------------- */
@@ -225,22 +240,31 @@ int grist_tracer_step(grist_mesh mesh, const grist_tracer_batch *batch, double d
  *   levels_per_thread   1 or 2: levels one thread of a per-phase launch
  *                       carries (levels g and g + ceil(L/2) for 2; the
  *                       entity's stencil tables are read once for both);
- *                       the persistent launch uses 1. */
+ *                       the persistent launch uses 1.
+ *   cell_edges          1 = with beta_upwind = 1 the edge fluxes are formed
+ *                       cell-centrically: the thread of a cell gathers q over
+ *                       the cell and its neighbours once and writes the flux
+ *                       of every edge whose flux leaves the cell (same
+ *                       weights, same summation order: bit-identical to 0,
+ *                       the edge-centric form, which is also used whenever
+ *                       beta_upwind != 1 or the mesh's stencils are not the
+ *                       upwind cell's neighbour ring). */
 typedef struct {
-    int32_t block, tracers_per_thread, persistent, use_graph, fused, levels_per_thread;
+    int32_t block, tracers_per_thread, persistent, use_graph, fused, levels_per_thread, cell_edges;
 } grist_tracer_tuning;
 
 /* Set / get the tuning used by later grist_tracer_step calls on the mesh
  * (default: block 128, tracers_per_thread 4, persistent 0, use_graph 0,
- * fused 0, levels_per_thread 2 - the autotuner's choice on the level-9
- * mesh with 60 levels and 4 tracers).
+ * fused 0, levels_per_thread 2, cell_edges 1 - the autotuner's choice on
+ * the level-9 mesh with 60 levels and 4 tracers).
  * GRIST_EINVAL for out-of-range values. */
 int grist_tracer_set_tuning(grist_mesh mesh, const grist_tracer_tuning *tuning);
 int grist_tracer_get_tuning(grist_mesh mesh, grist_tracer_tuning *tuning);
 
 /* Autotuner: time candidate tunings (block sizes - hence cells per block -
  * tracers per thread, fused tiles on/off, then levels per thread at the
- * best of those, then per-phase vs persistent launch and graph on/off) on
+ * best of those, the edge-flux form, then per-phase vs persistent launch
+ * and graph on/off) on
  * `steps` tracer steps of
  * the given batch, keep the fastest as the mesh's tuning and return it in
  * *best (and its mean step time in milliseconds in *best_ms, may be NULL).

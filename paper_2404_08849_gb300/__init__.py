@@ -182,6 +182,13 @@ class Mesh:
         self.edge_old = np.argsort(self.edge_new).astype(np.int64)
         self.vertex_old = np.argsort(self.vertex_new).astype(np.int64)
 
+    def features(self):
+        """Stencil properties found at creation (grist_mesh_features):
+        {"combined_stencil": bool, "ring_stencil": bool}."""
+        f = ctypes.c_uint32()
+        _lib.check("grist_mesh_features", _lib.load().grist_mesh_features(self.handle, ctypes.byref(f)))
+        return {"combined_stencil": bool(f.value & 1), "ring_stencil": bool(f.value & 2)}
+
     def close(self):
         if getattr(self, "handle", None):
             _lib.load().grist_mesh_destroy(self.handle)
@@ -243,16 +250,17 @@ class Mesh:
                                                               _stream_handle(stream)))
 
     def set_tracer_tuning(self, block=128, tracers_per_thread=4, persistent=False, use_graph=False, fused=False,
-                          levels_per_thread=2):
+                          levels_per_thread=2, cell_edges=True):
         t = _lib.TracerTuning(int(block), int(tracers_per_thread), int(bool(persistent)), int(bool(use_graph)),
-                              int(bool(fused)), int(levels_per_thread))
+                              int(bool(fused)), int(levels_per_thread), int(bool(cell_edges)))
         _lib.check("grist_tracer_set_tuning", _lib.load().grist_tracer_set_tuning(self.handle, ctypes.byref(t)))
 
     def tracer_tuning(self):
         t = _lib.TracerTuning()
         _lib.check("grist_tracer_get_tuning", _lib.load().grist_tracer_get_tuning(self.handle, ctypes.byref(t)))
         return {"block": t.block, "tracers_per_thread": t.tracers_per_thread, "persistent": bool(t.persistent),
-                "use_graph": bool(t.use_graph), "fused": bool(t.fused), "levels_per_thread": t.levels_per_thread}
+                "use_graph": bool(t.use_graph), "fused": bool(t.fused), "levels_per_thread": t.levels_per_thread,
+                "cell_edges": bool(t.cell_edges)}
 
     def autotune_tracer(self, members, dt, prec="mix", limiter=True, beta=1.0, steps=3, stream=None,
                         cache_path=None, cache_key=None):

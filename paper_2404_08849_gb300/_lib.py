@@ -47,7 +47,7 @@ class TracerBatch(ctypes.Structure):
 
 class TracerTuning(ctypes.Structure):
     _fields_ = [("block", _I), ("tracers_per_thread", _I), ("persistent", _I), ("use_graph", _I), ("fused", _I),
-                ("levels_per_thread", _I)]
+                ("levels_per_thread", _I), ("cell_edges", _I)]
 
 
 class DycoreParams(ctypes.Structure):
@@ -67,6 +67,7 @@ EXPORTS = {
     "grist_mesh_destroy": ([_V], ctypes.c_int),
     "grist_mesh_permutation": ([_V, _P(_I), _P(_I), _P(_I)], ctypes.c_int),
     "grist_mesh_counts": ([_V, _P(_I), _P(_I), _P(_I)], ctypes.c_int),
+    "grist_mesh_features": ([_V, _P(ctypes.c_uint32)], ctypes.c_int),
     "grist_tracer_step": ([_V, _P(TracerBatch), _D, _V], ctypes.c_int),
     "grist_dycore_step_hydro": ([_V, _P(DycoreState), _P(DycoreParams), ctypes.c_int, _D, _V], ctypes.c_int),
     "grist_dycore_step_nh": ([_V, _P(DycoreState), _P(DycoreParams), ctypes.c_int, _D, _V], ctypes.c_int),

@@ -62,6 +62,10 @@ struct DevMesh {
     const double *d2w;    // [nE][2][8]
     const float *d2w_f;
     int d2w_ok;
+    // 1 when every edge side's combined stencil is its cell's ring {i,
+    // coc[i][0..5]} in that order (so the upwind cell can form the edge
+    // value from its ring) and cdiv[i][j] > 0 exactly when i is c1
+    int ring_ok;
     const int32_t *eoe;   // [nE][10] pad: e itself
     const double *wpv;    // [nE][10]
     const float *wpv_f;
@@ -177,6 +181,17 @@ __device__ __forceinline__ void load_d2w(const DevMesh &m, int e, int s, int (&c
     const float4 u = __ldg((const float4 *)(m.d2w_f + r)), v = __ldg((const float4 *)(m.d2w_f + r) + 1);
     c[0] = a.x; c[1] = a.y; c[2] = a.z; c[3] = a.w; c[4] = b.x; c[5] = b.y; c[6] = b.z;
     w[0] = u.x; w[1] = u.y; w[2] = u.z; w[3] = u.w; w[4] = v.x; w[5] = v.y; w[6] = v.z;
+}
+// The weights alone of the combined stencil row of edge e, side s.
+__device__ __forceinline__ void load_d2w_weights(const DevMesh &m, int e, int s, float (&w)[GRIST_D2P]) {
+    const size_t r = ((size_t)e * 2 + s) * 8;
+    const float4 u = __ldg((const float4 *)(m.d2w_f + r)), v = __ldg((const float4 *)(m.d2w_f + r) + 1);
+    w[0] = u.x; w[1] = u.y; w[2] = u.z; w[3] = u.w; w[4] = v.x; w[5] = v.y; w[6] = v.z;
+}
+__device__ __forceinline__ void load_d2w_weights(const DevMesh &m, int e, int s, double (&w)[GRIST_D2P]) {
+    const double2 *p = (const double2 *)(m.d2w + ((size_t)e * 2 + s) * 8);
+    const double2 u0 = __ldg(p), u1 = __ldg(p + 1), u2 = __ldg(p + 2), u3 = __ldg(p + 3);
+    w[0] = u0.x; w[1] = u0.y; w[2] = u1.x; w[3] = u1.y; w[4] = u2.x; w[5] = u2.y; w[6] = u3.x;
 }
 __device__ __forceinline__ void load_d2w(const DevMesh &m, int e, int s, int (&c)[GRIST_D2P],
                                          double (&w)[GRIST_D2P]) {

@@ -393,6 +393,25 @@ extern "C" int grist_mesh_create(const grist_mesh_desc *desc, int device, grist_
         }
     }
 
+    // Every edge side's stencil is its cell's ring {cell, neighbours in the
+    // order of the cell's neighbour list}, and the cell is c1 of its edge
+    // exactly when its divergence coefficient is positive: then the edge
+    // flux can be formed cell-centrically by the upwind cell.
+    int ring_ok = d2w_ok;
+    for (int i = 0; i < nC && ring_ok; i++) {
+        for (int j = 0; j < 6 && ring_ok; j++) {
+            const size_t x = (size_t)i * 6 + j;
+            if (cdiv[x] == 0.0) continue;   // padding of a pentagon
+            const int e = eoc[x];
+            const int s = coe[e].x == i ? 0 : (coe[e].y == i ? 1 : -1);
+            if (s < 0 || (cdiv[x] > 0.0) != (s == 0)) { ring_ok = 0; break; }
+            const int32_t *row = d2wi.data() + ((size_t)e * 2 + s) * 8;
+            if (row[0] != i) ring_ok = 0;
+            for (int q = 0; q < 6; q++)
+                if (row[1 + q] != coc[(size_t)i * 6 + q]) ring_ok = 0;
+        }
+    }
+
     // ---- upload into one arena -------------------------------------------
     Arena ar;
     size_t o_eoc = ar.add(eoc.size() * 4), o_coc = ar.add(coc.size() * 4), o_cdiv = ar.add(cdiv.size() * 8),
@@ -452,6 +471,7 @@ extern "C" int grist_mesh_create(const grist_mesh_desc *desc, int device, grist_
     D.d2i = place<int32_t>(dev, o_d2i); D.d2c = place<double>(dev, o_d2c); D.d2c_f = place<float>(dev, o_d2cf);
     D.d2w = place<double>(dev, o_d2w); D.d2w_f = place<float>(dev, o_d2wf); D.d2wi = place<int32_t>(dev, o_d2wi);
     D.d2w_ok = d2w_ok;
+    D.ring_ok = ring_ok;
     D.eoe = place<int32_t>(dev, o_eoe); D.wpv = place<double>(dev, o_wpv); D.wpv_f = place<float>(dev, o_wpvf);
     D.eov = place<int32_t>(dev, o_eov); D.cov = place<int32_t>(dev, o_cov);
     D.ccurl = place<double>(dev, o_ccurl); D.ccurl_f = place<float>(dev, o_ccurlf);
@@ -523,6 +543,12 @@ extern "C" int grist_mesh_counts(grist_mesh m, int32_t *nC, int32_t *nE, int32_t
     if (nC) *nC = m->nC;
     if (nE) *nE = m->nE;
     if (nV) *nV = m->nV;
+    return GRIST_OK;
+}
+
+extern "C" int grist_mesh_features(grist_mesh m, uint32_t *flags) {
+    if (!m || !flags) return GRIST_EINVAL;
+    *flags = (m->d.d2w_ok ? GRIST_MESH_COMBINED_STENCIL : 0u) | (m->d.ring_ok ? GRIST_MESH_RING_STENCIL : 0u);
     return GRIST_OK;
 }
 

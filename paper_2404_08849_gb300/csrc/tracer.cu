@@ -74,7 +74,7 @@ struct TileMesh {
 };
 
 struct TracerCtx {
-    grist_tracer_tuning tune{128, 4, 0, 0, 0, 2};
+    grist_tracer_tuning tune{128, 4, 0, 0, 0, 2, 1};
     // tile tables (built on first use)
     char *dtile = nullptr;
     TileMesh tiles{};
@@ -142,6 +142,7 @@ struct Batch {
     double dt3;     // dt / 3, the first RK stage (formed on the host)
     int fct;
     int beta1;
+    int ring;       // the edge phases run cell-centrically (item_edge_ring) over the space C
     double beta;
     double cmax;    // vertical transport: largest explicit Courant number
 };
@@ -350,6 +351,50 @@ __device__ __forceinline__ void item_edge_levels(const DevMesh &m, const MemberD
     }
 }
 
+// Cell-centric form of the edge flux (beta = 1, combined weights, every
+// stencil the upwind cell's ring {i, neighbours} in the order of the cell's
+// neighbour list): the thread of cell i gathers q over its ring once per
+// tracer and forms the flux of each edge whose flux leaves the cell, so each
+// edge-level is written once, by its upwind cell, with the weights and the
+// summation order of the edge-centric form (bit-identical), from 7 gathers
+// per cell-level instead of 7 per edge-level.
+template <bool PERS, typename TQ, typename TC, int LPT>
+__device__ __forceinline__ void item_edge_ring(const DevMesh &m, const MemberDev &mb, const CellRow<TC> &r,
+                                               const TQ *q, int t0, int t1, int i, int kg) {
+    const int ld = mb.ld;
+    TC *FH = (TC *)mb.FH;
+#pragma unroll
+    for (int u = 0; u < LPT; u++) {
+        const int k = kg + u * mb.Lg;
+        if (LPT > 1 && k >= mb.L) break;
+        TC f[GRIST_MAXE];
+        unsigned out = 0;
+#pragma unroll
+        for (int j = 0; j < GRIST_MAXE; j++) {
+            f[j] = flux_at<PERS, TC>(mb, (size_t)r.e[j] * ld + k);
+            if (r.cw[j] != (TC)0 && ((f[j] >= (TC)0) == (r.cw[j] > (TC)0))) out |= 1u << j;
+        }
+        for (int t = t0; t < t1; t++) {
+            const TQ *qt = q + (size_t)t * mb.qs;
+            TC qr[GRIST_D2P];
+            qr[0] = static_cast<TC>(lds<PERS>(qt + (size_t)i * ld + k));
+#pragma unroll
+            for (int j = 0; j < GRIST_MAXE; j++) qr[1 + j] = static_cast<TC>(lds<PERS>(qt + (size_t)r.nb[j] * ld + k));
+            TC *ft = FH + (size_t)t * mb.fs;
+#pragma unroll
+            for (int j = 0; j < GRIST_MAXE; j++) {
+                if (!(out & (1u << j))) continue;
+                TC w[GRIST_D2P];
+                load_d2w_weights(m, r.e[j], r.cw[j] > (TC)0 ? 0 : 1, w);
+                TC v = 0;
+#pragma unroll
+                for (int p = 0; p < GRIST_D2P; p++) v += w[p] * qr[p];
+                ft[(size_t)r.e[j] * ld + k] = f[j] * v;
+            }
+        }
+    }
+}
+
 // RK stage update: q^(s) = (dpi^n q^n - dt_s div F^H) / dpi^(s),
 // written as r1 q^n - r2 div with r1 = dpi^n/dpi^(s), r2 = dt_s/dpi^(s)
 // taken once per (cell, level) in FP64 and rounded to the tracer type
@@ -521,9 +566,13 @@ enum Phase { P_DIV = 0, P_EDGE0, P_UPD0, P_EDGE1, P_UPD1, P_EDGE2, P_UPD2, P_LOW
 // member and tracer group; the thread takes the LPT levels g, g + Lg, ...
 // (Lg = ceil(L / LPT)), so consecutive threads still touch consecutive
 // levels, and the entity's tables are read once for its LPT levels.
-template <bool PERS, typename TQ, typename TC, int PH, int LPT = 1>
+// RING: the form of an edge phase, -1 = as B.ring says (the persistent
+// launch), 0 / 1 = compiled for one form (the per-phase kernels, so that a
+// kernel's registers serve the form it runs).
+template <bool PERS, typename TQ, typename TC, int PH, int LPT = 1, int RING = -1>
 __device__ void run_phase(const DevMesh &m, const Batch &B, uint32_t *status) {
-    const Space &S = (PH == P_DIV) ? B.D : (PH == P_EDGE0 || PH == P_EDGE1 || PH == P_EDGE2) ? B.E : B.C;
+    const bool ring = RING < 0 ? (B.ring != 0) : (RING == 1);
+    const Space &S = (PH == P_DIV) ? B.D : ((PH == P_EDGE0 || PH == P_EDGE1 || PH == P_EDGE2) && !ring) ? B.E : B.C;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     int seg = -1;
     bool bad = false;
@@ -538,10 +587,17 @@ __device__ void run_phase(const DevMesh &m, const Batch &B, uint32_t *status) {
         split_index((uint32_t)(n - S.start[seg]), mb.DL, ent, kg);
         const int t0 = mg.y * B.tpt;
         const int t1 = min(mb.T, t0 + B.tpt);
-        if (PH == P_EDGE0) item_edge_levels<PERS, TQ, TC, LPT>(m, mb, (const TQ *)mb.q, t0, t1, ent, kg, B.beta1, beta);
-        if (PH == P_EDGE1) item_edge_levels<PERS, TQ, TC, LPT>(m, mb, (const TQ *)mb.qA, t0, t1, ent, kg, B.beta1, beta);
-        if (PH == P_EDGE2) item_edge_levels<PERS, TQ, TC, LPT>(m, mb, (const TQ *)mb.qB, t0, t1, ent, kg, B.beta1, beta);
-        if (PH == P_EDGE0 || PH == P_EDGE1 || PH == P_EDGE2) continue;
+        if constexpr (PH == P_EDGE0 || PH == P_EDGE1 || PH == P_EDGE2) {
+            const TQ *qs = (const TQ *)(PH == P_EDGE0 ? mb.q : (PH == P_EDGE1 ? mb.qA : mb.qB));
+            if (ring) {
+                CellRow<TC> r;
+                load_cell_row<true>(m, ent, r);
+                item_edge_ring<PERS, TQ, TC, LPT>(m, mb, r, qs, t0, t1, ent, kg);
+            } else {
+                item_edge_levels<PERS, TQ, TC, LPT>(m, mb, qs, t0, t1, ent, kg, B.beta1, beta);
+            }
+            continue;
+        }
         // the cell's row, once for its LPT levels (FP64 weights for the
         // continuity phase); the limited-flux phase, the one with the most
         // live values per level, reads it again for each level instead
@@ -578,6 +634,9 @@ __device__ void run_phase(const DevMesh &m, const Batch &B, uint32_t *status) {
 #ifndef GRIST_TR_REGS_EDGE
 #define GRIST_TR_REGS_EDGE 56
 #endif
+#ifndef GRIST_TR_REGS_RING
+#define GRIST_TR_REGS_RING 72
+#endif
 #ifndef GRIST_TR_REGS_UPD
 #define GRIST_TR_REGS_UPD 64
 #endif
@@ -592,9 +651,10 @@ __device__ void run_phase(const DevMesh &m, const Batch &B, uint32_t *status) {
 #endif
 constexpr int kTracerRegLimit = 65536 / kTracerMaxBlock;
 constexpr int cap_or_none(int r) { return r > 0 && r < kTracerRegLimit ? r : kTracerRegLimit; }
-template <typename TC, int PH> constexpr int tracer_phase_regs() {
+template <typename TC, int PH, int RING> constexpr int tracer_phase_regs() {
     return sizeof(TC) != 4                                      ? kTracerRegLimit
-           : (PH == P_EDGE0 || PH == P_EDGE1 || PH == P_EDGE2) ? cap_or_none(GRIST_TR_REGS_EDGE)
+           : (PH == P_EDGE0 || PH == P_EDGE1 || PH == P_EDGE2) ? cap_or_none(RING == 1 ? GRIST_TR_REGS_RING
+                                                                                    : GRIST_TR_REGS_EDGE)
            : (PH == P_UPD0 || PH == P_UPD1 || PH == P_UPD2)    ? cap_or_none(GRIST_TR_REGS_UPD)
            : PH == P_LOWRES                                    ? cap_or_none(GRIST_TR_REGS_LOWRES)
            : PH == P_RATIOS                                    ? cap_or_none(GRIST_TR_REGS_RATIOS)
@@ -602,9 +662,9 @@ template <typename TC, int PH> constexpr int tracer_phase_regs() {
                                                                : kTracerRegLimit;
 }
 
-template <typename TQ, typename TC, int PH, int LPT>
-__global__ void __maxnreg__((tracer_phase_regs<TC, PH>())) k_tracer_phase(DevMesh m, Batch B, uint32_t *status) {
-    run_phase<false, TQ, TC, PH, LPT>(m, B, status);
+template <typename TQ, typename TC, int PH, int LPT, int RING>
+__global__ void __maxnreg__((tracer_phase_regs<TC, PH, RING>())) k_tracer_phase(DevMesh m, Batch B, uint32_t *status) {
+    run_phase<false, TQ, TC, PH, LPT, RING>(m, B, status);
 }
 
 // Fused RK stage (no limiter) on one tile x 32 levels x the tracers of one
@@ -1088,6 +1148,7 @@ int upload_plan(grist_mesh_s *h, TracerCtx *c, HostPlan &P, const grist_tracer_b
     B.dt3 = dt / 3.0;
     B.fct = b->limiter ? 1 : 0;
     B.beta1 = b->beta_upwind == 1.0 ? 1 : 0;
+    B.ring = (c->tune.cell_edges && B.beta1 && dev_mesh(h).ring_ok) ? 1 : 0;
     B.beta = b->beta_upwind;
     B.cmax = b->vertical_courant_max;
     return GRIST_OK;
@@ -1166,16 +1227,26 @@ int enqueue_horizontal(grist_mesh_s *h, TracerCtx *c, const Batch &B, cudaStream
             if (rc != GRIST_OK) return rc;
             continue;
         }
-        const Space &S = (ph == P_DIV) ? B.D : (ph == P_EDGE0 || ph == P_EDGE1 || ph == P_EDGE2) ? B.E : B.C;
+        const Space &S = (ph == P_DIV) ? B.D : ((ph == P_EDGE0 || ph == P_EDGE1 || ph == P_EDGE2) && !B.ring) ? B.E : B.C;
         long long want = (long long)((S.total + block - 1) / block);
         const long long cap = (long long)sms * 2048 * 32 / block;  // enough blocks to fill every SM many times
         const unsigned grid = (unsigned)(want < 1 ? 1 : (want > cap ? cap : want));
         const char *nm = sizeof(TC) == 4 ? names_f[ph] : names_d[ph];
         switch (ph) {
+#define GRIST_PHASE_LAUNCH(P_, R_) \
+        if (B.lpt == 2) GRIST_LAUNCH(h, nm, st, (k_tracer_phase<TQ, TC, P_, 2, R_><<<grid, block, 0, st>>>(m, B, status))); \
+        else GRIST_LAUNCH(h, nm, st, (k_tracer_phase<TQ, TC, P_, 1, R_><<<grid, block, 0, st>>>(m, B, status)));
 #define GRIST_PHASE_CASE(P_) \
     case P_:                                                                                                   \
-        if (B.lpt == 2) GRIST_LAUNCH(h, nm, st, (k_tracer_phase<TQ, TC, P_, 2><<<grid, block, 0, st>>>(m, B, status))); \
-        else GRIST_LAUNCH(h, nm, st, (k_tracer_phase<TQ, TC, P_, 1><<<grid, block, 0, st>>>(m, B, status)));   \
+        if constexpr (P_ == P_EDGE0 || P_ == P_EDGE1 || P_ == P_EDGE2) {                                       \
+            if (B.ring) {                                                                                      \
+                GRIST_PHASE_LAUNCH(P_, 1)                                                                      \
+            } else {                                                                                           \
+                GRIST_PHASE_LAUNCH(P_, 0)                                                                      \
+            }                                                                                                  \
+        } else {                                                                                               \
+            GRIST_PHASE_LAUNCH(P_, 0)                                                                          \
+        }                                                                                                      \
         break;
             GRIST_PHASE_CASE(P_DIV)
             GRIST_PHASE_CASE(P_EDGE0)
@@ -1189,6 +1260,7 @@ int enqueue_horizontal(grist_mesh_s *h, TracerCtx *c, const Batch &B, cudaStream
             GRIST_PHASE_CASE(P_FINAL)
             GRIST_PHASE_CASE(P_COPY)
 #undef GRIST_PHASE_CASE
+#undef GRIST_PHASE_LAUNCH
         }
     }
     return cudaGetLastError() == cudaSuccess ? GRIST_OK : GRIST_ECUDA;
@@ -1325,7 +1397,7 @@ int tracer_step_t(grist_mesh_s *h, const grist_tracer_batch *b, double dt, cudaS
     sig.push_back((unsigned long long)(uintptr_t)st);
     sig.push_back(((unsigned long long)c->tune.block << 32) | (unsigned)c->tune.tracers_per_thread);
     sig.push_back((unsigned long long)c->tune.persistent | ((unsigned long long)c->tune.levels_per_thread << 8) |
-                  ((unsigned long long)c->tune.fused << 16));
+                  ((unsigned long long)c->tune.fused << 16) | ((unsigned long long)c->tune.cell_edges << 24));
     for (int i = 0; i < b->n_members; i++) {
         const grist_tracer_member &mm = b->members[i];
         sig.push_back((unsigned long long)(uintptr_t)mm.q);
@@ -1408,6 +1480,7 @@ int check_tuning(const grist_tracer_tuning *t) {
     if (t->use_graph != 0 && t->use_graph != 1) return GRIST_EINVAL;
     if (t->fused != 0 && t->fused != 1) return GRIST_EINVAL;
     if (t->levels_per_thread != 1 && t->levels_per_thread != 2) return GRIST_EINVAL;
+    if (t->cell_edges != 0 && t->cell_edges != 1) return GRIST_EINVAL;
     return GRIST_OK;
 }
 
@@ -1512,7 +1585,7 @@ extern "C" int grist_tracer_autotune(grist_mesh h, const grist_tracer_batch *b, 
         for (int bl : blocks) {
             for (int tp : tpts) {
                 if (tp > 1 && tp / 2 >= maxT) continue;
-                grist_tracer_tuning t{bl, tp, 0, 0, fu, 1};
+                grist_tracer_tuning t{bl, tp, 0, 0, fu, 1, 1};
                 double ms = 0;
                 if (time_cfg(t, &ms) == GRIST_OK && ms < bestms) { bestms = ms; bestt = t; }
             }
@@ -1523,10 +1596,17 @@ extern "C" int grist_tracer_autotune(grist_mesh h, const grist_tracer_batch *b, 
     {
         const int tp = bestt.tracers_per_thread, fu = bestt.fused;
         for (int bl : blocks) {
-            grist_tracer_tuning t{bl, tp, 0, 0, fu, 2};
+            grist_tracer_tuning t{bl, tp, 0, 0, fu, 2, 1};
             double ms = 0;
             if (time_cfg(t, &ms) == GRIST_OK && ms < bestms) { bestms = ms; bestt = t; }
         }
+    }
+    // the edge-centric form of the edge fluxes at the best so far
+    {
+        grist_tracer_tuning t = bestt;
+        t.cell_edges = 0;
+        double ms = 0;
+        if (time_cfg(t, &ms) == GRIST_OK && ms < bestms) { bestms = ms; bestt = t; }
     }
     for (int pers = 0; pers <= 1; pers++) {
         for (int gr = 0; gr <= 1; gr++) {

@@ -61,7 +61,9 @@ TUNINGS = [None,
            {"block": 256, "tracers_per_thread": 2, "use_graph": True},
            {"block": 256, "tracers_per_thread": 4, "persistent": True, "use_graph": True},
            {"block": 256, "tracers_per_thread": 4, "levels_per_thread": 2},
-           {"block": 512, "tracers_per_thread": 1, "levels_per_thread": 2, "use_graph": True}]
+           {"block": 512, "tracers_per_thread": 1, "levels_per_thread": 2, "use_graph": True},
+           {"block": 128, "tracers_per_thread": 4, "levels_per_thread": 2, "cell_edges": False},
+           {"block": 256, "tracers_per_thread": 2, "persistent": True, "cell_edges": False}]
 
 
 @pytest.mark.parametrize("tuning", TUNINGS)
