@@ -78,10 +78,12 @@ def algorithmic_bytes(name, nC, nE, nV, L, T, prec):
         "k_tr_div": EL * 8 + CL * 8 + 2 * CL * sC + (EL * 4 if sC == 4 else 0),
         "k_tr_edge": T * CL * sQ + EL * sC + T * EL * sC,
         "k_tr_update": T * EL * sC + T * CL * sQ + 2 * CL * sC + T * CL * sQ,
-        "k_tr_lowres": T * CL * sQ + EL * sC + 2 * CL * sC + T * CL * sQ,
-        "k_tr_ratios": 2 * T * CL * sQ + T * EL * sC + EL * sC + 2 * CL * sC + 2 * T * CL * sC,
-        "k_tr_final": T * CL * sQ + T * EL * sC + EL * sC + 2 * CL * sC + 2 * T * CL * sC + T * CL * sQ,
-        "k_tr_copy": 2 * T * CL * sQ,
+        # limiter: q^n, F, {dpi, div F} -> local bounds {max, min}(q^n, q^td), div F^L
+        "k_tr_lowres": T * CL * sQ + EL * sC + 2 * CL * sC + 2 * T * CL * sC + T * CL * sC,
+        # q^n, bounds, A, {dpi, div F} -> {R+, R-}
+        "k_tr_ratios": T * CL * sQ + 2 * T * CL * sC + T * EL * sC + 2 * CL * sC + 2 * T * CL * sC,
+        # q^n, div F^L, A, {R+, R-}, {dpi, div F} -> q^{n+1} in place
+        "k_tr_final": T * CL * sQ + T * CL * sC + T * EL * sC + 2 * T * CL * sC + 2 * CL * sC + T * CL * sQ,
         "k_tr_vertical": 2 * CL * sC + CI * 8 + 2 * T * CL * sQ,
     }
     return table.get(base)

@@ -35,7 +35,9 @@ struct MemberDev {
     const double *F;        // [nE][ld]
     void *qA, *qB;          // scratch stage tracers [T][nC][ld]
     void *FH;               // scratch edge fluxes [T][nE][ld]
-    void *Rp, *Rm;          // scratch FCT ratios [T][nC][ld]
+    void *R2;               // scratch FCT ratios {R+, R-} [T][nC][ld] pairs in the compute type
+    void *X2;               // scratch FCT local bounds {max, min}(q^n, q^td) [T][nC][ld] pairs
+    void *DFL;              // scratch FCT div F^L [T][nC][ld] in the compute type
     const void *Ff;         // mass flux in the compute type [nE][ld]: a binary32 copy (scratch) or F itself
     void *DV;               // scratch {dpi, div F} pairs in the compute type [nC][ld]
     int L, T, ld, pad;
@@ -249,13 +251,30 @@ __device__ __forceinline__ TC flux_at(const MemberDev &mb, size_t x) {
     return (TC)ldg(mb.F + x);
 }
 
+// Products and sums of the limiter written with explicit rounding, so the
+// edge-centric and cell-centric forms (different kernels) give the same
+// bits: F^L = F q^n_upwind, A = F^H - F^L with F^H = F q_e, div F^L summed
+// by fused multiply-adds in edge order, q^td = r1 q^n - r2 div F^L.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+template <typename TC> __device__ __forceinline__ TC antidiff(TC f, TC qe, TC qup) {
+    return mul_rn(f, qe) - mul_rn(f, qup);
+}
+template <typename TC> __device__ __forceinline__ TC lowres_value(TC r1, TC r2, TC qn, TC divl) {
+    return fma_rn(r1, qn, -mul_rn(r2, divl));
+}
+
 // Third-order upwind edge flux (Skamarock-Gassmann form):
 //   q_e = (q1 + q2)/2 - (dc^2/12)(q''1 + q''2) + sgn(F) beta (dc^2/12)(q''2 - q''1)
 // F^H = F q_e.  With beta = 1 only the upwind side's second derivative
 // survives: q_e = (q1 + q2)/2 - 2 (dc^2/12) q''_upwind.
+// In the final stage of a limited step (qn = q^n) the phase stores the
+// antidiffusive flux A = F^H - F^L instead of F^H.
 template <bool PERS, typename TQ, typename TC>
-__device__ __forceinline__ void item_edge(const DevMesh &m, const MemberDev &mb, const TQ *q, int t0, int t1,
-                                          int e, int k, bool beta1, TC beta) {
+__device__ __forceinline__ void item_edge(const DevMesh &m, const MemberDev &mb, const TQ *q, const TQ *qn, int t0,
+                                          int t1, int e, int k, bool beta1, TC beta) {
     const int ld = mb.ld;
     const int2 c = ldg(m.coe + e);
     const TC f = flux_at<PERS, TC>(mb, (size_t)e * ld + k);
@@ -275,7 +294,8 @@ __device__ __forceinline__ void item_edge(const DevMesh &m, const MemberDev &mb,
             TC v = 0;
 #pragma unroll
             for (int j = 0; j < GRIST_D2P; j++) v += w[j] * static_cast<TC>(lds<PERS>(qt + (size_t)idx[j] * ld + k));
-            FH[(size_t)t * mb.fs + (size_t)e * ld + k] = f * v;
+            FH[(size_t)t * mb.fs + (size_t)e * ld + k] =
+                qn ? antidiff(f, v, static_cast<TC>(qn[(size_t)t * mb.qs + (size_t)idx[0] * ld + k])) : f * v;
         }
     } else if (beta1) {
         const int side = f >= (TC)0 ? 0 : 1;
@@ -292,7 +312,10 @@ __device__ __forceinline__ void item_edge(const DevMesh &m, const MemberDev &mb,
 #pragma unroll
             for (int j = 0; j < GRIST_D2P; j++) d += w[j] * static_cast<TC>(lds<PERS>(qt + (size_t)idx[j] * ld + k));
             const TC q1 = static_cast<TC>(lds<PERS>(qt + (size_t)c.x * ld + k)), q2 = static_cast<TC>(lds<PERS>(qt + (size_t)c.y * ld + k));
-            FH[(size_t)t * mb.fs + (size_t)e * ld + k] = f * ((TC)0.5 * (q1 + q2) - (TC)2 * dc2 * d);
+            const TC qe = (TC)0.5 * (q1 + q2) - (TC)2 * dc2 * d;
+            FH[(size_t)t * mb.fs + (size_t)e * ld + k] =
+                qn ? antidiff(f, qe, static_cast<TC>(qn[(size_t)t * mb.qs + (size_t)(f >= (TC)0 ? c.x : c.y) * ld + k]))
+                   : f * qe;
         }
     } else {
         const TC sgn = f >= (TC)0 ? (TC)1 : (TC)-1;
@@ -306,7 +329,9 @@ __device__ __forceinline__ void item_edge(const DevMesh &m, const MemberDev &mb,
             }
             const TC q1 = static_cast<TC>(lds<PERS>(qt + (size_t)c.x * ld + k)), q2 = static_cast<TC>(lds<PERS>(qt + (size_t)c.y * ld + k));
             const TC qe = (TC)0.5 * (q1 + q2) - dc2 * (d1 + d2) + sgn * beta * dc2 * (d2 - d1);
-            FH[(size_t)t * mb.fs + (size_t)e * ld + k] = f * qe;
+            FH[(size_t)t * mb.fs + (size_t)e * ld + k] =
+                qn ? antidiff(f, qe, static_cast<TC>(qn[(size_t)t * mb.qs + (size_t)(f >= (TC)0 ? c.x : c.y) * ld + k]))
+                   : f * qe;
         }
     }
 }
@@ -315,14 +340,14 @@ __device__ __forceinline__ void item_edge(const DevMesh &m, const MemberDev &mb,
 // combined weights, the upwind side's stencil (4 vector loads) is read once
 // and read again only for a level whose flux runs the other way.
 template <bool PERS, typename TQ, typename TC, int LPT>
-__device__ __forceinline__ void item_edge_levels(const DevMesh &m, const MemberDev &mb, const TQ *q, int t0, int t1,
-                                                 int e, int kg, bool beta1, TC beta) {
+__device__ __forceinline__ void item_edge_levels(const DevMesh &m, const MemberDev &mb, const TQ *q, const TQ *qn,
+                                                 int t0, int t1, int e, int kg, bool beta1, TC beta) {
     if (!(beta1 && m.d2w_ok)) {
 #pragma unroll
         for (int u = 0; u < LPT; u++) {
             const int k = kg + u * mb.Lg;
             if (LPT > 1 && k >= mb.L) break;
-            item_edge<PERS, TQ, TC>(m, mb, q, t0, t1, e, k, beta1, beta);
+            item_edge<PERS, TQ, TC>(m, mb, q, qn, t0, t1, e, k, beta1, beta);
         }
         return;
     }
@@ -346,7 +371,8 @@ __device__ __forceinline__ void item_edge_levels(const DevMesh &m, const MemberD
             TC v = 0;
 #pragma unroll
             for (int j = 0; j < GRIST_D2P; j++) v += w[j] * static_cast<TC>(lds<PERS>(qt + (size_t)idx[j] * ld + k));
-            FH[(size_t)t * mb.fs + (size_t)e * ld + k] = f * v;
+            FH[(size_t)t * mb.fs + (size_t)e * ld + k] =
+                qn ? antidiff(f, v, static_cast<TC>(qn[(size_t)t * mb.qs + (size_t)idx[0] * ld + k])) : f * v;
         }
     }
 }
@@ -360,7 +386,7 @@ __device__ __forceinline__ void item_edge_levels(const DevMesh &m, const MemberD
 // per cell-level instead of 7 per edge-level.
 template <bool PERS, typename TQ, typename TC, int LPT>
 __device__ __forceinline__ void item_edge_ring(const DevMesh &m, const MemberDev &mb, const CellRow<TC> &r,
-                                               const TQ *q, int t0, int t1, int i, int kg) {
+                                               const TQ *q, const TQ *qn, int t0, int t1, int i, int kg) {
     const int ld = mb.ld;
     TC *FH = (TC *)mb.FH;
 #pragma unroll
@@ -381,6 +407,8 @@ __device__ __forceinline__ void item_edge_ring(const DevMesh &m, const MemberDev
 #pragma unroll
             for (int j = 0; j < GRIST_MAXE; j++) qr[1 + j] = static_cast<TC>(lds<PERS>(qt + (size_t)r.nb[j] * ld + k));
             TC *ft = FH + (size_t)t * mb.fs;
+            // the upwind cell's q^n of a limited final stage: this cell's
+            const TC qup = qn ? static_cast<TC>(qn[(size_t)t * mb.qs + (size_t)i * ld + k]) : (TC)0;
 #pragma unroll
             for (int j = 0; j < GRIST_MAXE; j++) {
                 if (!(out & (1u << j))) continue;
@@ -389,7 +417,7 @@ __device__ __forceinline__ void item_edge_ring(const DevMesh &m, const MemberDev
                 TC v = 0;
 #pragma unroll
                 for (int p = 0; p < GRIST_D2P; p++) v += w[p] * qr[p];
-                ft[(size_t)r.e[j] * ld + k] = f[j] * v;
+                ft[(size_t)r.e[j] * ld + k] = qn ? antidiff(f[j], v, qup) : f[j] * v;
             }
         }
     }
@@ -423,144 +451,125 @@ __device__ __forceinline__ bool item_update(const CellRow<TC> &r, const MemberDe
     return bad;
 }
 
-// Low-order (first-order upwind) flux of edge j of cell i from q^n.  The
-// upwind cell is c1 when F >= 0, c2 otherwise; cell i is c1 of its edge
-// exactly when its divergence coefficient is positive.
-template <bool PERS, typename TQ, typename TC>
-__device__ __forceinline__ TC upwind_flux(TC f, TC cw, int i, int nb, const TQ *qt, int ld, int k) {
-    const bool i_is_c1 = cw > (TC)0;
-    const int up = ((f >= (TC)0) == i_is_c1) ? i : nb;
-    return f * static_cast<TC>(lds<PERS>(qt + (size_t)up * ld + k));
-}
-
-// FCT 1: low-order solution q^td = (dpi^n q^n - dt div F^L) / dpi^(3).
+// FCT 1: low-order solution q^td = (dpi^n q^n - dt div F^L) / dpi^(3),
+// with F^L the first-order upwind flux of q^n (the upwind cell is c1 when
+// F >= 0, c2 otherwise; cell i is c1 of its edge exactly when its
+// divergence coefficient is positive), stored as the cell's local bounds
+// {max, min}(q^n, q^td) (X2: q^td is the member of the pair that is not
+// q^n, or q^n itself), and div F^L (DFL) for the later phases.
 template <bool PERS, typename TQ, typename TC>
 __device__ __forceinline__ void item_lowres(const CellRow<TC> &r, const MemberDev &mb, int t0, int t1, int i, int k,
                                             double dt, float dtf) {
+    using T2 = typename Vec2<TC>::T;
     const int ld = mb.ld;
     const size_t x = (size_t)i * ld + k;
     TC r1, r2;
     stage_ratios(dv_at<PERS, TC>(mb, x), dt, dtf, r1, r2);
-    const int *nb = r.nb;
-    const TC *cw = r.cw;
     TC fe[GRIST_MAXE];
 #pragma unroll
     for (int j = 0; j < GRIST_MAXE; j++) fe[j] = flux_at<PERS, TC>(mb, (size_t)r.e[j] * ld + k);
     const TQ *qn = (const TQ *)mb.q;
-    TQ *qtd = (TQ *)mb.qA;
+    T2 *X2 = (T2 *)mb.X2;
+    TC *DFL = (TC *)mb.DFL;
     for (int t = t0; t < t1; t++) {
         const TQ *qt = qn + (size_t)t * mb.qs;
-        TC div = 0;
+        TC divl = 0;
 #pragma unroll
-        for (int j = 0; j < GRIST_MAXE; j++) div += cw[j] * upwind_flux<PERS, TQ, TC>(fe[j], cw[j], i, nb[j], qt, ld, k);
-        qtd[(size_t)t * mb.qs + x] = static_cast<TQ>(r1 * static_cast<TC>(qt[x]) - r2 * div);
+        for (int j = 0; j < GRIST_MAXE; j++) {
+            const int up = ((fe[j] >= (TC)0) == (r.cw[j] > (TC)0)) ? i : r.nb[j];
+            divl = fma_rn(r.cw[j], mul_rn(fe[j], static_cast<TC>(lds<PERS>(qt + (size_t)up * ld + k))), divl);
+        }
+        const TC qi = static_cast<TC>(qt[x]);
+        const TC qd = static_cast<TC>(static_cast<TQ>(lowres_value(r1, r2, qi, divl)));
+        X2[(size_t)t * mb.qs + x] = T2{fmax_(qi, qd), fmin_(qi, qd)};
+        DFL[(size_t)t * mb.qs + x] = divl;
     }
 }
 
-// FCT 2: local bounds over the cell and its neighbours of {q^n, q^td};
-// antidiffusive in/out sums P+-, allowed changes Q+-, ratios
-// R+- = min(1, Q / (P + TINY)) (Sec. 2.2 (iii): TINY of the working type).
+// FCT 2: bounds over the cell and its neighbours of {q^n, q^td} (from the
+// cells' local bounds); antidiffusive in/out sums P+- of A = F^H - F^L (as
+// the final edge phase stored it); allowed changes Q+-; ratios
+// R+- = min(1, Q / (P + TINY)) (Sec. 2.2 (iii): TINY of the working type),
+// stored as the pair {R+, R-}.
 template <bool PERS, typename TQ, typename TC>
 __device__ __forceinline__ void item_ratios(const CellRow<TC> &r, const MemberDev &mb, int t0, int t1, int i, int k,
                                             double dt, float dtf) {
+    using T2 = typename Vec2<TC>::T;
     const int ld = mb.ld;
     const size_t x = (size_t)i * ld + k;
     const TC dp3 = static_cast<TC>(end_mass(dv_at<PERS, TC>(mb, x), dt, dtf));
     const TC dtc = sizeof(TC) == 4 ? (TC)dtf : (TC)dt;
-    const int *nb = r.nb, *eidx = r.e;
-    const TC *cw = r.cw;
-    TC fe[GRIST_MAXE];
-#pragma unroll
-    for (int j = 0; j < GRIST_MAXE; j++) fe[j] = flux_at<PERS, TC>(mb, (size_t)eidx[j] * ld + k);
-    const TQ *qn = (const TQ *)mb.q, *qtd = (const TQ *)mb.qA;
-    const TC *FH = (const TC *)mb.FH;
-    TC *Rp = (TC *)mb.Rp, *Rm = (TC *)mb.Rm;
+    const T2 *X2 = (const T2 *)mb.X2;
+    const TQ *qn = (const TQ *)mb.q;
+    const TC *A = (const TC *)mb.FH;
+    T2 *R2 = (T2 *)mb.R2;
     for (int t = t0; t < t1; t++) {
-        const TQ *qt = qn + (size_t)t * mb.qs;
-        const TQ *qd = qtd + (size_t)t * mb.qs;
-        const TC *ft = FH + (size_t)t * mb.fs;
-        const TC qtd_i = static_cast<TC>(lds<PERS>(qd + x));
-        const TC qn_i = static_cast<TC>(qt[x]);
-        TC qmax = fmax_(qn_i, qtd_i), qmin = fmin_(qn_i, qtd_i);
+        const T2 *xt = X2 + (size_t)t * mb.qs;
+        const TC *at = A + (size_t)t * mb.fs;
+        const T2 bi = lds<PERS>(xt + x);
+        TC qmax = bi.x, qmin = bi.y;
         TC pp = 0, pm = 0;
 #pragma unroll
         for (int j = 0; j < GRIST_MAXE; j++) {
-            const size_t y = (size_t)nb[j] * ld + k;
-            const TC a = static_cast<TC>(qt[y]), b = static_cast<TC>(lds<PERS>(qd + y));
-            qmax = fmax_(qmax, fmax_(a, b));
-            qmin = fmin_(qmin, fmin_(a, b));
-            // low-order flux from the upwind cell's q^n (already in registers)
-            const TC fl = fe[j] * (((fe[j] >= (TC)0) == (cw[j] > (TC)0)) ? qn_i : a);
-            const TC ae = lds<PERS>(ft + (size_t)eidx[j] * ld + k) - fl;
-            const TC out = cw[j] * ae;  // outward antidiffusive flux / A_i (sign and dv folded in)
+            const T2 bn = lds<PERS>(xt + (size_t)r.nb[j] * ld + k);
+            qmax = fmax_(qmax, bn.x);
+            qmin = fmin_(qmin, bn.y);
+            const TC out = r.cw[j] * lds<PERS>(at + (size_t)r.e[j] * ld + k);  // outward A / A_i
             pp += fmax_((TC)0, -out);
             pm += fmax_((TC)0, out);
         }
         pp *= dtc;
         pm *= dtc;
+        const TC qn_i = static_cast<TC>(qn[(size_t)t * mb.qs + x]);
+        const TC qtd_i = bi.x == qn_i ? bi.y : bi.x;
         const TC Qp = (qmax - qtd_i) * dp3, Qm = (qtd_i - qmin) * dp3;
-        Rp[(size_t)t * mb.qs + x] = fmin_((TC)1, Qp / (pp + tiny_of<TC>()));
-        Rm[(size_t)t * mb.qs + x] = fmin_((TC)1, Qm / (pm + tiny_of<TC>()));
+        R2[(size_t)t * mb.qs + x] = T2{fmin_((TC)1, Qp / (pp + tiny_of<TC>())), fmin_((TC)1, Qm / (pm + tiny_of<TC>()))};
     }
 }
 
-// FCT 3: limited flux F^L + C A with C = min(R-(c1), R+(c2)) when the
-// antidiffusive flux A runs c1 -> c2 (A >= 0), min(R+(c1), R-(c2)) else;
-// q^{n+1} = (dpi^n q^n - dt div(F^L + C A)) / dpi^(3) into qB.
+// FCT 3: limited flux F^L + C A with C = min(R-(c1), R+(c2)) when A runs
+// c1 -> c2 (A >= 0), min(R+(c1), R-(c2)) else; q^{n+1} = (dpi^n q^n - dt
+// div(F^L + C A)) / dpi^(3), with div F^L from the low-order phase, written
+// over q^n in place (each thread reads only its own cell's q^n).
 template <bool PERS, typename TQ, typename TC>
 __device__ __forceinline__ bool item_final(const CellRow<TC> &r, const MemberDev &mb, int t0, int t1, int i, int k,
                                            double dt, float dtf) {
+    using T2 = typename Vec2<TC>::T;
     const int ld = mb.ld;
     const size_t x = (size_t)i * ld + k;
     TC r1, r2;
     stage_ratios(dv_at<PERS, TC>(mb, x), dt, dtf, r1, r2);
-    const int *nb = r.nb, *eidx = r.e;
-    const TC *cw = r.cw;
-    TC fe[GRIST_MAXE];
-#pragma unroll
-    for (int j = 0; j < GRIST_MAXE; j++) fe[j] = flux_at<PERS, TC>(mb, (size_t)eidx[j] * ld + k);
-    const TQ *qn = (const TQ *)mb.q;
-    const TC *FH = (const TC *)mb.FH;
-    const TC *Rp = (const TC *)mb.Rp, *Rm = (const TC *)mb.Rm;
-    TQ *qout = (TQ *)mb.qB;
+    TQ *q = (TQ *)mb.q;
+    const TC *A = (const TC *)mb.FH, *DFL = (const TC *)mb.DFL;
+    const T2 *R2 = (const T2 *)mb.R2;
     bool bad = false;
     for (int t = t0; t < t1; t++) {
-        const TQ *qt = qn + (size_t)t * mb.qs;
-        const TC *ft = FH + (size_t)t * mb.fs;
-        const TC *rp = Rp + (size_t)t * mb.qs, *rm = Rm + (size_t)t * mb.qs;
-        const TC rp_i = lds<PERS>(rp + x), rm_i = lds<PERS>(rm + x);
-        TC div = 0;
+        const TC *at = A + (size_t)t * mb.fs;
+        const T2 *rt = R2 + (size_t)t * mb.qs;
+        const T2 ri = lds<PERS>(rt + x);
+        TC div = lds<PERS>(DFL + (size_t)t * mb.qs + x);
 #pragma unroll
         for (int j = 0; j < GRIST_MAXE; j++) {
-            const size_t y = (size_t)nb[j] * ld + k;
-            const TC fl = upwind_flux<PERS, TQ, TC>(fe[j], cw[j], i, nb[j], qt, ld, k);
-            const TC ae = lds<PERS>(ft + (size_t)eidx[j] * ld + k) - fl;
-            const bool i_is_c1 = cw[j] > (TC)0;
-            const TC rpy = lds<PERS>(rp + y), rmy = lds<PERS>(rm + y);
-            const TC rp1 = i_is_c1 ? rp_i : rpy, rm1 = i_is_c1 ? rm_i : rmy;
-            const TC rp2 = i_is_c1 ? rpy : rp_i, rm2 = i_is_c1 ? rmy : rm_i;
+            const TC ae = lds<PERS>(at + (size_t)r.e[j] * ld + k);
+            const T2 rn = lds<PERS>(rt + (size_t)r.nb[j] * ld + k);
+            const bool i_is_c1 = r.cw[j] > (TC)0;
+            const TC rp1 = i_is_c1 ? ri.x : rn.x, rm1 = i_is_c1 ? ri.y : rn.y;
+            const TC rp2 = i_is_c1 ? rn.x : ri.x, rm2 = i_is_c1 ? rn.y : ri.y;
             const TC c = ae >= (TC)0 ? fmin_(rm1, rp2) : fmin_(rp1, rm2);
-            div += cw[j] * (fl + c * ae);
+            div += r.cw[j] * (c * ae);
         }
-        const TC v = r1 * static_cast<TC>(qt[x]) - r2 * div;
+        const size_t y = (size_t)t * mb.qs + x;
+        const TC v = r1 * static_cast<TC>(q[y]) - r2 * div;
         bad |= !isfinite(v);
-        qout[(size_t)t * mb.qs + x] = static_cast<TQ>(v);
+        q[y] = static_cast<TQ>(v);
     }
     return bad;
-}
-
-template <bool PERS, typename TQ>
-__device__ __forceinline__ void item_copy(const MemberDev &mb, int t0, int t1, int i, int k) {
-    const size_t x = (size_t)i * mb.ld + k;
-    const TQ *src = (const TQ *)mb.qB;
-    TQ *dst = (TQ *)mb.q;
-    for (int t = t0; t < t1; t++) dst[(size_t)t * mb.qs + x] = lds<PERS>(src + (size_t)t * mb.qs + x);
 }
 
 // ---------------------------------------------------------------------------
 // phases: grid-stride loops over a work space
 
-enum Phase { P_DIV = 0, P_EDGE0, P_UPD0, P_EDGE1, P_UPD1, P_EDGE2, P_UPD2, P_LOWRES, P_RATIOS, P_FINAL, P_COPY };
+enum Phase { P_DIV = 0, P_EDGE0, P_UPD0, P_EDGE1, P_UPD1, P_EDGE2, P_UPD2, P_LOWRES, P_RATIOS, P_FINAL, P_NPHASE };
 
 // One pass over a work space.  A work item is (entity, level group g) of a
 // member and tracer group; the thread takes the LPT levels g, g + Lg, ...
@@ -589,12 +598,14 @@ __device__ void run_phase(const DevMesh &m, const Batch &B, uint32_t *status) {
         const int t1 = min(mb.T, t0 + B.tpt);
         if constexpr (PH == P_EDGE0 || PH == P_EDGE1 || PH == P_EDGE2) {
             const TQ *qs = (const TQ *)(PH == P_EDGE0 ? mb.q : (PH == P_EDGE1 ? mb.qA : mb.qB));
+            // the final stage of a limited step stores A = F^H - F^L
+            const TQ *qn = (PH == P_EDGE2 && B.fct) ? (const TQ *)mb.q : nullptr;
             if (ring) {
                 CellRow<TC> r;
                 load_cell_row<true>(m, ent, r);
-                item_edge_ring<PERS, TQ, TC, LPT>(m, mb, r, qs, t0, t1, ent, kg);
+                item_edge_ring<PERS, TQ, TC, LPT>(m, mb, r, qs, qn, t0, t1, ent, kg);
             } else {
-                item_edge_levels<PERS, TQ, TC, LPT>(m, mb, qs, t0, t1, ent, kg, B.beta1, beta);
+                item_edge_levels<PERS, TQ, TC, LPT>(m, mb, qs, qn, t0, t1, ent, kg, B.beta1, beta);
             }
             continue;
         }
@@ -605,7 +616,7 @@ __device__ void run_phase(const DevMesh &m, const Batch &B, uint32_t *status) {
         constexpr bool kNb = PH == P_LOWRES || PH == P_RATIOS || PH == P_FINAL;
         constexpr bool kRowPerLevel = PH == P_FINAL;
         CellRow<TW> r;
-        if (PH != P_COPY && !kRowPerLevel) load_cell_row<kNb>(m, ent, r);
+        if (!kRowPerLevel) load_cell_row<kNb>(m, ent, r);
 #pragma unroll
         for (int u = 0; u < LPT; u++) {
         const int k = kg + u * mb.Lg;
@@ -618,7 +629,6 @@ __device__ void run_phase(const DevMesh &m, const Batch &B, uint32_t *status) {
         if constexpr (PH == P_LOWRES) item_lowres<PERS, TQ, TC>(r, mb, t0, t1, ent, k, B.dt, dtf);
         if constexpr (PH == P_RATIOS) item_ratios<PERS, TQ, TC>(r, mb, t0, t1, ent, k, B.dt, dtf);
         if constexpr (PH == P_FINAL) bad |= item_final<PERS, TQ, TC>(r, mb, t0, t1, ent, k, B.dt, dtf);
-        if constexpr (PH == P_COPY) item_copy<PERS, TQ>(mb, t0, t1, ent, k);
         }
     }
     if (bad) atomicOr(status, GRIST_FLAG_NONFINITE);
@@ -644,7 +654,7 @@ __device__ void run_phase(const DevMesh &m, const Batch &B, uint32_t *status) {
 #define GRIST_TR_REGS_LOWRES 64
 #endif
 #ifndef GRIST_TR_REGS_RATIOS
-#define GRIST_TR_REGS_RATIOS 96
+#define GRIST_TR_REGS_RATIOS 72
 #endif
 #ifndef GRIST_TR_REGS_FINAL
 #define GRIST_TR_REGS_FINAL 0
@@ -653,8 +663,8 @@ constexpr int kTracerRegLimit = 65536 / kTracerMaxBlock;
 constexpr int cap_or_none(int r) { return r > 0 && r < kTracerRegLimit ? r : kTracerRegLimit; }
 template <typename TC, int PH, int RING> constexpr int tracer_phase_regs() {
     return sizeof(TC) != 4                                      ? kTracerRegLimit
-           : (PH == P_EDGE0 || PH == P_EDGE1 || PH == P_EDGE2) ? cap_or_none(RING == 1 ? GRIST_TR_REGS_RING
-                                                                                    : GRIST_TR_REGS_EDGE)
+           : (PH == P_EDGE0 || PH == P_EDGE1 || PH == P_EDGE2)
+               ? cap_or_none(RING == 1 ? GRIST_TR_REGS_RING : GRIST_TR_REGS_EDGE)
            : (PH == P_UPD0 || PH == P_UPD1 || PH == P_UPD2)    ? cap_or_none(GRIST_TR_REGS_UPD)
            : PH == P_LOWRES                                    ? cap_or_none(GRIST_TR_REGS_LOWRES)
            : PH == P_RATIOS                                    ? cap_or_none(GRIST_TR_REGS_RATIOS)
@@ -996,8 +1006,6 @@ __global__ void k_tracer_persistent(DevMesh m, Batch B, unsigned *bar, uint32_t 
     run_phase<true, TQ, TC, P_RATIOS>(m, B, status);
     if (!grid_sync(bar, status)) return;
     run_phase<true, TQ, TC, P_FINAL>(m, B, status);
-    if (!grid_sync(bar, status)) return;
-    run_phase<true, TQ, TC, P_COPY>(m, B, status);
 }
 
 // ---------------------------------------------------------------------------
@@ -1040,8 +1048,9 @@ int plan_batch(const DevMesh &m, const grist_tracer_batch *b, int tpt, int lpt, 
         d.qA = (void *)(uintptr_t)off; off += al256(bq);
         d.qB = (void *)(uintptr_t)off; off += al256(bq);
         d.FH = (void *)(uintptr_t)off; off += al256(bf);
-        d.Rp = (void *)(uintptr_t)off; off += al256(br);
-        d.Rm = (void *)(uintptr_t)off; off += al256(br);
+        d.R2 = (void *)(uintptr_t)off; off += al256(2 * br);
+        d.X2 = (void *)(uintptr_t)off; off += al256(2 * br);
+        d.DFL = (void *)(uintptr_t)off; off += al256(br);
         if (sizeof(TC) == 4) { d.Ff = (const void *)(uintptr_t)off; off += al256(d.fs * sizeof(float)); }
         d.DV = (void *)(uintptr_t)off; off += al256(d.qs * 2 * sizeof(TC));
         const int idx = (int)P.mem.size();
@@ -1078,8 +1087,9 @@ int upload_plan(grist_mesh_s *h, TracerCtx *c, HostPlan &P, const grist_tracer_b
         d.qA = scr + (uintptr_t)d.qA;
         d.qB = scr + (uintptr_t)d.qB;
         d.FH = scr + (uintptr_t)d.FH;
-        d.Rp = scr + (uintptr_t)d.Rp;
-        d.Rm = scr + (uintptr_t)d.Rm;
+        d.R2 = scr + (uintptr_t)d.R2;
+        d.X2 = scr + (uintptr_t)d.X2;
+        d.DFL = scr + (uintptr_t)d.DFL;
         d.Ff = sizeof(TC) == 4 ? (const void *)(scr + (uintptr_t)d.Ff) : (const void *)d.F;
         d.DV = scr + (uintptr_t)d.DV;
     }
@@ -1185,16 +1195,12 @@ int enqueue_horizontal(grist_mesh_s *h, TracerCtx *c, const Batch &B, cudaStream
                                                                 args, 0, st)));
         return GRIST_OK;
     }
-    static const char *names[] = {"k_tr_div", "k_tr_edge", "k_tr_update", "k_tr_edge", "k_tr_update",
-                                  "k_tr_edge", "k_tr_update", "k_tr_lowres", "k_tr_ratios", "k_tr_final",
-                                  "k_tr_copy"};
     static const char *names_f[] = {"k_tr_div/mix", "k_tr_edge/mix", "k_tr_update/mix", "k_tr_edge/mix",
                                     "k_tr_update/mix", "k_tr_edge/mix", "k_tr_update/mix", "k_tr_lowres/mix",
-                                    "k_tr_ratios/mix", "k_tr_final/mix", "k_tr_copy/mix"};
+                                    "k_tr_ratios/mix", "k_tr_final/mix"};
     static const char *names_d[] = {"k_tr_div/fp64", "k_tr_edge/fp64", "k_tr_update/fp64", "k_tr_edge/fp64",
                                     "k_tr_update/fp64", "k_tr_edge/fp64", "k_tr_update/fp64", "k_tr_lowres/fp64",
-                                    "k_tr_ratios/fp64", "k_tr_final/fp64", "k_tr_copy/fp64"};
-    (void)names;
+                                    "k_tr_ratios/fp64", "k_tr_final/fp64"};
     const int sms = sm_count(dev);
     const bool fused = c->tune.fused != 0;
     if (fused) {
@@ -1218,7 +1224,7 @@ int enqueue_horizontal(grist_mesh_s *h, TracerCtx *c, const Batch &B, cudaStream
         }
         return GRIST_OK;
     };
-    for (int ph = P_DIV; ph <= P_COPY; ph++) {
+    for (int ph = P_DIV; ph < P_NPHASE; ph++) {
         if (!B.fct && ph > P_UPD2) break;
         if (B.fct && ph == P_UPD2) continue;
         if (fused && (ph == P_EDGE0 || ph == P_EDGE1 || (!B.fct && ph == P_EDGE2))) continue;
@@ -1258,7 +1264,6 @@ int enqueue_horizontal(grist_mesh_s *h, TracerCtx *c, const Batch &B, cudaStream
             GRIST_PHASE_CASE(P_LOWRES)
             GRIST_PHASE_CASE(P_RATIOS)
             GRIST_PHASE_CASE(P_FINAL)
-            GRIST_PHASE_CASE(P_COPY)
 #undef GRIST_PHASE_CASE
 #undef GRIST_PHASE_LAUNCH
         }
