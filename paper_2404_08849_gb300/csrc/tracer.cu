@@ -379,13 +379,22 @@ __device__ __forceinline__ void item_edge_levels(const DevMesh &m, const MemberD
 
 // Cell-centric form of the edge flux (beta = 1, combined weights, every
 // stencil the upwind cell's ring {i, neighbours} in the order of the cell's
-// neighbour list): the thread of cell i gathers q over its ring once per
-// tracer and forms the flux of each edge whose flux leaves the cell, so each
-// edge-level is written once, by its upwind cell, with the weights and the
-// summation order of the edge-centric form (bit-identical), from 7 gathers
-// per cell-level instead of 7 per edge-level.
+// neighbour list): the thread of cell i gathers q over its ring and forms
+// the flux of each edge whose flux leaves the cell, so each edge-level is
+// written once, by its upwind cell, with the weights and the summation
+// order of the edge-centric form (bit-identical), from 7 gathers per
+// cell-level instead of 7 per edge-level.  The ring values of up to
+// kRingT tracers are gathered first, so each drained edge's weights are
+// read once for them; the cell's divergence signs are kept as two masks
+// (real edge; i is c1).  In the final stage of a limited step (qn = q^n)
+// the phase stores A = F^H - F^L, F^L = F q^n_i.
+#ifndef GRIST_TR_RING_T
+#define GRIST_TR_RING_T 2
+#endif
+constexpr int kRingT = GRIST_TR_RING_T;
 template <bool PERS, typename TQ, typename TC, int LPT>
-__device__ __forceinline__ void item_edge_ring(const DevMesh &m, const MemberDev &mb, const CellRow<TC> &r,
+__device__ __forceinline__ void item_edge_ring(const DevMesh &m, const MemberDev &mb, const int (&e)[GRIST_MAXE],
+                                               const int (&nb)[GRIST_MAXE], unsigned real, unsigned c1,
                                                const TQ *q, const TQ *qn, int t0, int t1, int i, int kg) {
     const int ld = mb.ld;
     TC *FH = (TC *)mb.FH;
@@ -397,27 +406,34 @@ __device__ __forceinline__ void item_edge_ring(const DevMesh &m, const MemberDev
         unsigned out = 0;
 #pragma unroll
         for (int j = 0; j < GRIST_MAXE; j++) {
-            f[j] = flux_at<PERS, TC>(mb, (size_t)r.e[j] * ld + k);
-            if (r.cw[j] != (TC)0 && ((f[j] >= (TC)0) == (r.cw[j] > (TC)0))) out |= 1u << j;
+            f[j] = flux_at<PERS, TC>(mb, (size_t)e[j] * ld + k);
+            if (((real >> j) & 1u) && ((f[j] >= (TC)0) == (((c1 >> j) & 1u) != 0))) out |= 1u << j;
         }
-        for (int t = t0; t < t1; t++) {
-            const TQ *qt = q + (size_t)t * mb.qs;
-            TC qr[GRIST_D2P];
-            qr[0] = static_cast<TC>(lds<PERS>(qt + (size_t)i * ld + k));
+        for (int tb = t0; tb < t1; tb += kRingT) {
+            const int nt = min(kRingT, t1 - tb);
+            TC qr[kRingT][GRIST_D2P], qup[kRingT];
 #pragma unroll
-            for (int j = 0; j < GRIST_MAXE; j++) qr[1 + j] = static_cast<TC>(lds<PERS>(qt + (size_t)r.nb[j] * ld + k));
-            TC *ft = FH + (size_t)t * mb.fs;
-            // the upwind cell's q^n of a limited final stage: this cell's
-            const TC qup = qn ? static_cast<TC>(qn[(size_t)t * mb.qs + (size_t)i * ld + k]) : (TC)0;
+            for (int a = 0; a < kRingT; a++) {
+                if (a >= nt) break;
+                const TQ *qt = q + (size_t)(tb + a) * mb.qs;
+                qr[a][0] = static_cast<TC>(lds<PERS>(qt + (size_t)i * ld + k));
+#pragma unroll
+                for (int j = 0; j < GRIST_MAXE; j++) qr[a][1 + j] = static_cast<TC>(lds<PERS>(qt + (size_t)nb[j] * ld + k));
+                qup[a] = qn ? static_cast<TC>(qn[(size_t)(tb + a) * mb.qs + (size_t)i * ld + k]) : (TC)0;
+            }
 #pragma unroll
             for (int j = 0; j < GRIST_MAXE; j++) {
                 if (!(out & (1u << j))) continue;
                 TC w[GRIST_D2P];
-                load_d2w_weights(m, r.e[j], r.cw[j] > (TC)0 ? 0 : 1, w);
-                TC v = 0;
+                load_d2w_weights(m, e[j], ((c1 >> j) & 1u) ? 0 : 1, w);
 #pragma unroll
-                for (int p = 0; p < GRIST_D2P; p++) v += w[p] * qr[p];
-                ft[(size_t)r.e[j] * ld + k] = qn ? antidiff(f[j], v, qup) : f[j] * v;
+                for (int a = 0; a < kRingT; a++) {
+                    if (a >= nt) break;
+                    TC v = 0;
+#pragma unroll
+                    for (int p = 0; p < GRIST_D2P; p++) v += w[p] * qr[a][p];
+                    FH[(size_t)(tb + a) * mb.fs + (size_t)e[j] * ld + k] = qn ? antidiff(f[j], v, qup[a]) : f[j] * v;
+                }
             }
         }
     }
@@ -601,9 +617,18 @@ __device__ void run_phase(const DevMesh &m, const Batch &B, uint32_t *status) {
             // the final stage of a limited step stores A = F^H - F^L
             const TQ *qn = (PH == P_EDGE2 && B.fct) ? (const TQ *)mb.q : nullptr;
             if (ring) {
-                CellRow<TC> r;
-                load_cell_row<true>(m, ent, r);
-                item_edge_ring<PERS, TQ, TC, LPT>(m, mb, r, qs, qn, t0, t1, ent, kg);
+                int e[GRIST_MAXE], nb[GRIST_MAXE];
+                TC cw[GRIST_MAXE];
+                load_row6(m.eoc8, ent, e);
+                load_row6(m.coc8, ent, nb);
+                load_row6(Coef<TC>::cdiv8(m), ent, cw);
+                unsigned real = 0, c1 = 0;
+#pragma unroll
+                for (int j = 0; j < GRIST_MAXE; j++) {
+                    if (cw[j] != (TC)0) real |= 1u << j;
+                    if (cw[j] > (TC)0) c1 |= 1u << j;
+                }
+                item_edge_ring<PERS, TQ, TC, LPT>(m, mb, e, nb, real, c1, qs, qn, t0, t1, ent, kg);
             } else {
                 item_edge_levels<PERS, TQ, TC, LPT>(m, mb, qs, qn, t0, t1, ent, kg, B.beta1, beta);
             }
