@@ -191,3 +191,24 @@ def test_deriv_two_quadratic_exact(mesh_cache, level):
             got = np.dot(cf[st >= 0], q)
             assert abs(got - exact) < 1e-8 * (abs(D) + abs(E) + abs(Fq)), (e, side)
             assert abs(np.sum(cf)) < 1e-9 * np.max(np.abs(cf))        # constants -> 0
+
+
+@pytest.mark.parametrize("level", [3, 5])
+def test_stencils_are_upwind_cell_rings(mesh_cache, level):
+    """The property the cell-centric edge fluxes rely on: the deriv-two
+    stencil of side s of every edge is the ring of its cell c_s - the cell
+    itself, then its neighbours in the order of cells_on_cell - and the cell
+    is c1 of an edge exactly when its edge sign is +1 (so the upwind cell of
+    an edge, F >= 0 -> c1, is known from the sign alone)."""
+    m = mesh_cache(level)
+    c12 = m["cells_on_edge"]
+    st = m["d2_stencil"]
+    ring = np.concatenate([np.arange(m["n_cells"])[:, None], m["cells_on_cell"]], 1)
+    for s in range(2):
+        assert np.array_equal(st[:, s, :], ring[c12[:, s]])
+    eoc, sgn = m["edges_on_cell"], m["edge_sign_on_cell"]
+    valid = eoc >= 0
+    cells = np.broadcast_to(np.arange(m["n_cells"])[:, None], eoc.shape)
+    is_c1 = c12[np.where(valid, eoc, 0), 0] == cells
+    assert np.array_equal((sgn > 0)[valid], is_c1[valid])
+    assert np.all(sgn[valid] != 0) and np.all(sgn[~valid] == 0)
