@@ -666,10 +666,10 @@ __device__ void run_phase(const DevMesh &m, const Batch &B, uint32_t *status) {
 // tracers).  Compile-time, per phase; 0 = only the limit that lets a block
 // of kTracerMaxBlock threads launch (65536 registers per SM), which is also
 // the FP64 policy's cap.
-#ifndef GRIST_TR_REGS_EDGE
+#ifndef GRIST_TR_REGS_EDGE   // edge fluxes, edge-centric form
 #define GRIST_TR_REGS_EDGE 56
 #endif
-#ifndef GRIST_TR_REGS_RING
+#ifndef GRIST_TR_REGS_RING   // edge fluxes, cell-centric form
 #define GRIST_TR_REGS_RING 72
 #endif
 #ifndef GRIST_TR_REGS_UPD
