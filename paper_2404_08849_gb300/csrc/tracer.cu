@@ -34,7 +34,7 @@ struct MemberDev {
     const double *dpi;      // [nC][ld]
     const double *F;        // [nE][ld]
     void *qA, *qB;          // scratch stage tracers [T][nC][ld]
-    void *FH;               // scratch edge fluxes [T][nE][ld]
+    void *FH;               // scratch edge fluxes [T][nE][ld]; A = F^H - F^L in a limited final stage
     void *R2;               // scratch FCT ratios {R+, R-} [T][nC][ld] pairs in the compute type
     void *X2;               // scratch FCT local bounds {max, min}(q^n, q^td) [T][nC][ld] pairs
     void *DFL;              // scratch FCT div F^L [T][nC][ld] in the compute type
