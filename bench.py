@@ -102,7 +102,7 @@ def algorithmic_bytes(name, nC, nE, nV, L, T, prec):
 FP64_WORK_MIX = {
     # kernel: (unit, FP64 flop per unit, DRAM bytes per unit)
     "k_nh_solve": ("c", 63.70, 280.8),
-    "k_momentum": ("e", 19.88, 36.8),
+    "k_momentum": ("e", 19.88, 36.9),      # DRAM: the capture with the edge PV formed in the kernel
     "k_nh_explicit": ("i", 13.38, 73.4),
     "k_ke": ("c", 18.00, 18.3),
     "k_eos": ("c", 93.0, 21.1),
